@@ -1,0 +1,341 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix (no GPU needed).
+
+Each test names the passage of arXiv:2506.19339 (or the external closed form) it checks.  They are
+chosen so that a plausible mistake in the oracle -- a dropped term, a swapped leg, a wrong sign,
+a transposed operand -- fails at least one of them.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import bruteforce, ising, onsager, reduced_ctmrg, split_ctmrg as sc
+from paper_2506_19339_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), 'golden')
+
+
+def _rand_env(rng, chi, D, d):
+    env = {c: rng.standard_normal((chi, chi)) for c in ('C1', 'C2', 'C3', 'C4')}
+    for t in ('T1', 'T2', 'T3', 'T4'):
+        env[t] = [rng.standard_normal((chi, chi, m)) for m in (D, d, D)]
+    return env
+
+
+def _rand_problem(seed, chi=3, D=2, d=3, p=2):
+    rng = np.random.default_rng(seed)
+    O = rng.standard_normal((p, p, d, d, d, d))
+    A = rng.standard_normal((p, D, D, D, D))
+    B = rng.standard_normal((p, D, D, D, D))
+    return _rand_env(rng, chi, D, d), A, O, B
+
+
+# ---------------------------------------------------------------- V1: model tensors (Sec. II, IV)
+
+def test_sqrt_boltzmann_closed_form():
+    """sqrt(W)^2 = W, and the eigendecomposition gives the closed form: eigenvalues 2cosh(beta) on
+    (1,1)/sqrt2 and 2sinh(beta) on (1,-1)/sqrt2."""
+    for beta in (0.0, 0.1, 1 / 4.5115, 1.0):
+        W = ising.boltzmann_matrix(beta)
+        Q = ising.sqrt_boltzmann(beta)
+        assert np.allclose(Q @ Q, W, rtol=1e-14, atol=1e-14)
+        a = (np.sqrt(2 * np.cosh(beta)) + np.sqrt(2 * np.sinh(beta))) / 2
+        b = (np.sqrt(2 * np.cosh(beta)) - np.sqrt(2 * np.sinh(beta))) / 2
+        assert np.allclose(Q, [[a, b], [b, a]], rtol=1e-13, atol=1e-15)
+
+
+@pytest.mark.parametrize('L', [(2, 2, 2), (2, 2, 3), (1, 3, 2)])
+def test_pepo_trace_is_ising_partition_function(L):
+    """Eq. "TN for partition function": tTr of the uniform O network equals the enumerated 3D Ising
+    partition function on a periodic lattice."""
+    beta = 1 / 4.6
+    Z_tn = bruteforce.pepo_network_trace(ising.ising_pepo(beta), L)
+    Z_bf = bruteforce.ising_Z_enumeration(beta, L)
+    assert abs(Z_tn - Z_bf) <= 1e-13 * Z_bf
+
+
+def test_pepo_symmetries():
+    """O is invariant under the full cubic group (Sec. IV): any leg permutation, in particular
+    s_up <-> s_dn, which the frames of the split-CTMRG rely on."""
+    O = ising.ising_pepo(1 / 4.5)
+    for perm in [(1, 0, 2, 3, 4, 5), (0, 1, 3, 2, 5, 4), (2, 3, 0, 1, 5, 4), (5, 4, 3, 2, 1, 0)]:
+        assert np.allclose(O, O.transpose(perm), atol=1e-15)
+
+
+# ---------------------------------------------------------------- V2: network conventions
+
+@pytest.mark.parametrize('Lx,Ly', [(2, 2), (3, 2)])
+def test_torus_overlap_equals_reduced_network(Lx, Ly):
+    """Eq. "free energy expression": <psi|T|psi> with T built by enumeration from W and sqrt(W)
+    equals the tensor trace of the reduced site tensor a = A-bar O A on the same torus; the norm
+    <psi|psi> equals the trace of A-bar 1 A."""
+    rng = np.random.default_rng(11)
+    A = rng.standard_normal((2, 2, 2, 2, 2))
+    beta = 1 / 4.5
+    psi = bruteforce.peps_torus_amplitudes(A, Lx, Ly)
+    Tm = bruteforce.transfer_matrix_torus(beta, Lx, Ly)
+    num_bf = psi @ Tm @ psi
+    den_bf = psi @ psi
+    a = bruteforce.reduced_site_tensor(A, ising.ising_pepo(beta), A)
+    a0 = bruteforce.reduced_site_tensor(A, ising.identity_pepo(), A)
+    assert abs(bruteforce.torus_trace_site(a, Lx, Ly) - num_bf) <= 1e-12 * abs(num_bf)
+    assert abs(bruteforce.torus_trace_site(a0, Lx, Ly) - den_bf) <= 1e-12 * abs(den_bf)
+
+
+# ---------------------------------------------------------------- V3: split form == fused form
+
+def _fuse(env):
+    f = {k: env[k] for k in ('C1', 'C2', 'C3', 'C4')}
+    for t in ('T1', 'T2', 'T3', 'T4'):
+        k, i, b = env[t]
+        F = np.einsum('acx,cey,ebz->abxyz', k, i, b)
+        f[t] = F.reshape(F.shape[0], F.shape[1], -1)
+    return f
+
+
+def test_split_local_contractions_equal_fused():
+    """Sec. III.A: Z00, Z10, Z01, Z11 and the bra environment E computed with the three split edge
+    layers equal the same quantities with the layers fused into one edge tensor and A, O, A-bar
+    fused into a (exact identity)."""
+    env, A, O, _ = _rand_problem(1, chi=3, D=2, d=3)
+    loc = sc.local_contractions(env, A, O, A)
+    E = sc.bra_environment(env, loc)
+    ref = reduced_ctmrg.local_values(_fuse(env), A, O)
+    for k in ('Z00', 'Z10', 'Z01', 'Z11'):
+        assert abs(loc[k] - ref[k]) <= 1e-12 * abs(ref[k]), k
+    assert np.allclose(E, ref['E'], rtol=1e-11, atol=1e-11 * np.abs(ref['E']).max())
+
+
+def test_z11_is_the_same_through_every_cut():
+    """The full 3x3 network evaluated across the kappa, iota and alpha cuts and from the top."""
+    env, A, O, B = _rand_problem(2, chi=5, D=4, d=3)
+    loc = sc.local_contractions(env, A, O, B)
+    vals = [np.sum(loc['Uk'] * loc['Lk']), np.sum(loc['Ui'] * loc['Li']),
+            np.sum(loc['Ua'] * loc['Cbot']), np.sum(loc['Ctop'] * loc['La'])]
+    assert np.allclose(vals, vals[0], rtol=1e-12)
+    assert abs(np.sum(A * sc.ket_environment(env, loc)) - vals[0]) <= 1e-12 * abs(vals[0])
+    assert abs(np.sum(B * sc.bra_environment(env, loc)) - vals[0]) <= 1e-12 * abs(vals[0])
+
+
+# ---------------------------------------------------------------- frames (the four moves)
+
+def test_frames_relabel_the_same_network():
+    """The right / up / down moves are the left move in a relabelled network: Z00 and Z11 are
+    unchanged, Z10 and Z01 trade places under the diagonal reflection, and every frame round-trips."""
+    env, A, O, B = _rand_problem(3, chi=3, D=2, d=3)
+    l0 = sc.local_contractions(env, A, O, B)
+    for w in 'LRUD':
+        e, a, o, b = sc.to_frame(w, env, A, O, B)
+        l1 = sc.local_contractions(e, a, o, b)
+        swap = w in 'UD'
+        assert abs(l1['Z11'] - l0['Z11']) <= 1e-12 * abs(l0['Z11'])
+        assert abs(l1['Z00'] - l0['Z00']) <= 1e-12 * abs(l0['Z00'])
+        assert abs(l1['Z10'] - l0['Z01' if swap else 'Z10']) <= 1e-12 * abs(l1['Z10'])
+        back = sc.from_frame(w, e)
+        for k in ('C1', 'C2', 'C3', 'C4'):
+            assert np.array_equal(back[k], env[k])
+        for t in ('T1', 'T2', 'T3', 'T4'):
+            for i in range(3):
+                assert np.array_equal(back[t][i], env[t][i])
+
+
+# ---------------------------------------------------------------- wiring: exact when nothing is cut
+
+def _absorb_row(X, env, A, O, B):
+    """X[v, a, o, b, A, O, B, w] (two columns, open at the bottom) -> one row further down."""
+    T4k, T4i, T4b = env['T4']
+    T2k, T2i, T2b = env['T2']
+    X = sc._c2('vaobPQRw,vxl->xaobPQRwl', X, T4k)
+    X = sc._c2('xaobPQRwl,salEr->xobPQRwsEr', X, A)
+    X = sc._c2('xobPQRwsEr,SPrFG->xobQRwsESFG', X, A)
+    X = sc._c2('xobQRwsESFG,wyG->xobQRsESFy', X, T2k)
+    X = sc._c2('xobQRsESFy,xXl->XobQRsESFyl', X, T4i)
+    X = sc._c2('XobQRsESFyl,tsolfq->XbQRESFytfq', X, O)
+    X = sc._c2('XbQRESFytfq,TSQqgH->XbREFytfTgH', X, O)
+    X = sc._c2('XbREFytfTgH,yYH->XbREFtfTgY', X, T2i)
+    X = sc._c2('XbREFtfTgY,XZl->bREFtfTgYZl', X, T4b)
+    X = sc._c2('bREFtfTgYZl,tblhm->REFfTgYZhm', X, B)
+    X = sc._c2('REFfTgYZhm,TRmKn->EFfgYZhKn', X, B)
+    X = sc._c2('EFfgYZhKn,YWn->EFfgZhKW', X, T2b)
+    return X.transpose(4, 0, 2, 5, 1, 3, 6, 7)
+
+
+def _two_column_Z(env, A, O, B, rows):
+    Ct1, Ct2, Ct3, Ct4 = sc.absorbed_corners(env)
+    X = np.einsum('hvpob,hwPQR->vpobPQRw', Ct1, Ct2)
+    for _ in range(rows):
+        X = _absorb_row(X, env, A, O, B)
+    bot = np.einsum('hvpob,hwPQR->vpobPQRw', Ct4, Ct3)
+    return float(np.sum(X * bot))
+
+
+def test_untruncated_projectors_are_exact():
+    """Sec. III.C: with every singular value kept, P_T P_B = I and inserting the projectors changes
+    no network.  Pins the one-column patches, the two-column patches of every stage-2 projector
+    (against a direct row-by-row contraction), and the renormalisation: after an untruncated left
+    move the new corners / edges reproduce the old network one column wider
+    (Z00' = Z10, Z01' = Z11)."""
+    env, A, O, B = _rand_problem(4, chi=2, D=2, d=3)
+    halves = sc.one_column_halves(env, A, O, B)
+    left, right = sc.stage1_projectors(halves, None, 1e-10)
+    for cut, (U, L) in halves.items():
+        PB, PT, _ = left[cut]
+        k = PT.shape[0]
+        P = PT.reshape(k, -1) @ PB.reshape(-1, k)
+        kept = np.diag(P) > 0.5
+        assert np.allclose(P, np.diag(kept.astype(float)), atol=1e-8)
+        assert kept.sum() == min(PB.reshape(-1, k).shape[0], k)
+    h2 = sc.two_column_halves(env, A, O, B, left, right)
+    z1 = _two_column_Z(env, A, O, B, 1)
+    z2 = _two_column_Z(env, A, O, B, 2)
+    assert abs(np.sum(h2['kappa'][0] * h2['kappa'][1]) - z1) <= 1e-8 * abs(z1)
+    assert abs(np.sum(h2['iota'][0] * h2['iota'][1]) - z1) <= 1e-8 * abs(z1)
+    assert abs(np.sum(h2['alpha'][0] * h2['alpha'][1]) - z2) <= 1e-8 * abs(z2)
+    old = sc.local_contractions(env, A, O, B)
+    C1n, T4n, C4n = sc.left_move(env, A, O, B, None, 1e-10, normalise=False)
+    new_env = dict(env)
+    new_env.update({'C1': C1n, 'T4': T4n, 'C4': C4n})
+    new = sc.local_contractions(new_env, A, O, B)
+    assert abs(new['Z00'] - old['Z10']) <= 1e-7 * abs(old['Z10'])
+    assert abs(new['Z01'] - old['Z11']) <= 1e-7 * abs(old['Z11'])
+
+
+# ---------------------------------------------------------------- V4: projector identities
+
+def test_projector_pair_identities():
+    """Eqs. "projector construction" and "projector construction 2": P_T P_B = I_chi;
+    rho_B P_B = U~ S~^1/2 and P_T rho_T = S~^1/2 V~^T, so rho_B P_B P_T rho_T is the best rank-chi
+    approximation of rho_B rho_T (Eckart-Young)."""
+    rng = np.random.default_rng(5)
+    U = rng.standard_normal((3, 4, 2, 5))
+    L = rng.standard_normal((3, 4, 2, 5))
+    chi = 6
+    PB, PT, S = sc.projector_pair(U, L, (0, 2), chi, 1e-12)
+    assert np.allclose(np.einsum('kab,abl->kl', PT, PB), np.eye(chi), atol=1e-10)
+    Um = U.transpose(0, 2, 1, 3).reshape(6, 20)
+    Lm = L.transpose(0, 2, 1, 3).reshape(6, 20)
+    M = Lm.T @ Um
+    approx = Lm.T @ PB.reshape(6, chi) @ PT.reshape(chi, 6) @ Um
+    u, s, vh = np.linalg.svd(M)
+    best = (u[:, :chi] * s[:chi]) @ vh[:chi]
+    assert np.allclose(approx, best, atol=1e-10 * s[0])
+    # sign gauge: largest-magnitude entry of each kept left vector is positive
+    assert np.all(S[:-1] >= S[1:])
+
+
+# ---------------------------------------------------------------- V5 / V6: closed forms
+
+def test_onsager_closed_forms():
+    """Onsager: ln z(K_c) = ln(2)/2 + 2G/pi (G Catalan's constant), ln z(0) = ln 2."""
+    G = 0.915965594177219015054603514932
+    Kc = 0.5 * np.log(1 + np.sqrt(2))
+    assert abs(onsager.ln_z_onsager(Kc) - (0.5 * np.log(2) + 2 * G / np.pi)) < 1e-12
+    assert abs(onsager.ln_z_onsager(0.0) - np.log(2)) < 1e-15
+
+
+def test_reduced_ctmrg_plus_state_is_onsager():
+    """For the product PEPS |+> the numerator is cosh(beta) x the 2D Ising network (Sec. II with
+    D=1), so f = -T[ln cosh(1/T) + ln z_Onsager(1/T)].  Reduced CTMRG, T = 4.6, chi = 16."""
+    T = 4.6
+    A = inputs.product_plus_peps()
+    r = reduced_ctmrg.evaluate(A, ising.ising_pepo(1 / T), ising.identity_pepo(), T, 16, 100, 1e-13)
+    assert abs(r['f'] - onsager.f_plus_state(T)) < 1e-10 * abs(r['f'])
+    # the value quoted for this case in the project survey (computed there by quadrature)
+    assert abs(onsager.f_plus_state(4.6) - (-3.5226689540075)) < 1e-12
+
+
+def test_split_ctmrg_plus_state_is_onsager():
+    """The same closed form through the split-CTMRG engine.  A product PEPS leaves the kappa / iota
+    bonds at rank 2 in this scheme (their patches connect left and right only through the
+    boundary and the trivial A / A-bar lines), an error of order the third corner singular value;
+    at T = 10 it is far below the tolerance."""
+    T = 10.0
+    A = inputs.product_plus_peps()
+    r = sc.evaluate(A, ising.ising_pepo(1 / T), ising.identity_pepo(), T, 8, 100, 1e-13)
+    assert abs(r['f'] - onsager.f_plus_state(T)) < 1e-10 * abs(r['f'])
+
+
+@pytest.mark.parametrize('D', [1, 2])
+def test_infinite_temperature_product_state(D):
+    """beta = 0: O has rank 1 in the plane, and for a product PEPS beta*f = -ln 2 exactly."""
+    A = inputs.product_plus_peps(D)
+    r = sc.evaluate(A, ising.ising_pepo(0.0), ising.identity_pepo(), np.inf, 4, 5, None)
+    assert abs(r['beta_f'] + np.log(2)) < 1e-12
+
+
+# ---------------------------------------------------------------- V7: invariances
+
+def test_free_energy_invariances():
+    """f(cA) = f(A) (so <A, g> = 0); f is invariant under an orthogonal gauge transformation of
+    the virtual bonds (with the starting environment transformed alike, every step of the
+    algorithm is covariant); kappa is invariant under rescaling of any environment tensor."""
+    T = 4.6
+    O, Oid = ising.ising_pepo(1 / T), ising.identity_pepo()
+    A = inputs.perturbed_product_peps(2, 7)
+    r0 = sc.evaluate(A, O, Oid, T, 6, 8)
+    r1 = sc.evaluate(3.7 * A, O, Oid, T, 6, 8)
+    assert abs(r0['f'] - r1['f']) < 1e-10 * abs(r0['f'])
+    assert abs(np.sum(A * r0['g'])) < 1e-12 * np.linalg.norm(r0['g'])
+    rng = np.random.default_rng(9)
+    G = np.linalg.qr(rng.standard_normal((2, 2)))[0]
+    H = np.linalg.qr(rng.standard_normal((2, 2)))[0]
+    Ag = np.einsum('sulde,uU,lL,dD,eE->sULDE', A, H, G, H, G)
+    envs = []
+    for d in (2, 1):
+        e = sc.init_env(6, 2, d)
+        for t, M in (('T1', H), ('T3', H), ('T2', G), ('T4', G)):
+            e[t] = [np.einsum('abm,mM->abM', e[t][0], M), e[t][1], np.einsum('abm,mM->abM', e[t][2], M)]
+        envs.append(e)
+    r2 = sc.evaluate(Ag, O, Oid, T, 6, 8, env_num=envs[0], env_den=envs[1])
+    assert abs(r0['f'] - r2['f']) < 1e-10 * abs(r0['f'])
+    env, A3, O3, B3 = _rand_problem(6)
+    k0 = sc.local_contractions(env, A3, O3, B3)
+    env['C2'] = 2.5 * env['C2']
+    env['T3'][1] = -0.3 * env['T3'][1]
+    k1 = sc.local_contractions(env, A3, O3, B3)
+    kap = lambda l: l['Z11'] * l['Z00'] / (l['Z10'] * l['Z01'])
+    assert abs(kap(k0) - kap(k1)) < 1e-12 * abs(kap(k0))
+
+
+# ---------------------------------------------------------------- V8 / V9: reference algorithm, FD
+
+@pytest.mark.slow
+def test_split_converges_to_reduced_reference():
+    """Sec. IV.A: the split result approaches the reduced method at large chi as chi grows (the
+    paper's own accuracy check, with the reduced method as the reference)."""
+    T = 4.6
+    O, Oid = ising.ising_pepo(1 / T), ising.identity_pepo()
+    A = inputs.perturbed_product_peps(2, 7)
+    ref = reduced_ctmrg.evaluate(A, O, Oid, T, 48, 100, 1e-11)['f']
+    gaps = [abs(sc.evaluate(A, O, Oid, T, chi, 100, 1e-10)['f'] - ref) for chi in (8, 16, 24)]
+    assert gaps[0] > gaps[1] > gaps[2]
+    assert gaps[2] < 1e-7
+
+
+@pytest.mark.slow
+def test_gradient_against_finite_differences():
+    """Eq. "gradient expression": the environment gradient g = 2 d f / d A-bar agrees with central
+    finite differences of f along random directions up to the truncation gap."""
+    T = 4.6
+    O, Oid = ising.ising_pepo(1 / T), ising.identity_pepo()
+    A = inputs.perturbed_product_peps(2, 7)
+    r = sc.evaluate(A, O, Oid, T, 12, 100, 1e-11)
+    rng = np.random.default_rng(3)
+    h = 1e-5
+    for _ in range(2):
+        v = rng.standard_normal(A.shape)
+        v -= np.sum(v * A) * A / np.sum(A * A)
+        fp = sc.evaluate(A + h * v, O, Oid, T, 12, 100, 1e-11)['f']
+        fm = sc.evaluate(A - h * v, O, Oid, T, 12, 100, 1e-11)['f']
+        fd = (fp - fm) / (2 * h)
+        assert abs(fd - np.sum(r['g'] * v)) < 1e-4 * np.linalg.norm(r['g']) * np.linalg.norm(v)
+
+
+# ---------------------------------------------------------------- counter-based initialisation
+
+def test_splitmix64_known_answers():
+    lines = open(os.path.join(GOLDEN, 'splitmix64_seed0.txt')).read().splitlines()
+    vals = [int(x) for x in lines if x.strip() and not x.startswith('#')]
+    u = sc.splitmix64_uniform(0, [0, 1])
+    assert u[0] == (vals[0] >> 11) * 2.0 ** -53
+    assert u[1] == (vals[1] >> 11) * 2.0 ** -53
