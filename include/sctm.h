@@ -1,0 +1,165 @@
+/*
+ * sctm.h -- C ABI of the GB300 split-CTMRG library (libsctm.so).
+ *
+ * Split corner-transfer renormalization group for the triple-layer PEPS-PEPO-PEPS network of a
+ * 3D classical model (Xu, Lin & Zhang, arXiv:2506.19339): the free-energy density
+ *     f = -T (ln kappa_num - ln kappa_den)                        (Sec. II, Eq. "free energy expression")
+ * and its gradient g = 2 df/dA-bar                               (Sec. II, Eq. "gradient expression")
+ * from converged split-CTM environments (Sec. III) of the numerator <psi|T|psi> and of the norm
+ * <psi|psi>.  All compute runs in CUDA kernels on one GPU; cuSOLVER is used for the FP64 SVDs.
+ *
+ * Conventions shared by every entry point
+ *   - Tensors are dense, row-major, FP64.
+ *       PEPS  A[s,u,l,d,r]          shape (p, D, D, D, D)      (bra = A, real)
+ *       PEPO  O[s_up,s_dn,u,l,d,r]  shape (p, p, d, d, d, d)   (s_dn joins the ket, s_up the bra)
+ *   - Pointer arguments documented as "host or device" are inspected with
+ *     cudaPointerGetAttributes; either kind is accepted.  The library never keeps or frees a
+ *     caller's pointer: inputs are copied, outputs are written.
+ *   - Every call returns an sctm_status and never aborts; a context-level message is available
+ *     from sctm_last_error().  A NULL context returns SCTM_EINVAL.
+ *   - Calls on one context are not thread-safe; different contexts are independent.
+ *   - Results are deterministic: the same inputs and options give the same bits on the same GPU
+ *     (all reductions have a fixed order).
+ */
+#ifndef SCTM_H
+#define SCTM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sctm_ctx sctm_ctx;
+
+typedef enum {
+    SCTM_OK = 0,
+    SCTM_EINVAL = 1,     /* bad argument (NULL pointer, size out of range, unknown option)      */
+    SCTM_ECUDA = 2,      /* a CUDA runtime call or kernel launch failed                          */
+    SCTM_ECUSOLVER = 3,  /* a cuSOLVER call failed or did not converge                           */
+    SCTM_ENOMEM = 4,     /* device memory allocation failed                                      */
+    SCTM_ENOCONV = 5,    /* iteration limit reached before ||S[i+1]-S[i]||_2 < tol (Sec. III.D)  */
+    SCTM_ENUMERIC = 6,   /* kappa <= 0, a non-finite value, or an all-zero spectrum              */
+    SCTM_ETIMEOUT = 7    /* reserved: a bounded device-side wait ran out                         */
+} sctm_status;
+
+/* Arithmetic of the contraction kernels.  SVDs, normalisations and the free-energy ratio are
+ * FP64 in every mode. */
+enum {
+    SCTM_PREC_FP64 = 0,    /* all contractions in FP64                                         */
+    SCTM_PREC_TF32 = 1,    /* contractions on tensor cores, TF32 inputs, FP32 accumulation     */
+    SCTM_PREC_TF32X3 = 2,  /* TF32 with hi/lo split products (hi*hi + hi*lo + lo*hi)            */
+    SCTM_PREC_BF16 = 3,    /* contractions on tensor cores, BF16 inputs, FP32 accumulation     */
+    SCTM_PREC_BF16X3 = 4   /* BF16 with hi/lo split products                                   */
+};
+
+enum { SCTM_GRAD_ENV = 0, SCTM_GRAD_ADJOINT = 1 };
+enum { SCTM_NET_NUM = 0, SCTM_NET_DEN = 1 };          /* <psi|T|psi> and <psi|psi>            */
+enum { SCTM_MOVE_LEFT = 0, SCTM_MOVE_RIGHT = 1, SCTM_MOVE_UP = 2, SCTM_MOVE_DOWN = 3 };
+
+typedef struct {
+    double T;                     /* temperature; f = -T (...), g = -2T (...)               */
+    int D;                        /* PEPS virtual bond dimension, >= 1                      */
+    int p;                        /* physical dimension (2 for Ising), >= 1                 */
+    int d;                        /* PEPO in-plane bond dimension (2 for Ising), >= 1       */
+    int precision;                /* SCTM_PREC_*                                            */
+    int grad_mode;                /* SCTM_GRAD_ENV (the only mode implemented)              */
+    double svd_cutoff;            /* pseudo-inverse cutoff s_k/s_1 (default 1e-12)          */
+    unsigned long long init_seed; /* SplitMix64 seed of the cold-start environment (0)      */
+    int batch;                    /* reserved, must be 1                                    */
+    void* cuda_stream;            /* cudaStream_t for all work, NULL = legacy default       */
+} sctm_opts;
+
+/* Fill *o with the defaults: T=1, D=2, p=2, d=2, FP64, env gradient, cutoff 1e-12, seed 0,
+ * batch 1, default stream.  Returns SCTM_EINVAL for NULL. */
+sctm_status sctm_default_opts(sctm_opts* o);
+
+/* sctm_create -- the problem statement of Sec. II: a PEPS tensor A, a PEPO tensor O and the
+ * environment bond dimension chi.
+ *   peps  host or device, p*D^4 doubles, layout A[s,u,l,d,r]                 (copied)
+ *   pepo  host or device, p^2*d^4 doubles, layout O[s_up,s_dn,u,l,d,r]        (copied)
+ *   chi   environment bond dimension, 1 <= chi <= 4096
+ *   o     options (NULL = defaults); o->D, o->p, o->d give the shapes
+ *   out   receives the new context (NULL on failure)
+ * Allocates every device buffer of both networks (numerator with O, norm with the identity
+ * PEPO), builds the execution plans and writes the cold-start environment (SplitMix64, Sec. III
+ * gives no initialisation).  Errors: EINVAL (shapes, NULL), ENOMEM, ECUDA, ECUSOLVER. */
+sctm_status sctm_create(const double* peps, const double* pepo, int chi, const sctm_opts* o,
+                        sctm_ctx** out);
+
+/* sctm_set_peps -- replace A (host or device pointer, p*D^4 doubles, copied).  With
+ * reset_env != 0 the environments go back to the cold start; otherwise the current
+ * environments are kept as a warm start.  Errors: EINVAL, ECUDA. */
+sctm_status sctm_set_peps(sctm_ctx* ctx, const double* peps, int reset_env);
+
+/* sctm_iterate -- power iteration of both environments (Sec. III.B: left, right, up, down
+ * moves per iteration; Sec. III.D: stop once ||S[i+1]-S[i]||_2 < tol for the singular values S
+ * of rho_eff = C1 C2 C3 C4 / Tr).  Each network stops on its own.  tol <= 0 runs exactly
+ * max_it iterations.  *it_done (may be NULL) = the larger iteration count of the two networks;
+ * *last_dS (may be NULL) = the larger final ||dS||_2.  Returns SCTM_ENOCONV when tol > 0 and a
+ * network did not converge within max_it (the environments are still updated). */
+sctm_status sctm_iterate(sctm_ctx* ctx, int max_it, double tol, int* it_done, double* last_dS);
+
+/* sctm_free_energy -- f per 3D site in FP64 from the current environments (Sec. II):
+ * kappa = Z11 Z00 / (Z10 Z01) per network, f = -T (ln kappa_num - ln kappa_den).
+ *   f  host pointer to one double.
+ * Returns SCTM_ENUMERIC if a kappa is <= 0 or not finite (f is then NaN), SCTM_ENOCONV if the
+ * last sctm_iterate did not converge (f is still written). */
+sctm_status sctm_free_energy(sctm_ctx* ctx, double* f);
+
+/* sctm_grad -- the environment gradient g = -2T (E_num/Z11_num - E_den/Z11_den) (Sec. II,
+ * Fig. 4(c): E = Z11 with A-bar removed).
+ *   g  host or device pointer to p*D^4 doubles (layout of A), caller-owned.
+ * Same status rules as sctm_free_energy. */
+sctm_status sctm_grad(sctm_ctx* ctx, double* g);
+
+/* sctm_destroy -- release every resource of the context.  NULL-safe (returns SCTM_OK). */
+sctm_status sctm_destroy(sctm_ctx* ctx);
+
+/* sctm_ising_pepo -- host helper: the Ising PEPO at temperature T (Sec. II, Sec. IV): the
+ * six-leg delta tensor with sqrt(W), W = [[e^b, e^-b], [e^-b, e^b]], b = 1/T, on every leg.
+ *   O64  host pointer to 64 doubles, layout O[s_up,s_dn,u,l,d,r].  T <= 0 -> SCTM_EINVAL;
+ *   T = +inf gives the b = 0 tensor. */
+sctm_status sctm_ising_pepo(double T, double* O64);
+
+/* sctm_last_error -- message of the last failing call on ctx ("" if none; a static message
+ * for NULL).  The pointer stays valid until the next call on ctx. */
+const char* sctm_last_error(const sctm_ctx* ctx);
+
+/* ---- inspection and checkpoint / resume -------------------------------------------------- */
+
+/* Number of doubles of one network's environment in the export layout:
+ * C1, C2, C3, C4 (chi x chi each), then T1^{ket,int,bra}, T2^{...}, T3^{...}, T4^{...}
+ * (chi x chi x m each, m = D for ket/bra, d for int; d = 1 for the norm network).
+ * Returns 0 for a NULL context or an unknown network. */
+size_t sctm_env_size(const sctm_ctx* ctx, int network);
+
+/* Copy one network's environment to / from a host buffer of sctm_env_size() doubles.  Leg
+ * order (Sec. III.A): C1[h,v] (h to the top chain, v to the left chain), C2[h,v] (top, right),
+ * C3[h,v] (bottom, right), C4[h,v] (bottom, left); T1[a,b,m] (left bond, right bond, leg down
+ * into the site), T2[a,b,m] (up, down, leg left), T3[a,b,m] (left, right, leg up), T4[a,b,m]
+ * (up, down, leg right); each tensor row-major.  import overwrites the current environment
+ * (warm start).  Errors: EINVAL (network, NULL, n too small), ECUDA. */
+sctm_status sctm_env_export(sctm_ctx* ctx, int network, double* host_buf, size_t n);
+sctm_status sctm_env_import(sctm_ctx* ctx, int network, const double* host_buf, size_t n);
+
+/* sctm_move -- run one directional move (SCTM_MOVE_*) of one network (Sec. III.B), without a
+ * convergence check.  For inspection and tests. */
+sctm_status sctm_move(sctm_ctx* ctx, int network, int direction);
+
+/* sctm_spectrum -- the chi singular values of rho_eff of one network (Sec. III.D), descending,
+ * into a host buffer of chi doubles. */
+sctm_status sctm_spectrum(sctm_ctx* ctx, int network, double* S);
+
+/* sctm_profile -- cumulative device time (ms) of the contraction kernels, of the SVDs and of
+ * everything since the context was created or since the last reset (reset != 0 zeroes the
+ * counters after reading).  Timing is recorded only when the environment variable
+ * SCTM_PROFILE=1 was set at create time; otherwise the values are 0. */
+sctm_status sctm_profile(sctm_ctx* ctx, double* ctr_ms, double* svd_ms, double* total_ms,
+                         long long* ctr_launches, long long* ctr_flops, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SCTM_H */

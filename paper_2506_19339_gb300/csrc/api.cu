@@ -1,0 +1,393 @@
+// The C ABI of libsctm.so (declared in include/sctm.h).
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "engine.h"
+
+using namespace sctm;
+
+struct sctm_ctx {
+    std::unique_ptr<Engine> eng;
+    Network net[2];
+    sctm_opts opts{};
+    int chi = 0;
+    double* A_dev = nullptr;
+    double* A_stage = nullptr;
+    double* O_dev = nullptr;
+    double* Oid_dev = nullptr;
+    double* f_dev = nullptr;
+    double* g_dev = nullptr;
+    int* flag_dev = nullptr;
+    std::string err;
+    bool converged = true;
+};
+
+namespace {
+
+const char* kNullCtx = "sctm: NULL context";
+
+#define API_BEGIN(ctx)                  \
+    if (!(ctx)) return SCTM_EINVAL;     \
+    (ctx)->err.clear();                 \
+    try {
+#define API_END(ctx)                                             \
+    }                                                            \
+    catch (const Error& e) {                                     \
+        (ctx)->err = e.what();                                   \
+        return e.code;                                           \
+    }                                                            \
+    catch (const std::exception& e) {                            \
+        (ctx)->err = e.what();                                   \
+        return SCTM_ECUDA;                                       \
+    }
+
+void check_cuda(const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) throw Error(SCTM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+void cuda_ok(cudaError_t e, const char* what) {
+    if (e != cudaSuccess)
+        throw Error(e == cudaErrorMemoryAllocation ? SCTM_ENOMEM : SCTM_ECUDA,
+                    std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+long long peps_size(const sctm_opts& o) { return (long long)o.p * o.D * o.D * o.D * o.D; }
+long long pepo_size(const sctm_opts& o) { return (long long)o.p * o.p * o.d * o.d * o.d * o.d; }
+
+// guard on entry: a PEPS with a non-finite entry never reaches an SVD
+bool peps_is_finite(sctm_ctx* c, const double* dev) {
+    launch_check_finite(dev, peps_size(c->opts), c->flag_dev, c->eng->stream);
+    int flag = 1;
+    cuda_ok(cudaMemcpyAsync(&flag, c->flag_dev, sizeof(int), cudaMemcpyDeviceToHost, c->eng->stream),
+            "finite flag copy");
+    cuda_ok(cudaStreamSynchronize(c->eng->stream), "finite flag sync");
+    return flag == 0;
+}
+
+void check_svd_info(sctm_ctx* c) {
+    for (int n = 0; n < 2; ++n) {
+        Network& net = c->net[n];
+        std::vector<int> info(std::max(net.n_svd, 1));
+        cuda_ok(cudaMemcpyAsync(info.data(), net.svd_info, info.size() * sizeof(int),
+                                cudaMemcpyDeviceToHost, c->eng->stream),
+                "svd info copy");
+        cuda_ok(cudaStreamSynchronize(c->eng->stream), "stream sync");
+        for (int v : info)
+            if (v != 0)
+                throw Error(SCTM_ECUSOLVER, "gesvd reported info=" + std::to_string(v) +
+                                                (n ? " (norm network)" : " (numerator network)"));
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+sctm_status sctm_default_opts(sctm_opts* o) {
+    if (!o) return SCTM_EINVAL;
+    std::memset(o, 0, sizeof(*o));
+    o->T = 1.0;
+    o->D = 2;
+    o->p = 2;
+    o->d = 2;
+    o->precision = SCTM_PREC_FP64;
+    o->grad_mode = SCTM_GRAD_ENV;
+    o->svd_cutoff = 1e-12;
+    o->init_seed = 0;
+    o->batch = 1;
+    o->cuda_stream = nullptr;
+    return SCTM_OK;
+}
+
+sctm_status sctm_ising_pepo(double T, double* O64) {
+    if (!O64 || !(T > 0.0)) return SCTM_EINVAL;
+    const double b = std::isinf(T) ? 0.0 : 1.0 / T;
+    // sqrt(W): eigenvalues 2cosh(b) on (1,1)/sqrt2 and 2sinh(b) on (1,-1)/sqrt2 (Sec. IV)
+    const double cp = std::sqrt(2.0 * std::cosh(b)), sm = std::sqrt(2.0 * std::sinh(b));
+    const double Q[2][2] = {{0.5 * (cp + sm), 0.5 * (cp - sm)}, {0.5 * (cp - sm), 0.5 * (cp + sm)}};
+    for (int i = 0; i < 64; ++i) {
+        int idx[6];
+        for (int k = 0; k < 6; ++k) idx[k] = (i >> (5 - k)) & 1;
+        double v = 0.0;
+        for (int s = 0; s < 2; ++s) {
+            double t = 1.0;
+            for (int k = 0; k < 6; ++k) t *= Q[s][idx[k]];
+            v += t;
+        }
+        O64[i] = v;
+    }
+    return SCTM_OK;
+}
+
+sctm_status sctm_create(const double* peps, const double* pepo, int chi, const sctm_opts* o,
+                        sctm_ctx** out) {
+    if (!out) return SCTM_EINVAL;
+    *out = nullptr;
+    if (!peps || !pepo) return SCTM_EINVAL;
+    sctm_opts opts;
+    if (o) opts = *o; else sctm_default_opts(&opts);
+    if (chi < 1 || chi > 4096 || opts.D < 1 || opts.p < 1 || opts.d < 1 || opts.batch != 1 ||
+        opts.precision != SCTM_PREC_FP64 || opts.grad_mode != SCTM_GRAD_ENV ||
+        !(opts.svd_cutoff >= 0.0) || opts.D > 64 || opts.d > 64 || opts.p > 64)
+        return SCTM_EINVAL;
+    std::unique_ptr<sctm_ctx> c(new sctm_ctx());
+    c->opts = opts;
+    c->chi = chi;
+    try {
+        cudaStream_t s = (cudaStream_t)opts.cuda_stream;
+        c->eng.reset(new Engine(s, opts.precision, opts.svd_cutoff));
+        Engine& e = *c->eng;
+        const long long na = peps_size(opts), no = pepo_size(opts);
+        c->A_dev = e.dalloc(na);
+        c->O_dev = e.dalloc(no);
+        c->Oid_dev = e.dalloc((long long)opts.p * opts.p);
+        c->f_dev = e.dalloc(1);
+        c->g_dev = e.dalloc(na);
+        c->flag_dev = (int*)e.dalloc(1);
+        cuda_ok(cudaMemcpy(c->A_dev, peps, na * sizeof(double), cudaMemcpyDefault), "copy peps");
+        c->A_stage = e.dalloc(na);
+        if (!peps_is_finite(c.get(), c->A_dev)) return SCTM_ENUMERIC;
+        cuda_ok(cudaMemcpy(c->O_dev, pepo, no * sizeof(double), cudaMemcpyDefault), "copy pepo");
+        std::vector<double> oid((size_t)opts.p * opts.p, 0.0);
+        for (int i = 0; i < opts.p; ++i) oid[(size_t)i * opts.p + i] = 1.0;
+        cuda_ok(cudaMemcpy(c->Oid_dev, oid.data(), oid.size() * sizeof(double),
+                           cudaMemcpyHostToDevice), "copy identity pepo");
+        for (int n = 0; n < 2; ++n) {
+            Network& net = c->net[n];
+            net.D = opts.D;
+            net.p = opts.p;
+            net.d = n == 0 ? opts.d : 1;
+            net.chi = chi;
+            net.A = view(c->A_dev, {opts.p, opts.D, opts.D, opts.D, opts.D});
+            net.B = net.A;
+            net.O = n == 0 ? view(c->O_dev, {opts.p, opts.p, opts.d, opts.d, opts.d, opts.d})
+                           : view(c->Oid_dev, {opts.p, opts.p, 1, 1, 1, 1});
+            e.build_network(net);
+        }
+        cuda_ok(cudaDeviceSynchronize(), "plan build");
+        for (int n = 0; n < 2; ++n) e.init_env(c->net[n], opts.init_seed);
+        cuda_ok(cudaStreamSynchronize(s), "cold start");
+        check_cuda("create");
+    } catch (const Error& e) {
+        return e.code;
+    } catch (const std::exception&) {
+        return SCTM_ECUDA;
+    }
+    *out = c.release();
+    return SCTM_OK;
+}
+
+sctm_status sctm_set_peps(sctm_ctx* ctx, const double* peps, int reset_env) {
+    API_BEGIN(ctx)
+    if (!peps) throw Error(SCTM_EINVAL, "NULL peps");
+    const long long na = peps_size(ctx->opts);
+    cuda_ok(cudaMemcpyAsync(ctx->A_stage, peps, na * sizeof(double), cudaMemcpyDefault,
+                            ctx->eng->stream),
+            "copy peps");
+    if (!peps_is_finite(ctx, ctx->A_stage)) {
+        ctx->err = "PEPS tensor has a non-finite entry (previous PEPS kept)";
+        return SCTM_ENUMERIC;
+    }
+    launch_copy(ctx->A_stage, ctx->A_dev, na, ctx->eng->stream);
+    if (reset_env)
+        for (int n = 0; n < 2; ++n) ctx->eng->init_env(ctx->net[n], ctx->opts.init_seed);
+    check_cuda("set_peps");
+    return SCTM_OK;
+    API_END(ctx)
+}
+
+sctm_status sctm_iterate(sctm_ctx* ctx, int max_it, double tol, int* it_done, double* last_dS) {
+    API_BEGIN(ctx)
+    if (max_it < 0) throw Error(SCTM_EINVAL, "max_it < 0");
+    Engine& e = *ctx->eng;
+    int it_max = 0;
+    double dS_max = 0.0;
+    bool conv = true;
+    for (int n = 0; n < 2; ++n) {
+        Network& net = ctx->net[n];
+        double dS = INFINITY;
+        int it = 0;
+        for (it = 1; it <= max_it; ++it) {
+            for (int m = 0; m < 4; ++m) e.run(net.move[m]);
+            e.run(net.spectrum);
+            check_cuda("iteration");
+            cuda_ok(cudaMemcpyAsync(&dS, net.dS, sizeof(double), cudaMemcpyDeviceToHost, e.stream),
+                    "dS copy");
+            cuda_ok(cudaStreamSynchronize(e.stream), "iteration sync");
+            if (!std::isfinite(dS)) throw Error(SCTM_ENUMERIC, "non-finite spectrum change");
+            if (tol > 0.0 && dS < tol) break;
+        }
+        if (it > max_it) it = max_it;
+        if (tol > 0.0 && !(dS < tol)) conv = false;
+        it_max = std::max(it_max, it);
+        if (std::isfinite(dS)) dS_max = std::max(dS_max, dS);
+    }
+    check_svd_info(ctx);
+    ctx->converged = conv;
+    if (it_done) *it_done = it_max;
+    if (last_dS) *last_dS = dS_max;
+    if (!conv) {
+        ctx->err = "iteration limit reached before convergence";
+        return SCTM_ENOCONV;
+    }
+    return SCTM_OK;
+    API_END(ctx)
+}
+
+static sctm_status finish_local(sctm_ctx* ctx) {
+    Engine& e = *ctx->eng;
+    for (int n = 0; n < 2; ++n) e.run(ctx->net[n].local);
+    check_cuda("local contractions");
+    return SCTM_OK;
+}
+
+sctm_status sctm_free_energy(sctm_ctx* ctx, double* f) {
+    API_BEGIN(ctx)
+    if (!f) throw Error(SCTM_EINVAL, "NULL f");
+    Engine& e = *ctx->eng;
+    finish_local(ctx);
+    launch_free_energy(ctx->net[0].lnk, ctx->net[1].lnk, ctx->opts.T, ctx->f_dev, e.stream);
+    check_cuda("free energy");
+    cuda_ok(cudaMemcpyAsync(f, ctx->f_dev, sizeof(double), cudaMemcpyDeviceToHost, e.stream),
+            "f copy");
+    cuda_ok(cudaStreamSynchronize(e.stream), "f sync");
+    if (!std::isfinite(*f)) {
+        ctx->err = "kappa <= 0 or not finite";
+        return SCTM_ENUMERIC;
+    }
+    if (!ctx->converged) {
+        ctx->err = "environment not converged";
+        return SCTM_ENOCONV;
+    }
+    return SCTM_OK;
+    API_END(ctx)
+}
+
+sctm_status sctm_grad(sctm_ctx* ctx, double* g) {
+    API_BEGIN(ctx)
+    if (!g) throw Error(SCTM_EINVAL, "NULL g");
+    Engine& e = *ctx->eng;
+    finish_local(ctx);
+    const int n = (int)peps_size(ctx->opts);
+    launch_grad_combine(ctx->net[0].E.p, ctx->net[0].lnk, ctx->net[1].E.p, ctx->net[1].lnk,
+                        ctx->opts.T, n, ctx->g_dev, e.stream);
+    check_cuda("gradient");
+    cuda_ok(cudaMemcpyAsync(g, ctx->g_dev, n * sizeof(double), cudaMemcpyDefault, e.stream),
+            "g copy");
+    cuda_ok(cudaStreamSynchronize(e.stream), "g sync");
+    double lnk[2][2];
+    for (int k = 0; k < 2; ++k)
+        cuda_ok(cudaMemcpy(lnk[k], ctx->net[k].lnk, 2 * sizeof(double), cudaMemcpyDeviceToHost),
+                "lnk copy");
+    if (!std::isfinite(lnk[0][0]) || !std::isfinite(lnk[1][0])) {
+        ctx->err = "kappa <= 0 or not finite";
+        return SCTM_ENUMERIC;
+    }
+    if (!ctx->converged) {
+        ctx->err = "environment not converged";
+        return SCTM_ENOCONV;
+    }
+    return SCTM_OK;
+    API_END(ctx)
+}
+
+sctm_status sctm_destroy(sctm_ctx* ctx) {
+    if (!ctx) return SCTM_OK;
+    if (ctx->eng) cudaStreamSynchronize(ctx->eng->stream);
+    delete ctx;
+    return SCTM_OK;
+}
+
+const char* sctm_last_error(const sctm_ctx* ctx) {
+    if (!ctx) return kNullCtx;
+    return ctx->err.c_str();
+}
+
+size_t sctm_env_size(const sctm_ctx* ctx, int network) {
+    if (!ctx || network < 0 || network > 1) return 0;
+    const Network& n = ctx->net[network];
+    size_t s = 0;
+    for (int i = 0; i < 4; ++i) s += (size_t)n.C[i].numel();
+    for (int i = 0; i < 4; ++i)
+        for (int x = 0; x < 3; ++x) s += (size_t)n.T[i][x].numel();
+    return s;
+}
+
+static sctm_status env_copy(sctm_ctx* ctx, int network, double* host, size_t n, bool to_host) {
+    API_BEGIN(ctx)
+    if (network < 0 || network > 1 || !host || n < sctm_env_size(ctx, network))
+        throw Error(SCTM_EINVAL, "bad network, buffer or size");
+    Network& net = ctx->net[network];
+    std::vector<Ten*> ts;
+    for (int i = 0; i < 4; ++i) ts.push_back(&net.C[i]);
+    for (int i = 0; i < 4; ++i)
+        for (int x = 0; x < 3; ++x) ts.push_back(&net.T[i][x]);
+    size_t off = 0;
+    cuda_ok(cudaStreamSynchronize(ctx->eng->stream), "sync");
+    for (Ten* t : ts) {
+        const size_t bytes = (size_t)t->numel() * sizeof(double);
+        if (to_host)
+            cuda_ok(cudaMemcpy(host + off, t->p, bytes, cudaMemcpyDeviceToHost), "env export");
+        else
+            cuda_ok(cudaMemcpy(t->p, host + off, bytes, cudaMemcpyHostToDevice), "env import");
+        off += (size_t)t->numel();
+    }
+    return SCTM_OK;
+    API_END(ctx)
+}
+
+sctm_status sctm_env_export(sctm_ctx* ctx, int network, double* host_buf, size_t n) {
+    return env_copy(ctx, network, host_buf, n, true);
+}
+
+sctm_status sctm_env_import(sctm_ctx* ctx, int network, const double* host_buf, size_t n) {
+    return env_copy(ctx, network, const_cast<double*>(host_buf), n, false);
+}
+
+sctm_status sctm_move(sctm_ctx* ctx, int network, int direction) {
+    API_BEGIN(ctx)
+    if (network < 0 || network > 1 || direction < 0 || direction > 3)
+        throw Error(SCTM_EINVAL, "bad network or direction");
+    ctx->eng->run(ctx->net[network].move[direction]);
+    check_cuda("move");
+    cuda_ok(cudaStreamSynchronize(ctx->eng->stream), "move sync");
+    return SCTM_OK;
+    API_END(ctx)
+}
+
+sctm_status sctm_spectrum(sctm_ctx* ctx, int network, double* S) {
+    API_BEGIN(ctx)
+    if (network < 0 || network > 1 || !S) throw Error(SCTM_EINVAL, "bad network or buffer");
+    Network& net = ctx->net[network];
+    ctx->eng->run(net.spectrum);
+    check_cuda("spectrum");
+    cuda_ok(cudaMemcpyAsync(S, net.S_old, net.chi * sizeof(double), cudaMemcpyDeviceToHost,
+                            ctx->eng->stream),
+            "spectrum copy");
+    cuda_ok(cudaStreamSynchronize(ctx->eng->stream), "spectrum sync");
+    return SCTM_OK;
+    API_END(ctx)
+}
+
+sctm_status sctm_profile(sctm_ctx* ctx, double* ctr_ms, double* svd_ms, double* total_ms,
+                         long long* ctr_launches, long long* ctr_flops, int reset) {
+    API_BEGIN(ctx)
+    Engine& e = *ctx->eng;
+    if (ctr_ms) *ctr_ms = e.ctr_ms;
+    if (svd_ms) *svd_ms = e.svd_ms;
+    if (total_ms) *total_ms = e.ctr_ms + e.svd_ms;
+    if (ctr_launches) *ctr_launches = e.ctr_launches;
+    if (ctr_flops) *ctr_flops = e.ctr_flops;
+    if (reset) {
+        e.ctr_ms = e.svd_ms = 0;
+        e.ctr_launches = e.ctr_flops = 0;
+    }
+    return SCTM_OK;
+    API_END(ctx)
+}
+
+}  // extern "C"

@@ -1,0 +1,718 @@
+// Plan builder and executor of the split-CTMRG runtime (Sec. III of arXiv:2506.19339).
+//
+// Every directional move, the convergence check and the local contractions are compiled once,
+// at context creation, into a static list of steps whose buffers, gather tables and cuSOLVER
+// workspaces are all allocated up front.  An iteration is then a replay of those steps on one
+// stream: no allocation, no host logic beyond the loop, one device->host scalar per iteration.
+#include "engine.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <map>
+
+namespace sctm {
+
+#define CUDA_OK(x)                                                                        \
+    do {                                                                                  \
+        cudaError_t e_ = (x);                                                             \
+        if (e_ != cudaSuccess)                                                            \
+            throw Error(e_ == cudaErrorMemoryAllocation ? SCTM_ENOMEM : SCTM_ECUDA,       \
+                        std::string(#x) + ": " + cudaGetErrorString(e_));                 \
+    } while (0)
+
+#define SOLVER_OK(x)                                                                      \
+    do {                                                                                  \
+        cusolverStatus_t s_ = (x);                                                        \
+        if (s_ != CUSOLVER_STATUS_SUCCESS)                                                \
+            throw Error(SCTM_ECUSOLVER, std::string(#x) + " failed: " + std::to_string(s_)); \
+    } while (0)
+
+Ten view(double* p, const std::vector<int>& dims) {
+    Ten t;
+    t.p = p;
+    t.nd = (int)dims.size();
+    long long s = 1;
+    for (int i = t.nd - 1; i >= 0; --i) {
+        t.dim[i] = dims[i];
+        t.st[i] = s;
+        s *= dims[i];
+    }
+    return t;
+}
+
+Ten permute(const Ten& t, const std::vector<int>& perm) {
+    Ten o;
+    o.p = t.p;
+    o.nd = t.nd;
+    for (int k = 0; k < t.nd; ++k) {
+        o.dim[k] = t.dim[perm[k]];
+        o.st[k] = t.st[perm[k]];
+    }
+    return o;
+}
+
+// ---------------------------------------------------------------------------------------------
+// steps
+// ---------------------------------------------------------------------------------------------
+struct CtrStep : Step {
+    CtrLaunch a;
+    size_t partial_need = 0;
+    long long flops = 0;
+    void run(Engine& e) override {
+        if (e.profile) cudaEventRecord(e.ev0, e.stream);
+        launch_ctr(a, e.stream);
+        if (e.profile) {
+            cudaEventRecord(e.ev1, e.stream);
+            cudaEventSynchronize(e.ev1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e.ev0, e.ev1);
+            e.ctr_ms += ms;
+            e.ctr_launches += 1;
+            e.ctr_flops += flops;
+        }
+    }
+};
+
+struct SvdStep : Step {
+    double* M = nullptr;
+    int n = 0;
+    double* S = nullptr;
+    double* U = nullptr;
+    double* VT = nullptr;
+    bool vectors = true;
+    Network* net = nullptr;
+    int info_idx = 0;
+    void run(Engine& e) override {
+        if (e.profile) cudaEventRecord(e.ev0, e.stream);
+        signed char jobu = vectors ? 'S' : 'N';
+        cusolverStatus_t st = cusolverDnDgesvd(e.solver, jobu, jobu, n, n, M, n, S, U, n, VT, n,
+                                               net->svd_work, net->svd_lwork, net->svd_rwork,
+                                               net->svd_info + info_idx);
+        if (st != CUSOLVER_STATUS_SUCCESS)
+            throw Error(SCTM_ECUSOLVER, "cusolverDnDgesvd failed: " + std::to_string(st));
+        if (e.profile) {
+            cudaEventRecord(e.ev1, e.stream);
+            cudaEventSynchronize(e.ev1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e.ev0, e.ev1);
+            e.svd_ms += ms;
+        }
+    }
+};
+
+struct FnStep : Step {
+    std::function<void(cudaStream_t)> f;
+    explicit FnStep(std::function<void(cudaStream_t)> g) : f(std::move(g)) {}
+    void run(Engine& e) override { f(e.stream); }
+};
+
+// ---------------------------------------------------------------------------------------------
+// engine
+// ---------------------------------------------------------------------------------------------
+Engine::Engine(cudaStream_t s, int prec, double cut) : stream(s), precision(prec), cutoff(cut) {
+    SOLVER_OK(cusolverDnCreate(&solver));
+    SOLVER_OK(cusolverDnSetStream(solver, stream));
+    const char* pf = getenv("SCTM_PROFILE");
+    profile = pf && pf[0] == '1';
+    if (profile) {
+        CUDA_OK(cudaEventCreate(&ev0));
+        CUDA_OK(cudaEventCreate(&ev1));
+    }
+}
+
+Engine::~Engine() {
+    for (void* p : allocs_) cudaFree(p);
+    if (solver) cusolverDnDestroy(solver);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+}
+
+double* Engine::dalloc(long long n) {
+    void* p = nullptr;
+    CUDA_OK(cudaMalloc(&p, std::max<long long>(n, 1) * sizeof(double)));
+    allocs_.push_back(p);
+    CUDA_OK(cudaMemset(p, 0, std::max<long long>(n, 1) * sizeof(double)));
+    return (double*)p;
+}
+
+int* Engine::ialloc(const std::vector<int>& host) {
+    void* p = nullptr;
+    size_t bytes = std::max<size_t>(host.size(), 1) * sizeof(int);
+    CUDA_OK(cudaMalloc(&p, bytes));
+    allocs_.push_back(p);
+    if (!host.empty())
+        CUDA_OK(cudaMemcpy(p, host.data(), host.size() * sizeof(int), cudaMemcpyHostToDevice));
+    return (int*)p;
+}
+
+void Engine::run(Plan& P) {
+    for (auto& s : P) s->run(*this);
+}
+
+// offsets of a multi-index group (row-major over `labs`) in a tensor with per-label strides
+static std::vector<int> offsets(const std::string& labs, const std::map<char, int>& dims,
+                                const std::map<char, long long>& strides) {
+    long long n = 1;
+    for (char c : labs) n *= dims.at(c);
+    std::vector<int> out((size_t)n);
+    std::vector<int> idx(labs.size(), 0);
+    for (long long t = 0; t < n; ++t) {
+        long long off = 0;
+        for (size_t i = 0; i < labs.size(); ++i) {
+            auto it = strides.find(labs[i]);
+            if (it != strides.end()) off += idx[i] * it->second;
+        }
+        if (off > 0x7fffffffLL) throw Error(SCTM_EINVAL, "tensor too large for 32-bit offsets");
+        out[(size_t)t] = (int)off;
+        for (int i = (int)labs.size() - 1; i >= 0; --i) {
+            if (++idx[i] < dims.at(labs[i])) break;
+            idx[i] = 0;
+        }
+    }
+    return out;
+}
+
+Ten Engine::ctr(Network& net, Plan& P, const std::string& spec, const Ten& X, const Ten& Y,
+                const Ten* out, const double* rowscale, const double* colscale) {
+    const size_t comma = spec.find(','), arrow = spec.find("->");
+    if (comma == std::string::npos || arrow == std::string::npos)
+        throw Error(SCTM_EINVAL, "bad contraction spec " + spec);
+    const std::string xl = spec.substr(0, comma), yl = spec.substr(comma + 1, arrow - comma - 1),
+                      ol = spec.substr(arrow + 2);
+    if ((int)xl.size() != X.nd || (int)yl.size() != Y.nd)
+        throw Error(SCTM_EINVAL, "rank mismatch in " + spec);
+    std::map<char, int> dims;
+    std::map<char, long long> sx, sy, so;
+    auto add = [&](const std::string& l, const Ten& t, std::map<char, long long>& s) {
+        for (size_t i = 0; i < l.size(); ++i) {
+            auto it = dims.find(l[i]);
+            if (it != dims.end() && it->second != t.dim[i])
+                throw Error(SCTM_EINVAL, std::string("dimension mismatch for label ") + l[i] +
+                                             " in " + spec);
+            dims[l[i]] = t.dim[i];
+            if (s.count(l[i])) throw Error(SCTM_EINVAL, "repeated label in " + spec);
+            s[l[i]] = t.st[i];
+        }
+    };
+    add(xl, X, sx);
+    add(yl, Y, sy);
+    std::string bl, ml, nl, kl;
+    for (char c : ol) {
+        if (!dims.count(c)) throw Error(SCTM_EINVAL, "unknown output label in " + spec);
+        const bool inx = sx.count(c), iny = sy.count(c);
+        if (inx && iny) bl += c;
+        else if (inx) ml += c;
+        else nl += c;
+    }
+    for (char c : xl) {
+        if (sy.count(c) && ol.find(c) == std::string::npos) kl += c;
+        if (!sy.count(c) && ol.find(c) == std::string::npos)
+            throw Error(SCTM_EINVAL, "label only in the first operand and not kept: " + spec);
+    }
+    for (char c : yl)
+        if (!sx.count(c) && ol.find(c) == std::string::npos)
+            throw Error(SCTM_EINVAL, "label only in the second operand and not kept: " + spec);
+
+    Ten O;
+    if (out) {
+        O = *out;
+        if ((int)ol.size() != O.nd) throw Error(SCTM_EINVAL, "output rank mismatch in " + spec);
+        for (size_t i = 0; i < ol.size(); ++i)
+            if (O.dim[i] != dims[ol[i]]) throw Error(SCTM_EINVAL, "output dims mismatch " + spec);
+    } else {
+        std::vector<int> od;
+        for (char c : ol) od.push_back(dims[c]);
+        O = alloc(od);
+    }
+    for (size_t i = 0; i < ol.size(); ++i) so[ol[i]] = O.st[i];
+
+    auto st = std::make_unique<CtrStep>();
+    CtrLaunch& a = st->a;
+    a.X = X.p;
+    a.Y = Y.p;
+    a.O = O.p;
+    std::vector<int> txm = offsets(ml, dims, sx), txk = offsets(kl, dims, sx),
+                     tyk = offsets(kl, dims, sy), tyn = offsets(nl, dims, sy),
+                     tom = offsets(ml, dims, so), ton = offsets(nl, dims, so);
+    a.M = (int)txm.size();
+    a.N = (int)tyn.size();
+    a.K = (int)txk.size();
+    a.xm = ialloc(txm);
+    a.xk = ialloc(txk);
+    a.yk = ialloc(tyk);
+    a.yn = ialloc(tyn);
+    a.om = ialloc(tom);
+    a.on = ialloc(ton);
+    if (!bl.empty()) {
+        std::vector<int> txb = offsets(bl, dims, sx), tyb = offsets(bl, dims, sy),
+                         tob = offsets(bl, dims, so);
+        a.nb = (int)txb.size();
+        a.xb = ialloc(txb);
+        a.yb = ialloc(tyb);
+        a.ob = ialloc(tob);
+    }
+    a.rowscale = rowscale;
+    a.colscale = colscale;
+    a.precision = precision;
+    // split K when the output tile grid cannot fill the GPU
+    const long long tiles = (long long)((a.M + 63) / 64) * ((a.N + 63) / 64) * a.nb;
+    a.splits = 1;
+    a.kchunk = std::max(a.K, 1);
+    if (tiles < 152 && a.K > 256) {
+        int want = (int)std::min<long long>(std::max<long long>(304 / tiles, 1), (a.K + 127) / 128);
+        want = std::max(1, std::min(want, 128));
+        int kchunk = (a.K + want - 1) / want;
+        kchunk = ((kchunk + 15) / 16) * 16;
+        a.kchunk = kchunk;
+        a.splits = (a.K + kchunk - 1) / kchunk;
+        if (a.splits > 1)
+            st->partial_need = (size_t)a.nb * a.splits * (size_t)a.M * a.N;
+        else
+            a.kchunk = std::max(a.K, 1);
+    }
+    st->flops = 2LL * a.M * a.N * (long long)a.K * a.nb;
+    net.ctr_steps.push_back(st.get());
+    net.splitk_need = std::max(net.splitk_need, st->partial_need);
+    P.push_back(std::move(st));
+    return O;
+}
+
+Engine::PPair Engine::projector(Network& net, Plan& P, const Ten& U, const Ten& L,
+                                const std::string& labels, const std::string& tl) {
+    static const std::string pool = "0123456789@$%&*+=?^~|";
+    const char K = '#';
+    std::string rl, rlL, Llab = labels;
+    int n = 1;
+    std::vector<int> rdims;
+    size_t next = 0;
+    for (size_t i = 0; i < labels.size(); ++i) {
+        if (tl.find(labels[i]) != std::string::npos) continue;
+        rl += labels[i];
+        rlL += pool[next];
+        Llab[i] = pool[next];
+        ++next;
+        rdims.push_back(U.dim[i]);
+        n *= U.dim[i];
+    }
+    const int chi = net.chi;
+    if (n < chi) throw Error(SCTM_EINVAL, "projector: remaining dimension smaller than chi");
+    // M[r', r] = sum_t L[t, r'] U[t, r], column-major (row r' from L, column r from U)
+    Ten M;
+    M.p = dalloc((long long)n * n);
+    M.nd = (int)(2 * rl.size());
+    {
+        long long s = 1;
+        for (int i = (int)rl.size() - 1; i >= 0; --i) {
+            M.dim[i] = rdims[i];
+            M.st[i] = s;
+            s *= rdims[i];
+        }
+        s = n;
+        for (int i = (int)rl.size() - 1; i >= 0; --i) {
+            M.dim[rl.size() + i] = rdims[i];
+            M.st[rl.size() + i] = s;
+            s *= rdims[i];
+        }
+    }
+    ctr(net, P, Llab + "," + labels + "->" + rlL + rl, L, U, &M);
+    double* S = dalloc(n);
+    double* Us = dalloc((long long)n * n);
+    double* VT = dalloc((long long)n * n);
+    auto sv = std::make_unique<SvdStep>();
+    sv->M = M.p;
+    sv->n = n;
+    sv->S = S;
+    sv->U = Us;
+    sv->VT = VT;
+    sv->vectors = true;
+    sv->net = &net;
+    sv->info_idx = net.n_svd++;
+    net.svd_nmax = std::max(net.svd_nmax, n);
+    net.svd_steps.push_back(sv.get());
+    P.push_back(std::move(sv));
+    P.push_back(std::make_unique<FnStep>([=](cudaStream_t s) { launch_signfix(Us, VT, n, chi, s); }));
+    double* scale = dalloc(chi);
+    const double cut = cutoff;
+    P.push_back(std::make_unique<FnStep>(
+        [=](cudaStream_t s) { launch_scalevec(S, chi, cut, scale, s); }));
+    // V[r, c] = VT[c + r n]; Us[r', c] = Us[r' + c n]
+    Ten V, Uv;
+    V.p = VT;
+    Uv.p = Us;
+    V.nd = Uv.nd = (int)rl.size() + 1;
+    {
+        long long s = 1;
+        for (int i = (int)rl.size() - 1; i >= 0; --i) {
+            V.dim[i] = Uv.dim[i] = rdims[i];
+            V.st[i] = s * n;
+            Uv.st[i] = s;
+            s *= rdims[i];
+        }
+        V.dim[rl.size()] = Uv.dim[rl.size()] = chi;
+        V.st[rl.size()] = 1;
+        Uv.st[rl.size()] = n;
+    }
+    PPair pp;
+    pp.PB = ctr(net, P, labels + "," + rl + K + "->" + tl + K, U, V, nullptr, nullptr, scale);
+    pp.PT = ctr(net, P, rlL + K + "," + Llab + "->" + K + tl, Uv, L, nullptr, scale, nullptr);
+    return pp;
+}
+
+// ---------------------------------------------------------------------------------------------
+// frames: the right / up / down moves are the left move in a relabelled network
+// (diagonal reflection; 180-degree rotation with ket <-> bra; both)
+// ---------------------------------------------------------------------------------------------
+struct Frame {
+    Ten C[4];
+    Ten T[4][3];
+    Ten A, O, B;
+};
+
+static Frame make_frame(const Network& n, int move) {
+    Frame f;
+    auto tr = [](const Ten& t) { return permute(t, {1, 0}); };
+    auto sw = [](const Ten& t) { return permute(t, {1, 0, 2}); };
+    if (move == SCTM_MOVE_LEFT) {
+        for (int i = 0; i < 4; ++i) {
+            f.C[i] = n.C[i];
+            for (int x = 0; x < 3; ++x) f.T[i][x] = n.T[i][x];
+        }
+        f.A = n.A;
+        f.O = n.O;
+        f.B = n.B;
+    } else if (move == SCTM_MOVE_UP) {
+        f.C[0] = tr(n.C[0]);
+        f.C[1] = tr(n.C[3]);
+        f.C[2] = tr(n.C[2]);
+        f.C[3] = tr(n.C[1]);
+        const int tmap[4] = {3, 2, 1, 0};
+        for (int i = 0; i < 4; ++i)
+            for (int x = 0; x < 3; ++x) f.T[i][x] = n.T[tmap[i]][x];
+        f.A = permute(n.A, {0, 2, 1, 4, 3});
+        f.B = permute(n.B, {0, 2, 1, 4, 3});
+        f.O = permute(n.O, {0, 1, 3, 2, 5, 4});
+    } else if (move == SCTM_MOVE_RIGHT) {
+        f.C[0] = n.C[2];
+        f.C[1] = n.C[3];
+        f.C[2] = n.C[0];
+        f.C[3] = n.C[1];
+        const int tmap[4] = {2, 3, 0, 1};
+        for (int i = 0; i < 4; ++i)
+            for (int x = 0; x < 3; ++x) f.T[i][x] = sw(n.T[tmap[i]][2 - x]);
+        f.A = permute(n.B, {0, 3, 4, 1, 2});
+        f.B = permute(n.A, {0, 3, 4, 1, 2});
+        f.O = permute(n.O, {1, 0, 4, 5, 2, 3});
+    } else {  // down = diagonal reflection of the rotated frame
+        f.C[0] = tr(n.C[2]);
+        f.C[1] = tr(n.C[1]);
+        f.C[2] = tr(n.C[0]);
+        f.C[3] = tr(n.C[3]);
+        const int tmap[4] = {1, 0, 3, 2};
+        for (int i = 0; i < 4; ++i)
+            for (int x = 0; x < 3; ++x) f.T[i][x] = sw(n.T[tmap[i]][2 - x]);
+        f.A = permute(n.B, {0, 4, 3, 2, 1});
+        f.B = permute(n.A, {0, 4, 3, 2, 1});
+        f.O = permute(n.O, {1, 0, 5, 4, 3, 2});
+    }
+    return f;
+}
+
+// ---------------------------------------------------------------------------------------------
+// the left move (Sec. III.B, Fig. 5; Sec. III.C and Appendix for the projectors)
+// ---------------------------------------------------------------------------------------------
+static void build_left_move(Engine& e, Network& net, Plan& P, const Frame& f) {
+    auto C = [&](const char* spec, const Ten& X, const Ten& Y) { return e.ctr(net, P, spec, X, Y); };
+    const Ten &C1 = f.C[0], &C2 = f.C[1], &C3 = f.C[2], &C4 = f.C[3];
+    const Ten &T1k = f.T[0][0], &T1i = f.T[0][1], &T1b = f.T[0][2];
+    const Ten &T2k = f.T[1][0], &T2i = f.T[1][1], &T2b = f.T[1][2];
+    const Ten &T3k = f.T[2][0], &T3i = f.T[2][1], &T3b = f.T[2][2];
+    const Ten &T4k = f.T[3][0], &T4i = f.T[3][1], &T4b = f.T[3][2];
+    const Ten &A = f.A, &O = f.O, &B = f.B;
+    Ten X;
+
+    // insertion + absorption of one column into the corners (Fig. 5(a),(b))
+    X = C("av,acp->vcp", C1, T1k);
+    X = C("vcp,ceo->vepo", X, T1i);
+    const Ten Ct1 = C("vepo,ehb->hvpob", X, T1b);            // [h, v, ua, uo, ub]
+    X = C("egb,gw->ewb", T1b, C2);
+    X = C("ceo,ewb->cwob", T1i, X);
+    const Ten Ct2 = C("hcp,cwob->hwpob", T1k, X);            // [h, w, ua, uo, ub]
+    X = C("av,acE->vcE", C4, T3k);
+    X = C("vcE,cef->veEf", X, T3i);
+    const Ten Ct4 = C("veEf,ehg->hvEfg", X, T3b);            // [h, v, da, do, db]
+    X = C("egG,gw->ewG", T3b, C3);
+    X = C("cef,ewG->cwfG", T3i, X);
+    const Ten Ct3 = C("hcE,cwfG->hwEfG", T3k, X);            // [h, w, da, do, db]
+
+    // one-column patches: upper / lower halves at the kappa, iota, alpha cuts
+    const Ten Ctop = C("hvpob,hw->vpobw", Ct1, C2);          // [v1, ua, uo, ub, v2]
+    const Ten Cbot = C("hvEfg,hw->vEfgw", Ct4, C3);          // [v4, da, do, db, v3]
+    X = C("vaobw,vxl->xaoblw", Ctop, T4k);
+    X = C("xaoblw,saler->xobwser", X, A);
+    const Ten Uk = C("xobwser,wyr->xesoby", X, T2k);         // (xl, A.d, s, O.u, B.u, xr)
+    X = C("xesoby,xXl->Xesobyl", Uk, T4i);
+    X = C("Xesobyl,tsolfr->Xebyftr", X, O);
+    const Ten Ui = C("Xebyftr,yYr->XeftbY", X, T2i);         // (xl, A.d, O.d, s', B.u, xr)
+    X = C("xeftby,xXl->Xeftbyl", Ui, T4b);
+    X = C("Xeftbyl,tblgr->Xefygr", X, B);
+    const Ten Ua = C("Xefygr,yYr->XefgY", X, T2b);           // (xl, A_v, O_v, B_v, xr)
+    X = C("vefgw,xvl->xefgwl", Cbot, T4b);
+    X = C("xefgwl,tblgr->xefwtbr", X, B);
+    const Ten Li = C("xefwtbr,ywr->xeftby", X, T2b);
+    X = C("XeftbY,xXl->xeftbYl", Li, T4i);
+    X = C("xeftbYl,tsolfr->xebYsor", X, O);
+    const Ten Lk = C("xebYsor,yYr->xesoby", X, T2i);
+    X = C("XesobY,xXl->xesobYl", Lk, T4k);
+    X = C("xesobYl,saler->xobYar", X, A);
+    const Ten La = C("xobYar,yYr->xaoby", X, T2k);
+
+    // stage 1: bra-related legs of this column (P1, P2, P3) and the mirror-image pairs of the
+    // opposite boundary on the ket-related legs of the next column
+    const Engine::PPair Pa = e.projector(net, P, Ua, La, "xAOBy", "xB");     // [xl, B_v | k]
+    const Engine::PPair Qa = e.projector(net, P, Ua, La, "xAOBy", "yA");     // [xr, A_v | k]
+    const Engine::PPair Pk = e.projector(net, P, Uk, Lk, "xesoby", "xsb");   // [xl, s, B.u | k]
+    const Engine::PPair Qk = e.projector(net, P, Uk, Lk, "xesoby", "yes");   // [xr, A.d, s | k]
+    const Engine::PPair Pi = e.projector(net, P, Ui, Li, "xeftby", "xtb");   // [xl, s', B.u | k]
+    const Engine::PPair Qi = e.projector(net, P, Ui, Li, "xeftby", "yet");   // [xr, A.d, s' | k]
+
+    // stage 2: two-column patches
+    // kappa (1 x 2 cells): (k2, A.d, O.u | O.u', B.u', kR)
+    const Ten ULA = C("hpobxl,splEr->hobxsEr", C("hvpob,vxl->hpobxl", Ct1, T4k), A);
+    const Ten ULk = C("hobxsEr,kxsb->hkEor", ULA, Pk.PT);
+    X = C("hwpob,wyr->hpobyr", Ct2, T2k);
+    const Ten URA = C("hpobyr,splEr->hobysEl", X, A);        // shared by kappa and iota
+    const Ten URk = C("hobysEl,kyEs->hlobk", URA, Qk.PT);
+    const Ten U2k = C("hkEor,hrOBK->kEoOBK", ULk, URk);
+    X = C("hvEfg,Xvm->hEfgXm", Ct4, T4b);
+    X = C("hEfgXm,tbmgQ->hEfXtbQ", X, B);
+    X = C("hEfXtbQ,xXl->hEftbQxl", X, T4i);
+    X = C("hEftbQxl,tsolfR->hEbQxsoR", X, O);
+    const Ten LLk = C("hEbQxsoR,xsbk->hkEoRQ", X, Pk.PB);
+    X = C("hwEfG,Ywm->hEfGYm", Ct3, T2b);
+    X = C("hEfGYm,tbMGm->hEfYtbM", X, B);
+    X = C("hEfYtbM,yYl->hEftbMyl", X, T2i);
+    X = C("hEftbMyl,tsoLfl->hEbMysoL", X, O);
+    const Ten LRk = C("hEbMysoL,yEsk->hLMobk", X, Qk.PB);
+    const Ten L2k = C("hkEoRQ,hRQOBK->kEoOBK", LLk, LRk);
+
+    // iota (1 x 2 cells): (k3, A.d, O.d | O.d', B.u', kR)
+    const Ten ULAO = C("hobsErXL,tsoLfR->hbErXtfR", C("hobxsEr,xXL->hobsErXL", ULA, T4i), O);
+    const Ten ULi = C("hbErXtfR,kXtb->hkEfrR", ULAO, Pi.PT);
+    const Ten URAO = C("hobsElYR,tsoLfR->hbElYtfL", C("hobysEl,yYR->hobsElYR", URA, T2i), O);
+    const Ten URi = C("hbElYtfL,kYEt->hlLfbk", URAO, Qi.PT);
+    const Ten U2i = C("hkEfrR,hrRFBK->kEfFBK", ULi, URi);
+    X = C("hvEfg,xvm->hEfgxm", Ct4, T4b);
+    X = C("hEfgxm,tbmgQ->hEfxtbQ", X, B);
+    const Ten LLi = C("hEfxtbQ,xtbk->hkEfQ", X, Pi.PB);
+    X = C("hwEfG,ywm->hEfGym", Ct3, T2b);
+    X = C("hEfGym,tbMGm->hEfytbM", X, B);
+    const Ten LRi = C("hEfytbM,yEtk->hMfbk", X, Qi.PB);
+    const Ten L2i = C("hkEfQ,hQFBK->kEfFBK", LLi, LRi);
+
+    // alpha (2 x 2 cells): (k1, A_v, O_v | O_v', B_v', kR)
+    X = C("hbErXtfR,XZM->hbErtfRZM", ULAO, T4b);
+    X = C("hbErtfRZM,tbMgS->hErfRZgS", X, B);
+    const Ten Q1 = C("hErfRZgS,kZg->hkEfrRS", X, Pa.PT);
+    X = C("hbElYtfL,YWS->hbElWtfLS", URAO, T2b);
+    X = C("hbElWtfLS,tbMgS->hElWfLMg", X, B);
+    const Ten Q2 = C("hElWfLMg,kWE->hlLMfgk", X, Qa.PT);
+    const Ten U2a = C("hkEfrRS,hrRSFGK->kEfFGK", Q1, Q2);
+    X = C("hvEfg,YvM->hEfgYM", Ct4, T4b);
+    X = C("hEfgYM,tbMgS->hEfYtbS", X, B);
+    X = C("hEfYtbS,XYL->hEftbSXL", X, T4i);
+    X = C("hEftbSXL,tsoLfR->hEbSXsoR", X, O);
+    X = C("hEbSXsoR,xXl->hEbSsoRxl", X, T4k);
+    X = C("hEbSsoRxl,splEr->hbSoRxpr", X, A);
+    const Ten Q4 = C("hbSoRxpr,xbk->hkporRS", X, Pa.PB);
+    X = C("hwEfg,WwS->hEfgWS", Ct3, T2b);
+    X = C("hEfgWS,tbMgS->hEfWtbM", X, B);
+    X = C("hEfWtbM,ZWR->hEftbMZR", X, T2i);
+    X = C("hEftbMZR,tsoLfR->hEbMZsoL", X, O);
+    X = C("hEbMZsoL,yZr->hEbMsoLyr", X, T2k);
+    X = C("hEbMsoLyr,splEr->hbMoLypl", X, A);
+    const Ten Q3 = C("hbMoLypl,ypk->hlLMobk", X, Qa.PB);
+    const Ten L2a = C("hkporRS,hrRSOBK->kpoOBK", Q4, Q3);
+
+    const Engine::PPair P4 = e.projector(net, P, U2a, L2a, "abcdef", "abc");
+    const Engine::PPair P5 = e.projector(net, P, U2k, L2k, "abcdef", "abc");
+    const Engine::PPair P6 = e.projector(net, P, U2i, L2i, "abcdef", "abc");
+
+    // composite projector of each cut (stage 1 then stage 2)
+    const Ten PaB = C("xbK,Kaok->xaobk", Pa.PB, P4.PB);      // [xl, A_v, O_v, B_v, k]
+    const Ten PaT = C("kKao,Kxb->kxaob", P4.PT, Pa.PT);
+    const Ten PkB = C("xsbK,Keok->xesobk", Pk.PB, P5.PB);    // [xl, A.d, s, O.u, B.u, k]
+    const Ten PkT = C("kKeo,Kxsb->kxesob", P5.PT, Pk.PT);
+    const Ten PiB = C("xtbK,Kefk->xeftbk", Pi.PB, P6.PB);    // [xl, A.d, O.d, s', B.u, k]
+    const Ten PiT = C("kKef,Kxtb->kxeftb", P6.PT, Pi.PT);
+
+    // renormalisation (Fig. 5(c)); crossing lines are summed between the two projectors
+    const Ten C1n = C("hvpob,kvpob->hk", Ct1, PaT);
+    const Ten C4n = C("hvEfg,vEfgk->hk", Ct4, PaB);
+    X = C("xpobK,xXl->pobKXl", PaB, T4k);
+    X = C("pobKXl,splEr->obKXsEr", X, A);
+    const Ten T4kn = C("obKXsEr,kXEsob->Kkr", X, PkT);
+    X = C("xEsobK,xXL->EsobKXL", PkB, T4i);
+    X = C("EsobKXL,tsoLfR->EbKXtfR", X, O);
+    const Ten T4in = C("EbKXtfR,kXEftb->KkR", X, PiT);
+    X = C("xEftbK,xXM->EftbKXM", PiB, T4b);
+    X = C("EftbKXM,tbMgS->EfKXgS", X, B);
+    const Ten T4bn = C("EfKXgS,kXEfg->KkS", X, PaT);
+
+    // Frobenius normalisation, written back through the frame's views of C1, T4, C4
+    std::vector<NormItem> items;
+    auto item = [](const Ten& src, const Ten& dst) {
+        NormItem it;
+        it.src = src.p;
+        it.dst = dst.p;
+        it.d0 = src.dim[0];
+        it.d1 = src.nd > 1 ? src.dim[1] : 1;
+        it.d2 = src.nd > 2 ? src.dim[2] : 1;
+        it.s0 = dst.st[0];
+        it.s1 = dst.nd > 1 ? dst.st[1] : 0;
+        it.s2 = dst.nd > 2 ? dst.st[2] : 0;
+        return it;
+    };
+    items.push_back(item(C1n, f.C[0]));
+    items.push_back(item(T4kn, f.T[3][0]));
+    items.push_back(item(T4in, f.T[3][1]));
+    items.push_back(item(T4bn, f.T[3][2]));
+    items.push_back(item(C4n, f.C[3]));
+    NormItem* dev = (NormItem*)e.dalloc((long long)(items.size() * sizeof(NormItem) + 7) / 8);
+    CUDA_OK(cudaMemcpy(dev, items.data(), items.size() * sizeof(NormItem), cudaMemcpyHostToDevice));
+    const int cnt = (int)items.size();
+    P.push_back(std::make_unique<FnStep>([=](cudaStream_t s) { launch_normalize(dev, cnt, s); }));
+}
+
+// convergence check (Sec. III.D): singular values of rho_eff = C1 C2 C3 C4 / Tr
+static void build_spectrum(Engine& e, Network& net) {
+    Plan& P = net.spectrum;
+    const int chi = net.chi;
+    const Ten R1 = e.ctr(net, P, "ab,ac->bc", net.C[0], net.C[1]);
+    const Ten R2 = e.ctr(net, P, "bc,dc->bd", R1, net.C[2]);
+    const Ten rho = e.ctr(net, P, "bd,de->be", R2, net.C[3]);
+    double* work = e.dalloc((long long)chi * chi);
+    double* Sraw = e.dalloc(chi);
+    double* rho_p = rho.p;
+    P.push_back(std::make_unique<FnStep>(
+        [=](cudaStream_t s) { launch_copy(rho_p, work, (long long)chi * chi, s); }));
+    auto sv = std::make_unique<SvdStep>();
+    sv->M = work;
+    sv->n = chi;
+    sv->S = Sraw;
+    sv->U = work;
+    sv->VT = work;
+    sv->vectors = false;
+    sv->net = &net;
+    sv->info_idx = net.n_svd++;
+    net.svd_nmax = std::max(net.svd_nmax, chi);
+    net.svd_steps.push_back(sv.get());
+    P.push_back(std::move(sv));
+    double* S_old = net.S_old;
+    double* dS = net.dS;
+    P.push_back(std::make_unique<FnStep>(
+        [=](cudaStream_t s) { launch_spectrum_update(Sraw, rho_p, chi, S_old, dS, s); }));
+}
+
+// Z00, Z10, Z01, Z11, ln kappa and the bra environment E (Sec. II, Fig. 4(b),(c))
+static void build_local(Engine& e, Network& net) {
+    Plan& P = net.local;
+    auto C = [&](const char* spec, const Ten& X, const Ten& Y, const Ten* out = nullptr) {
+        return e.ctr(net, P, spec, X, Y, out);
+    };
+    const Ten &C1 = net.C[0], &C2 = net.C[1], &C3 = net.C[2], &C4 = net.C[3];
+    const Ten &T1k = net.T[0][0], &T1i = net.T[0][1], &T1b = net.T[0][2];
+    const Ten &T2k = net.T[1][0], &T2i = net.T[1][1], &T2b = net.T[1][2];
+    const Ten &T3k = net.T[2][0], &T3i = net.T[2][1], &T3b = net.T[2][2];
+    const Ten &T4k = net.T[3][0], &T4i = net.T[3][1], &T4b = net.T[3][2];
+    Ten X;
+    X = C("av,abx->vbx", C1, T1k);
+    X = C("vbx,bcy->vcxy", X, T1i);
+    X = C("vcxy,cez->vexyz", X, T1b);
+    const Ten Ctop = C("vexyz,ew->vxyzw", X, C2);
+    X = C("av,abx->vbx", C4, T3k);
+    X = C("vbx,bcy->vcxy", X, T3i);
+    X = C("vcxy,cez->vexyz", X, T3b);
+    const Ten Cbot = C("vexyz,ew->vxyzw", X, C3);
+    const Ten Z10 = C("vxyzw,vxyzw->", Ctop, Cbot);
+    const Ten X1 = C("hv,hw->vw", C1, C2);
+    const Ten X2 = C("hv,hw->vw", C4, C3);
+    const Ten Z00 = C("vw,vw->", X1, X2);
+    X = C("hv,vbx->hbx", C1, T4k);
+    X = C("hbx,bcy->hcxy", X, T4i);
+    X = C("hcxy,cez->hexyz", X, T4b);
+    const Ten Lrow = C("hexyz,ge->hxyzg", X, C4);
+    X = C("hv,vbx->hbx", C2, T2k);
+    X = C("hbx,bcy->hcxy", X, T2i);
+    X = C("hcxy,cez->hexyz", X, T2b);
+    const Ten Rrow = C("hexyz,ge->hxyzg", X, C3);
+    const Ten Z01 = C("hxyzg,hxyzg->", Lrow, Rrow);
+    X = C("vaobw,vxl->xaoblw", Ctop, T4k);
+    X = C("xaoblw,saler->xobwser", X, net.A);
+    const Ten Uk = C("xobwser,wyr->xesoby", X, T2k);
+    X = C("xesoby,xXl->Xesobyl", Uk, T4i);
+    X = C("Xesobyl,tsolfr->Xebyftr", X, net.O);
+    const Ten Ui = C("Xebyftr,yYr->XeftbY", X, T2i);
+    X = C("vefgw,xvl->xefgwl", Cbot, T4b);
+    X = C("xefgwl,tblgr->xefwtbr", X, net.B);
+    const Ten Li = C("xefwtbr,ywr->xeftby", X, T2b);
+    X = C("XeftbY,xXl->xeftbYl", Li, T4i);
+    X = C("xeftbYl,tsolfr->xebYsor", X, net.O);
+    const Ten Lk = C("xebYsor,yYr->xesoby", X, T2i);
+    const Ten Z11 = C("xesoby,xesoby->", Uk, Lk);
+    X = C("xeftby,xvl->eftbylv", Ui, T4b);
+    X = C("eftbylv,vefgw->tbylgw", X, Cbot);
+    C("tbylgw,ywr->tblgr", X, T2b, &net.E);
+    double *z00 = Z00.p, *z10 = Z10.p, *z01 = Z01.p, *z11 = Z11.p, *lnk = net.lnk;
+    P.push_back(std::make_unique<FnStep>(
+        [=](cudaStream_t s) { launch_lnkappa(z00, z10, z01, z11, lnk, s); }));
+}
+
+void Engine::init_env(Network& net, unsigned long long seed) {
+    unsigned long long q = 0;
+    for (int i = 0; i < 4; ++i) launch_splitmix_fill(net.C[i].p, net.C[i].numel(), seed, q++, stream);
+    for (int i = 0; i < 4; ++i)
+        for (int x = 0; x < 3; ++x)
+            launch_splitmix_fill(net.T[i][x].p, net.T[i][x].numel(), seed, q++, stream);
+    launch_zero(net.S_old, net.chi, stream);
+    CUDA_OK(cudaGetLastError());
+}
+
+void Engine::build_network(Network& net) {
+    const int chi = net.chi, D = net.D, d = net.d;
+    for (int i = 0; i < 4; ++i) net.C[i] = alloc({chi, chi});
+    for (int i = 0; i < 4; ++i) {
+        net.T[i][0] = alloc({chi, chi, D});
+        net.T[i][1] = alloc({chi, chi, d});
+        net.T[i][2] = alloc({chi, chi, D});
+    }
+    net.S_old = dalloc(chi);
+    net.dS = dalloc(1);
+    net.lnk = dalloc(2);
+    net.E = alloc({net.p, D, D, D, D});
+    for (int m = 0; m < 4; ++m) build_left_move(*this, net, net.move[m], make_frame(net, m));
+    build_spectrum(*this, net);
+    build_local(*this, net);
+    finalize(net);
+}
+
+void Engine::finalize(Network& net) {
+    if (net.splitk_need > 0) {
+        net.splitk_ws = dalloc((long long)net.splitk_need);
+        for (CtrStep* s : net.ctr_steps)
+            if (s->a.splits > 1) s->a.partial = net.splitk_ws;
+    }
+    int lwork = 0;
+    SOLVER_OK(cusolverDnDgesvd_bufferSize(solver, net.svd_nmax, net.svd_nmax, &lwork));
+    net.svd_lwork = std::max(lwork, 1);
+    net.svd_work = dalloc(net.svd_lwork);
+    net.svd_rwork = dalloc(net.svd_nmax);
+    void* p = nullptr;
+    CUDA_OK(cudaMalloc(&p, std::max(net.n_svd, 1) * sizeof(int)));
+    allocs_.push_back(p);
+    CUDA_OK(cudaMemset(p, 0, std::max(net.n_svd, 1) * sizeof(int)));
+    net.svd_info = (int*)p;
+}
+
+}  // namespace sctm

@@ -1,0 +1,118 @@
+// Plan builder and executor of the split-CTMRG runtime.
+#pragma once
+
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "sctm_internal.h"
+
+namespace sctm {
+
+struct Error : std::runtime_error {
+    sctm_status code;
+    Error(sctm_status c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+// A strided view of FP64 device memory.
+struct Ten {
+    double* p = nullptr;
+    int nd = 0;
+    int dim[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    long long st[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    long long numel() const {
+        long long n = 1;
+        for (int i = 0; i < nd; ++i) n *= dim[i];
+        return n;
+    }
+};
+
+Ten view(double* p, const std::vector<int>& dims);                 // contiguous row-major
+Ten permute(const Ten& t, const std::vector<int>& perm);           // out axis k = t axis perm[k]
+
+class Engine;
+
+struct Step {
+    virtual ~Step() = default;
+    virtual void run(Engine& e) = 0;
+};
+using Plan = std::vector<std::unique_ptr<Step>>;
+
+// One network (numerator with the PEPO O, or the norm with the identity PEPO).
+struct Network {
+    int D = 0, p = 0, d = 0, chi = 0;
+    Ten C[4];      // stored corners C1..C4 [h, v]
+    Ten T[4][3];   // stored edges T1..T4 x (ket, int, bra) [a, b, m]
+    Ten A, O, B;   // site tensors (B aliases A)
+    Plan move[4];  // SCTM_MOVE_LEFT, RIGHT, UP, DOWN
+    Plan spectrum; // rho_eff singular values and ||dS||
+    Plan local;    // Z00, Z10, Z01, Z11, ln kappa, bra environment E
+    double* S_old = nullptr;
+    double* dS = nullptr;     // device scalar
+    double* lnk = nullptr;    // device [ln kappa, Z11]
+    Ten E;                    // bra environment, layout of A
+    int* svd_info = nullptr;  // one int per SVD step
+    int n_svd = 0;
+    // per-network work buffers, sized after the plans are built
+    double* splitk_ws = nullptr;
+    size_t splitk_need = 0;
+    double* svd_work = nullptr;
+    int svd_lwork = 0;
+    double* svd_rwork = nullptr;
+    int svd_nmax = 1;
+    std::vector<struct CtrStep*> ctr_steps;
+    std::vector<struct SvdStep*> svd_steps;
+};
+
+class Engine {
+public:
+    Engine(cudaStream_t s, int precision, double cutoff);
+    ~Engine();
+    Engine(const Engine&) = delete;
+    Engine& operator=(const Engine&) = delete;
+
+    cudaStream_t stream;
+    cusolverDnHandle_t solver = nullptr;
+    int precision;
+    double cutoff;
+    bool profile = false;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    double ctr_ms = 0, svd_ms = 0;
+    long long ctr_launches = 0, ctr_flops = 0;
+
+    double* dalloc(long long n);                   // tracked, zero-filled device buffer
+    int* ialloc(const std::vector<int>& host);     // tracked device copy of an int table
+    Ten alloc(const std::vector<int>& dims) { return view(dalloc(prod(dims)), dims); }
+    static long long prod(const std::vector<int>& dims) {
+        long long n = 1;
+        for (int x : dims) n *= x;
+        return n;
+    }
+
+    // Contraction O = X * Y written as an einsum spec over single-character labels.  Labels
+    // present in X and Y but not in the output are summed; labels of X (Y) only must appear in
+    // the output.  With out == nullptr a contiguous output in the spec's order is allocated.
+    Ten ctr(Network& net, Plan& P, const std::string& spec, const Ten& X, const Ten& Y,
+            const Ten* out = nullptr, const double* rowscale = nullptr,
+            const double* colscale = nullptr);
+
+    struct PPair {
+        Ten PB, PT;
+    };
+    // Eqs. "projector construction" / "projector construction 2": U (rho_T) and L (rho_B) share
+    // the cut legs `labels`; `tl` are the truncated legs (in the order wanted for P_B / P_T).
+    // Returns P_B[t..., chi] and P_T[chi, t...].
+    PPair projector(Network& net, Plan& P, const Ten& U, const Ten& L, const std::string& labels,
+                    const std::string& tl);
+
+    void build_network(Network& net);
+    void finalize(Network& net);
+    void run(Plan& P);
+    void init_env(Network& net, unsigned long long seed);
+
+private:
+    std::vector<void*> allocs_;
+};
+
+}  // namespace sctm

@@ -1,0 +1,76 @@
+// Internal declarations of the split-CTMRG runtime (kernels + plan executor).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cusolverDn.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "sctm.h"
+
+namespace sctm {
+
+// ---------------------------------------------------------------------------------------------
+// Contraction launch descriptor.  A contraction O[b][m][n] = sum_k X[b][m][k] Y[b][k][n] over
+// multi-indices whose element offsets are read from gather tables (one table per operand and
+// index group), so any permutation of the stored legs is folded into the tile loads and the
+// epilogue store: no transpose kernel ever touches memory.
+// ---------------------------------------------------------------------------------------------
+struct CtrLaunch {
+    const double* X = nullptr;
+    const double* Y = nullptr;
+    double* O = nullptr;
+    const int* xm = nullptr;  // [M] offsets of X along the m group
+    const int* xk = nullptr;  // [K]
+    const int* yk = nullptr;  // [K]
+    const int* yn = nullptr;  // [N]
+    const int* om = nullptr;  // [M]
+    const int* on = nullptr;  // [N]
+    const int* xb = nullptr;  // [nb] batch offsets (nullptr when nb == 1)
+    const int* yb = nullptr;
+    const int* ob = nullptr;
+    int M = 1, N = 1, K = 1, nb = 1;
+    const double* rowscale = nullptr;  // optional O[m][n] *= rowscale[m]
+    const double* colscale = nullptr;  // optional O[m][n] *= colscale[n]
+    double* partial = nullptr;         // split-K workspace, nb*splits*M*N doubles
+    int splits = 1;
+    int kchunk = 1;
+    int precision = 0;                 // SCTM_PREC_*
+};
+
+void launch_ctr(const CtrLaunch& a, cudaStream_t s);
+
+// ---------------------------------------------------------------------------------------------
+// auxiliary kernels
+// ---------------------------------------------------------------------------------------------
+struct NormItem {          // dst[i0*s0+i1*s1+i2*s2] = src[i] / ||src||_F, i row-major over d0,d1,d2
+    const double* src;
+    double* dst;
+    int d0, d1, d2;
+    long long s0, s1, s2;
+};
+void launch_normalize(const NormItem* items_dev, int count, cudaStream_t s);
+
+void launch_splitmix_fill(double* p, long long n, unsigned long long seed, unsigned long long slot,
+                          cudaStream_t s);
+void launch_scalevec(const double* S, int k, double cutoff, double* out, cudaStream_t s);
+void launch_signfix(double* U, double* VT, int n, int k, cudaStream_t s);
+void launch_copy(const double* src, double* dst, long long n, cudaStream_t s);
+void launch_zero(double* p, long long n, cudaStream_t s);
+// flag[0] = 1 if any of p[0..n) is NaN or infinite, else 0
+void launch_check_finite(const double* p, long long n, int* flag, cudaStream_t s);
+void launch_spectrum_update(const double* Sraw, const double* rho, int chi, double* S_old,
+                            double* dS_out, cudaStream_t s);
+// lnk[0] = ln(Z11 Z00 / (Z10 Z01)) (NaN if the ratio is <= 0 or not finite), lnk[1] = Z11
+void launch_lnkappa(const double* Z00, const double* Z10, const double* Z01, const double* Z11,
+                    double* lnk, cudaStream_t s);
+// out[0] = -T (lnk_num - lnk_den)
+void launch_free_energy(const double* lnk_num, const double* lnk_den, double T, double* out,
+                        cudaStream_t s);
+// g = -2T (Enum / Z11num - Eden / Z11den)
+void launch_grad_combine(const double* Enum, const double* lnk_num, const double* Eden,
+                         const double* lnk_den, double T, int n, double* g, cudaStream_t s);
+
+}  // namespace sctm

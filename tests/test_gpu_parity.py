@@ -1,0 +1,173 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle on the same seeded
+inputs.  FP64 path tolerances: f to 1e-10 relative, g to 1e-8 relative (in norm), environment
+tensors element by element after single moves."""
+import numpy as np
+import pytest
+
+from oracle import ising, onsager, split_ctmrg as sc
+from paper_2506_19339_gb300 import build, inputs, sctm
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope='module', autouse=True)
+def lib():
+    build.build()
+    return sctm.load()
+
+
+def _run(A, T, chi, iters, tol=0.0, O=None):
+    if O is None:
+        st, O = sctm.sctm_ising_pepo(T)
+        assert st == sctm.SCTM_OK
+    r = sctm.SplitCTMRG(A, O, chi, T)
+    try:
+        st, it, ds = r.iterate(iters, tol)
+        return r.free_energy(), r.grad(), st, it, ds
+    finally:
+        r.close()
+
+
+def _oracle(A, T, chi, iters, tol=None):
+    return sc.evaluate(A, ising.ising_pepo(1.0 / T), ising.identity_pepo(), T, chi, iters, tol)
+
+
+def _rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b))
+
+
+@pytest.mark.parametrize('network', [sctm.SCTM_NET_NUM, sctm.SCTM_NET_DEN])
+def test_single_moves_match_oracle(network):
+    """Each directional move (left, right, up, down; Sec. III.B) from the same cold start gives the
+    same renormalised environment as the oracle, element by element (same SVD sign gauge)."""
+    T, D, chi = 4.6, 2, 5
+    A = inputs.random_peps(D, 0)
+    st, O = sctm.sctm_ising_pepo(T)
+    r = sctm.SplitCTMRG(A, O, chi, T)
+    Oo = ising.ising_pepo(1 / T) if network == sctm.SCTM_NET_NUM else ising.identity_pepo()
+    env = sc.init_env(chi, D, Oo.shape[2])
+    try:
+        got = r.env(network)
+        for k in ('C1', 'C2', 'C3', 'C4'):
+            assert np.array_equal(got[k], env[k]), 'cold start ' + k
+        for w, code in zip('LRUD', range(4)):
+            assert sctm.sctm_move(r.ctx, network, code) == sctm.SCTM_OK
+            env = sc.move(env, A, Oo, A, w, chi)
+            got = r.env(network)
+            for k in ('C1', 'C2', 'C3', 'C4'):
+                assert np.allclose(got[k], env[k], rtol=1e-9, atol=1e-10), (w, k)
+            for t in ('T1', 'T2', 'T3', 'T4'):
+                for x in range(3):
+                    assert np.allclose(got[t][x], env[t][x], rtol=1e-9, atol=1e-10), (w, t, x)
+    finally:
+        r.close()
+
+
+def test_config1_parity():
+    """D=2, chi=16, T=4.6, seed 0, 30 iterations (the plain FP64 configuration)."""
+    T, chi, iters = 4.6, 16, 30
+    A = inputs.random_peps(2, 0)
+    f, g, st, it, ds = _run(A, T, chi, iters)
+    ref = _oracle(A, T, chi, iters)
+    assert it == iters
+    assert abs(f - ref['f']) <= 1e-10 * abs(ref['f']), (f, ref['f'])
+    assert _rel(g, ref['g']) <= 1e-8
+
+
+def test_ragged_tiles_parity():
+    """D=3, chi=10: cut dimensions 60, 90, ... that do not fill 64-wide tiles."""
+    T, chi, iters = 4.5115, 10, 4
+    A = inputs.random_peps(3, 1)
+    f, g, *_ = _run(A, T, chi, iters)
+    ref = _oracle(A, T, chi, iters)
+    assert abs(f - ref['f']) <= 1e-10 * abs(ref['f'])
+    assert _rel(g, ref['g']) <= 1e-8
+
+
+def test_converged_perturbed_state_parity():
+    """A converging state, iterated to ||dS|| < 1e-10 on both sides."""
+    T, chi = 4.6, 12
+    A = inputs.perturbed_product_peps(2, 7)
+    f, g, st, it, ds = _run(A, T, chi, 100, 1e-10)
+    ref = _oracle(A, T, chi, 100, 1e-10)
+    assert st == sctm.SCTM_OK and ds < 1e-10
+    assert abs(f - ref['f']) <= 1e-10 * abs(ref['f'])
+    assert _rel(g, ref['g']) <= 1e-8
+
+
+def test_plus_state_is_onsager():
+    """D=1 product PEPS |+> at T=10: f = -T[ln cosh(1/T) + ln z_Onsager(1/T)] (closed form)."""
+    T = 10.0
+    A = inputs.product_plus_peps()
+    f, g, st, it, ds = _run(A, T, 8, 100, 1e-13)
+    assert abs(f - onsager.f_plus_state(T)) < 1e-10 * abs(f)
+
+
+def test_full_size_step_properties():
+    """D=4, chi=64 (the headline workload's shapes): one iteration against the oracle, and the
+    scale invariance <A, g> = 0 that holds at any size."""
+    T, chi = 4.5, 64
+    A = inputs.random_peps(4, 2)
+    f, g, *_ = _run(A, T, chi, 1)
+    assert np.isfinite(f)
+    assert abs(np.sum(A * g)) <= 1e-9 * np.linalg.norm(g) * np.linalg.norm(A)
+    ref = _oracle(A, T, chi, 1)
+    assert abs(f - ref['f']) <= 1e-10 * abs(ref['f'])
+    assert _rel(g, ref['g']) <= 1e-8
+
+
+def test_deterministic_and_checkpoint_roundtrip():
+    """Same inputs -> same bits; export / import of the environment resumes identically."""
+    T, chi = 4.6, 8
+    A = inputs.random_peps(2, 3)
+    st, O = sctm.sctm_ising_pepo(T)
+    r1 = sctm.SplitCTMRG(A, O, chi, T)
+    r2 = sctm.SplitCTMRG(A, O, chi, T)
+    try:
+        r1.iterate(3)
+        r2.iterate(3)
+        assert r1.free_energy() == r2.free_energy()
+        assert np.array_equal(r1.grad(), r2.grad())
+        for net in (0, 1):
+            st, buf = sctm.sctm_env_export(r1.ctx, net)
+            assert st == sctm.SCTM_OK
+            assert sctm.sctm_env_import(r2.ctx, net, buf) == sctm.SCTM_OK
+        r1.iterate(2)
+        r2.iterate(2)
+        assert r1.free_energy() == r2.free_energy()
+    finally:
+        r1.close()
+        r2.close()
+
+
+def test_status_codes():
+    T, chi = 4.6, 6
+    A = inputs.random_peps(2, 0)
+    st, O = sctm.sctm_ising_pepo(T)
+    r = sctm.SplitCTMRG(A, O, chi, T)
+    try:
+        st, it, ds = sctm.sctm_iterate(r.ctx, 1, 1e-14)
+        assert st == sctm.SCTM_ENOCONV and it == 1
+        st, f = sctm.sctm_free_energy(r.ctx)
+        assert st == sctm.SCTM_ENOCONV and np.isfinite(f)
+        assert sctm.sctm_iterate(r.ctx, -1, 0.0)[0] == sctm.SCTM_EINVAL
+        assert sctm.sctm_move(r.ctx, 0, 7) == sctm.SCTM_EINVAL
+        assert sctm.sctm_env_size(r.ctx, 2) == 0
+        Anan = A.copy()
+        Anan[0, 0, 0, 0, 0] = np.nan
+        # rejected on entry; the previous PEPS stays in place and the context stays usable
+        assert sctm.sctm_set_peps(r.ctx, Anan, 1) == sctm.SCTM_ENUMERIC
+        assert sctm.sctm_set_peps(r.ctx, A, 1) == sctm.SCTM_OK
+        st, it, ds = sctm.sctm_iterate(r.ctx, 1, 0.0)
+        assert st == sctm.SCTM_OK
+    finally:
+        r.close()
+
+
+def test_chi_one_and_d1():
+    """Degenerate sizes: chi = 1 and D = 1 run and agree with the oracle."""
+    T = 4.6
+    A = inputs.random_peps(1, 5)
+    f, g, *_ = _run(A, T, 1, 3)
+    ref = _oracle(A, T, 1, 3)
+    assert abs(f - ref['f']) <= 1e-10 * abs(ref['f'])
