@@ -148,14 +148,20 @@ sctm_status sctm_create(const double* peps, const double* pepo, int chi, const s
         c->f_dev = e.dalloc(1);
         c->g_dev = e.dalloc(na);
         c->flag_dev = (int*)e.dalloc(1);
-        cuda_ok(cudaMemcpy(c->A_dev, peps, na * sizeof(double), cudaMemcpyDefault), "copy peps");
+        if (!e.dry)
+            cuda_ok(cudaMemcpy(c->A_dev, peps, na * sizeof(double), cudaMemcpyDefault),
+                    "copy peps");
         c->A_stage = e.dalloc(na);
-        if (!peps_is_finite(c.get(), c->A_dev)) return SCTM_ENUMERIC;
-        cuda_ok(cudaMemcpy(c->O_dev, pepo, no * sizeof(double), cudaMemcpyDefault), "copy pepo");
-        std::vector<double> oid((size_t)opts.p * opts.p, 0.0);
-        for (int i = 0; i < opts.p; ++i) oid[(size_t)i * opts.p + i] = 1.0;
-        cuda_ok(cudaMemcpy(c->Oid_dev, oid.data(), oid.size() * sizeof(double),
-                           cudaMemcpyHostToDevice), "copy identity pepo");
+        if (!e.dry) {
+            if (!peps_is_finite(c.get(), c->A_dev)) return SCTM_ENUMERIC;
+            cuda_ok(cudaMemcpy(c->O_dev, pepo, no * sizeof(double), cudaMemcpyDefault),
+                    "copy pepo");
+            std::vector<double> oid((size_t)opts.p * opts.p, 0.0);
+            for (int i = 0; i < opts.p; ++i) oid[(size_t)i * opts.p + i] = 1.0;
+            cuda_ok(cudaMemcpy(c->Oid_dev, oid.data(), oid.size() * sizeof(double),
+                               cudaMemcpyHostToDevice),
+                    "copy identity pepo");
+        }
         for (int n = 0; n < 2; ++n) {
             Network& net = c->net[n];
             net.D = opts.D;
@@ -167,6 +173,10 @@ sctm_status sctm_create(const double* peps, const double* pepo, int chi, const s
             net.O = n == 0 ? view(c->O_dev, {opts.p, opts.p, opts.d, opts.d, opts.d, opts.d})
                            : view(c->Oid_dev, {opts.p, opts.p, 1, 1, 1, 1});
             e.build_network(net);
+        }
+        if (e.dry) {  // plans only: report success without a usable context
+            c.reset();
+            return SCTM_OK;
         }
         cuda_ok(cudaDeviceSynchronize(), "plan build");
         for (int n = 0; n < 2; ++n) e.init_env(c->net[n], opts.init_seed);

@@ -30,6 +30,7 @@ namespace sctm {
     } while (0)
 
 Ten view(double* p, const std::vector<int>& dims) {
+    if ((int)dims.size() > kMaxRank) throw Error(SCTM_EINVAL, "tensor rank above kMaxRank");
     Ten t;
     t.p = p;
     t.nd = (int)dims.size();
@@ -112,6 +113,9 @@ struct FnStep : Step {
 // engine
 // ---------------------------------------------------------------------------------------------
 Engine::Engine(cudaStream_t s, int prec, double cut) : stream(s), precision(prec), cutoff(cut) {
+    const char* dr = getenv("SCTM_DRYRUN");
+    dry = dr && dr[0] == '1';
+    if (dry) return;
     SOLVER_OK(cusolverDnCreate(&solver));
     SOLVER_OK(cusolverDnSetStream(solver, stream));
     const char* pf = getenv("SCTM_PROFILE");
@@ -129,7 +133,10 @@ Engine::~Engine() {
     if (ev1) cudaEventDestroy(ev1);
 }
 
+static char dry_base[64];
+
 double* Engine::dalloc(long long n) {
+    if (dry) return (double*)dry_base;
     void* p = nullptr;
     CUDA_OK(cudaMalloc(&p, std::max<long long>(n, 1) * sizeof(double)));
     allocs_.push_back(p);
@@ -138,6 +145,7 @@ double* Engine::dalloc(long long n) {
 }
 
 int* Engine::ialloc(const std::vector<int>& host) {
+    if (dry) return (int*)dry_base;
     void* p = nullptr;
     size_t bytes = std::max<size_t>(host.size(), 1) * sizeof(int);
     CUDA_OK(cudaMalloc(&p, bytes));
@@ -181,6 +189,7 @@ Ten Engine::ctr(Network& net, Plan& P, const std::string& spec, const Ten& X, co
         throw Error(SCTM_EINVAL, "bad contraction spec " + spec);
     const std::string xl = spec.substr(0, comma), yl = spec.substr(comma + 1, arrow - comma - 1),
                       ol = spec.substr(arrow + 2);
+    if ((int)ol.size() > kMaxRank) throw Error(SCTM_EINVAL, "output rank above kMaxRank: " + spec);
     if ((int)xl.size() != X.nd || (int)yl.size() != Y.nd)
         throw Error(SCTM_EINVAL, "rank mismatch in " + spec);
     std::map<char, int> dims;
@@ -299,6 +308,7 @@ Engine::PPair Engine::projector(Network& net, Plan& P, const Ten& U, const Ten& 
     const int chi = net.chi;
     if (n < chi) throw Error(SCTM_EINVAL, "projector: remaining dimension smaller than chi");
     // M[r', r] = sum_t L[t, r'] U[t, r], column-major (row r' from L, column r from U)
+    if (2 * (int)rl.size() > kMaxRank) throw Error(SCTM_EINVAL, "projector rank above kMaxRank");
     Ten M;
     M.p = dalloc((long long)n * n);
     M.nd = (int)(2 * rl.size());
@@ -580,7 +590,9 @@ static void build_left_move(Engine& e, Network& net, Plan& P, const Frame& f) {
     items.push_back(item(T4bn, f.T[3][2]));
     items.push_back(item(C4n, f.C[3]));
     NormItem* dev = (NormItem*)e.dalloc((long long)(items.size() * sizeof(NormItem) + 7) / 8);
-    CUDA_OK(cudaMemcpy(dev, items.data(), items.size() * sizeof(NormItem), cudaMemcpyHostToDevice));
+    if (!e.dry)
+        CUDA_OK(cudaMemcpy(dev, items.data(), items.size() * sizeof(NormItem),
+                           cudaMemcpyHostToDevice));
     const int cnt = (int)items.size();
     P.push_back(std::make_unique<FnStep>([=](cudaStream_t s) { launch_normalize(dev, cnt, s); }));
 }
@@ -670,6 +682,7 @@ static void build_local(Engine& e, Network& net) {
 }
 
 void Engine::init_env(Network& net, unsigned long long seed) {
+    if (dry) return;
     unsigned long long q = 0;
     for (int i = 0; i < 4; ++i) launch_splitmix_fill(net.C[i].p, net.C[i].numel(), seed, q++, stream);
     for (int i = 0; i < 4; ++i)
@@ -704,6 +717,7 @@ void Engine::finalize(Network& net) {
             if (s->a.splits > 1) s->a.partial = net.splitk_ws;
     }
     int lwork = 0;
+    if (dry) return;
     SOLVER_OK(cusolverDnDgesvd_bufferSize(solver, net.svd_nmax, net.svd_nmax, &lwork));
     net.svd_lwork = std::max(lwork, 1);
     net.svd_work = dalloc(net.svd_lwork);

@@ -15,12 +15,13 @@ struct Error : std::runtime_error {
     Error(sctm_status c, const std::string& m) : std::runtime_error(m), code(c) {}
 };
 
-// A strided view of FP64 device memory.
+// A strided view of FP64 device memory (rank <= kMaxRank).
+constexpr int kMaxRank = 12;
 struct Ten {
     double* p = nullptr;
     int nd = 0;
-    int dim[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    long long st[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int dim[kMaxRank] = {0};
+    long long st[kMaxRank] = {0};
     long long numel() const {
         long long n = 1;
         for (int i = 0; i < nd; ++i) n *= dim[i];
@@ -77,6 +78,7 @@ public:
     int precision;
     double cutoff;
     bool profile = false;
+    bool dry = false;  // SCTM_DRYRUN=1: build plans with placeholder pointers, no CUDA calls
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     double ctr_ms = 0, svd_ms = 0;
     long long ctr_launches = 0, ctr_flops = 0;
