@@ -151,6 +151,12 @@ sctm_status sctm_move(sctm_ctx* ctx, int network, int direction);
  * into a host buffer of chi doubles. */
 sctm_status sctm_spectrum(sctm_ctx* ctx, int network, double* S);
 
+/* sctm_local_values -- the local contractions of one network from its current environment
+ * (Sec. II, Fig. 4(b)): out[0..3] = Z00, Z10, Z01, Z11 and out[4] = ln kappa,
+ * kappa = Z11 Z00 / (Z10 Z01) (NaN when kappa <= 0).  Host buffer of 5 doubles.  Each Z depends
+ * on the normalisation of the environment tensors; kappa does not.  For inspection and tests. */
+sctm_status sctm_local_values(sctm_ctx* ctx, int network, double* out5);
+
 /* sctm_profile -- cumulative device time (ms) of the contraction kernels, of the SVDs and of
  * everything since the context was created or since the last reset (reset != 0 zeroes the
  * counters after reading).  Timing is recorded only when the environment variable

@@ -383,6 +383,24 @@ sctm_status sctm_spectrum(sctm_ctx* ctx, int network, double* S) {
     API_END(ctx)
 }
 
+sctm_status sctm_local_values(sctm_ctx* ctx, int network, double* out5) {
+    API_BEGIN(ctx)
+    if (network < 0 || network > 1 || !out5) throw Error(SCTM_EINVAL, "bad network or buffer");
+    Network& net = ctx->net[network];
+    ctx->eng->run(net.local);
+    check_cuda("local contractions");
+    for (int k = 0; k < 4; ++k)
+        cuda_ok(cudaMemcpyAsync(out5 + k, net.z[k], sizeof(double), cudaMemcpyDeviceToHost,
+                                ctx->eng->stream),
+                "Z copy");
+    cuda_ok(cudaMemcpyAsync(out5 + 4, net.lnk, sizeof(double), cudaMemcpyDeviceToHost,
+                            ctx->eng->stream),
+            "lnk copy");
+    cuda_ok(cudaStreamSynchronize(ctx->eng->stream), "Z sync");
+    return SCTM_OK;
+    API_END(ctx)
+}
+
 sctm_status sctm_profile(sctm_ctx* ctx, double* ctr_ms, double* svd_ms, double* total_ms,
                          long long* ctr_launches, long long* ctr_flops, int reset) {
     API_BEGIN(ctx)

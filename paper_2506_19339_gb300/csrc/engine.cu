@@ -677,6 +677,10 @@ static void build_local(Engine& e, Network& net) {
     X = C("eftbylv,vefgw->tbylgw", X, Cbot);
     C("tbylgw,ywr->tblgr", X, T2b, &net.E);
     double *z00 = Z00.p, *z10 = Z10.p, *z01 = Z01.p, *z11 = Z11.p, *lnk = net.lnk;
+    net.z[0] = z00;
+    net.z[1] = z10;
+    net.z[2] = z01;
+    net.z[3] = z11;
     P.push_back(std::make_unique<FnStep>(
         [=](cudaStream_t s) { launch_lnkappa(z00, z10, z01, z11, lnk, s); }));
 }

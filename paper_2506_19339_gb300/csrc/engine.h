@@ -52,6 +52,7 @@ struct Network {
     double* S_old = nullptr;
     double* dS = nullptr;     // device scalar
     double* lnk = nullptr;    // device [ln kappa, Z11]
+    double* z[4] = {nullptr, nullptr, nullptr, nullptr};  // device Z00, Z10, Z01, Z11
     Ten E;                    // bra environment, layout of A
     int* svd_info = nullptr;  // one int per SVD step
     int n_svd = 0;

@@ -66,6 +66,7 @@ def load():
         'sctm_env_import': (I, [P, I, P, S]),
         'sctm_move': (I, [P, I, I]),
         'sctm_spectrum': (I, [P, I, P]),
+        'sctm_local_values': (I, [P, I, P]),
         'sctm_profile': (I, [P, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D),
                              ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
                              I]),
@@ -162,6 +163,12 @@ def sctm_spectrum(ctx, network, chi):
     S = np.zeros(chi)
     st = load().sctm_spectrum(ctx, int(network), _ptr(S))
     return st, S
+
+
+def sctm_local_values(ctx, network):
+    out = np.zeros(5)
+    st = load().sctm_local_values(ctx, int(network), _ptr(out))
+    return st, out
 
 
 def sctm_profile(ctx, reset=False):
