@@ -1,0 +1,354 @@
+"""Benchmark: split-CTMRG free energy + gradient evaluations per second (arXiv:2506.19339).
+
+One step = one f + grad f evaluation of the workload: the numerator <psi|T|psi> and norm <psi|psi>
+environments are reset to the cold start and iterated (left, right, up, down moves per
+iteration; Sec. III.B) for a fixed budget of iterations (or until ||dS||_2 < tol), then f and g
+are evaluated (Sec. II).  Everything runs through the C ABI of libsctm.so.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--iters I] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun with N > 1 every rank runs an independent replica
+(the single-instance path does not shard) and `value` is the sum over ranks.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "split-CTMRG f+∇f evals/s at D=4 χ=64, mixed vs FP64 at |Δf|≤1e-8; % of peak"
+WORKLOAD = dict(D=4, chi=64, T=4.5, seed=2)   # the configuration the metric is quoted on
+NOMINAL_FP64_TFLOPS = 1.25                     # GB300 FP64 (vector and tensor), nominal
+NOMINAL_BF16_TFLOPS = 2250.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument('--gpus', type=int, default=1)
+    ap.add_argument('--steps', type=int, default=3)
+    ap.add_argument('--warmup', type=int, default=3)
+    ap.add_argument('--iters', type=int, default=10, help='split-CTMRG iterations per evaluation')
+    ap.add_argument('--tol', type=float, default=1e-10)
+    ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
+    ap.add_argument('--no-cpu-baseline', action='store_true')
+    return ap.parse_args()
+
+
+def workload_name(it):
+    w = WORKLOAD
+    return ('split-CTMRG f+grad, 3D Ising PEPO, PEPS D=%d N(0,1) seed %d, chi=%d, T=%g, '
+            '%d iterations (num + norm networks) per evaluation, tol %g' %
+            (w['D'], w['seed'], w['chi'], w['T'], it, 1e-10))
+
+
+# ------------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ('index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,'
+              'clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,'
+              'clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap')
+
+    def __init__(self, gpu=0):
+        self.gpu = gpu
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(['nvidia-smi', '-i', str(self.gpu), '--query-gpu=' + self.FIELDS,
+                                          '--format=csv,noheader,nounits', '-lms', '200'],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(',')]
+            if len(parts) >= 9:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+        sm = [float(s[1]) for s in self.samples if s[1].replace('.', '').isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace('.', '').isdigit()]
+        reasons = set()
+        names = ['hw_slowdown', 'hw_thermal_slowdown', 'sw_thermal_slowdown', 'sw_power_cap']
+        for s in self.samples:
+            for name, v in zip(names, s[5:9]):
+                if v.lower().startswith('active'):
+                    reasons.add(name)
+        return {'sm_mhz': float(np.median(sm)) if sm else None,
+                'sm_max_mhz': max(mx) if mx else None,
+                'reasons': sorted(reasons), 'samples': len(self.samples)}
+
+
+# ------------------------------------------------------------------------------------------------
+# CPU baseline / reference arm: the FP64 oracle on the host cores
+# ------------------------------------------------------------------------------------------------
+def oracle_sample(A, T, chi, iters, budget_s=20.0):
+    """Time the oracle on a bounded sample: moves of the numerator then the norm network (4 moves
+    per iteration each) until `budget_s` of CPU work; scale to evaluations/s at `iters` iterations
+    per evaluation."""
+    from oracle import ising, split_ctmrg as sc
+    D = A.shape[1]
+    nets = [ising.ising_pepo(1.0 / T), ising.identity_pepo()]
+    moves_done = [0, 0]
+    secs = [0.0, 0.0]
+    for n, O in enumerate(nets):
+        env = sc.init_env(chi, D, O.shape[2])
+        t0 = time.perf_counter()
+        for w in 'LRUD':
+            env = sc.move(env, A, O, A, w, chi)
+            moves_done[n] += 1
+            if time.perf_counter() - t0 > budget_s / 2:
+                break
+        secs[n] = time.perf_counter() - t0
+    per_move = [secs[n] / moves_done[n] for n in range(2)]
+    sec_per_eval = 4 * iters * (per_move[0] + per_move[1])
+    sample = ('%d numerator + %d norm left/right/up/down moves of the FP64 oracle at the workload '
+              'size (%.1f s), scaled to %d iterations x 4 moves x 2 networks per evaluation' %
+              (moves_done[0], moves_done[1], secs[0] + secs[1], iters))
+    return 1.0 / sec_per_eval, sample, secs[0] + secs[1]
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+def run_reference(args):
+    from paper_2506_19339_gb300 import inputs
+    w = WORKLOAD
+    rank = int(os.environ.get('RANK', '0'))
+    if rank != 0:
+        return
+    A = inputs.random_peps(w['D'], w['seed'])
+    budget = max(2.0, min(20.0, 150.0 / max(args.steps + args.warmup, 1)))
+    for _ in range(args.warmup):
+        oracle_sample(A, w['T'], w['chi'], args.iters, budget_s=budget / 4)
+    vals = []
+    samples = []
+    for _ in range(args.steps):
+        v, sample, secs = oracle_sample(A, w['T'], w['chi'], args.iters, budget_s=budget)
+        vals.append(v)
+        samples.append(secs)
+    value = float(np.mean(vals))
+    line = {
+        'impl': 'reference', 'metric': METRIC, 'value': value, 'unit': 'evals/s',
+        'n_gpus': args.gpus, 'steps': args.steps, 'warmup': args.warmup,
+        'ms_per_step': 1000.0 / value, 'higher_is_better': True, 'scaling': 'weak',
+        'vs_baseline': None, 'dtype': 'f64', 'data': 'synthetic',
+        'config': {'workload': workload_name(args.iters), 'D': w['D'], 'chi': w['chi'],
+                   'T': w['T'], 'seed': w['seed'], 'iterations_per_eval': args.iters},
+        'cpu_baseline': {'value': value, 'unit': 'evals/s', 'cores': cpu_cores(), 'kind': 'oracle',
+                         'sample': sample},
+        'e2e': {'value': value, 'unit': 'evals/s', 'h2d_bytes_per_step': 0,
+                'd2h_bytes_per_step': 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------------
+# our arm
+# ------------------------------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    from paper_2506_19339_gb300 import build, inputs, sctm
+    w = WORKLOAD
+    world = int(os.environ.get('WORLD_SIZE', '1'))
+    rank = int(os.environ.get('RANK', '0'))
+    local = int(os.environ.get('LOCAL_RANK', '0'))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group('nccl')
+    dev = torch.device('cuda', local)
+    torch.cuda.set_device(dev)
+    build.build()
+    sctm.load()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        A_cpu = inputs.random_peps(w['D'], w['seed'])
+        v, sample, secs = oracle_sample(A_cpu, w['T'], w['chi'], args.iters, budget_s=20.0)
+        cpu = {'value': v, 'unit': 'evals/s', 'cores': cpu_cores(), 'kind': 'oracle',
+               'sample': sample}
+
+    A_host = inputs.random_peps(w['D'], w['seed'])
+    st, O = sctm.sctm_ising_pepo(w['T'])
+    stream = torch.cuda.current_stream(dev)
+    st, o = sctm.sctm_default_opts()
+    o.T, o.D, o.p, o.d = w['T'], w['D'], 2, 2
+    o.cuda_stream = stream.cuda_stream
+    A_dev = torch.from_numpy(A_host).to(dev)
+    st, ctx = sctm.sctm_create(A_dev, np.ascontiguousarray(O), w['chi'], o)
+    if st != sctm.SCTM_OK:
+        raise RuntimeError('sctm_create failed: %s' % sctm.STATUS_NAMES[st])
+    g_dev = torch.zeros_like(A_dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (126 MB)
+
+    def evaluate(A_ptr, g_ptr):
+        assert sctm.sctm_set_peps(ctx, A_ptr, 1) == sctm.SCTM_OK
+        st, it, ds = sctm.sctm_iterate(ctx, args.iters, args.tol)
+        assert st in (sctm.SCTM_OK, sctm.SCTM_ENOCONV), sctm.sctm_last_error(ctx)
+        st, f = sctm.sctm_free_energy(ctx)
+        st2 = sctm.sctm_grad(ctx, g_ptr)
+        return f, it, ds, st
+
+    # warm-up
+    for _ in range(args.warmup):
+        evaluate(A_dev, g_dev)
+    torch.cuda.synchronize(dev)
+
+    # ---- timed region, device-resident inputs
+    sctm.sctm_profile(ctx, reset=True)
+    sctm.sctm_set_profiling(ctx, True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    step_ms = []
+    its = []
+    fs = []
+    statuses = []
+    t_wall = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        f, it, ds, stf = evaluate(A_dev, g_dev)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        its.append(it)
+        fs.append(f)
+        statuses.append(stf)
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    sctm.sctm_set_profiling(ctx, False)
+    st, prof = sctm.sctm_profile(ctx, reset=True)
+    ms = float(np.sum(step_ms))
+
+    # ---- e2e: host buffers through the C ABI, host<->device copies inside the timed region
+    A_pin = torch.from_numpy(A_host).pin_memory()
+    g_pin = torch.zeros(A_host.shape, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize(dev)
+    e2e_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        evaluate(A_pin.numpy(), g_pin.numpy())
+        torch.cuda.synchronize(dev)
+        e2e_ms.append(1000.0 * (time.perf_counter() - t0))
+    st, prof_e2e = sctm.sctm_profile(ctx, reset=True)
+
+    # FP64 matrix-multiply rate of this GPU (cuBLAS through torch), context for the roofline
+    a = torch.randn(4096, 4096, dtype=torch.float64, device=dev)
+    torch.matmul(a, a)
+    torch.cuda.synchronize(dev)
+    best = 1e9
+    for _ in range(3):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, a)
+        e1.record()
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    dgemm_tflops = 2 * 4096 ** 3 / (best * 1e-3) / 1e12
+    sctm.sctm_destroy(ctx)
+
+    # max over ranks
+    if dist:
+        t = torch.tensor([ms, float(np.sum(e2e_ms))], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, e2e_total = float(t[0]), float(t[1])
+        dist.destroy_process_group()
+    else:
+        e2e_total = float(np.sum(e2e_ms))
+    if rank != 0:
+        return
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, 'MEASURED_PEAKS.json')))
+    except (OSError, ValueError):
+        pass
+    if 'bf16_tflops_sustained' in peaks:
+        fp64_peak = peaks['bf16_tflops_sustained'] * NOMINAL_FP64_TFLOPS / NOMINAL_BF16_TFLOPS
+        peak_note = 'measured bf16 sustained x nominal FP64/BF16 ratio (1.25/2250)'
+    else:
+        fp64_peak = 1700.0 * NOMINAL_FP64_TFLOPS / NOMINAL_BF16_TFLOPS
+        peak_note = 'fallback bf16 sustained x nominal FP64/BF16 ratio'
+    achieved = (prof['ctr_flops'] / (prof['ctr_ms'] * 1e-3) / 1e12) if prof['ctr_ms'] > 0 else None
+    n_steps = args.steps * world
+    value = n_steps / (ms * 1e-3)
+    total_its = int(np.sum(its))
+    line = {
+        'metric': METRIC, 'value': value, 'unit': 'evals/s', 'n_gpus': world,
+        'steps': args.steps, 'warmup': args.warmup, 'ms_per_step': ms / args.steps,
+        'higher_is_better': True, 'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f64',
+        'data': 'synthetic',
+        'config': {'workload': workload_name(args.iters), 'D': w['D'], 'chi': w['chi'],
+                   'T': w['T'], 'seed': w['seed'], 'iterations_per_eval': args.iters,
+                   'precision': 'FP64 contractions, FP64 SVD', 'parallelism': 'replicas',
+                   'l2': 'flushed before every step (256 MiB write, outside the step events)'},
+        'iterations_per_s': total_its * world / (ms * 1e-3),
+        'f': fs[-1], 'status': [sctm.STATUS_NAMES[s] for s in statuses][-1],
+        'roofline': {'bound': 'alu', 'kernel': 'ctr_f64_kernel', 'achieved': achieved,
+                     'peak': fp64_peak, 'unit': 'TFLOP/s',
+                     'frac': (achieved / fp64_peak) if achieved else None, 'traffic': None,
+                     'peak_note': peak_note, 'dgemm_torch_tflops': dgemm_tflops,
+                     'ctr_ms_per_step': prof['ctr_ms'] / args.steps,
+                     'svd_ms_per_step': prof['svd_ms'] / args.steps,
+                     'ctr_launches_per_step': prof['ctr_launches'] / args.steps,
+                     'svd_calls_per_step': prof['svd_calls'] / args.steps},
+        'cpu_baseline': cpu,
+        'e2e': {'value': n_steps / (e2e_total * 1e-3), 'unit': 'evals/s',
+                'h2d_bytes_per_step': int(A_host.nbytes),
+                'd2h_bytes_per_step': int(A_host.nbytes + 8)},
+        'clocks': clk,
+        'gpu_launches': int(prof['kernel_launches']),
+        'wall_s': wall,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == 'reference':
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == '__main__':
+    main()

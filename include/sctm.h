@@ -157,12 +157,20 @@ sctm_status sctm_spectrum(sctm_ctx* ctx, int network, double* S);
  * on the normalisation of the environment tensors; kappa does not.  For inspection and tests. */
 sctm_status sctm_local_values(sctm_ctx* ctx, int network, double* out5);
 
-/* sctm_profile -- cumulative device time (ms) of the contraction kernels, of the SVDs and of
- * everything since the context was created or since the last reset (reset != 0 zeroes the
- * counters after reading).  Timing is recorded only when the environment variable
- * SCTM_PROFILE=1 was set at create time; otherwise the values are 0. */
-sctm_status sctm_profile(sctm_ctx* ctx, double* ctr_ms, double* svd_ms, double* total_ms,
-                         long long* ctr_launches, long long* ctr_flops, int reset);
+/* sctm_set_profiling -- on != 0 records CUDA events around every contraction kernel and every
+ * SVD (no host synchronisation is added; the events are read after each iteration).  Off by
+ * default, or on from creation when the environment variable SCTM_PROFILE=1 is set. */
+sctm_status sctm_set_profiling(sctm_ctx* ctx, int on);
+
+/* sctm_profile -- counters since creation or the last reset (reset != 0 zeroes them after
+ * reading).  Any output pointer may be NULL.
+ *   ctr_ms, ctr_launches, ctr_flops  device time, launches and algorithmic FLOPs (2 M N K per
+ *                                    contraction) of the contraction kernel (profiling only)
+ *   svd_ms, svd_calls                device time and count of the cuSOLVER SVDs (profiling only)
+ *   kernel_launches                  launches of this library's own kernels (always counted) */
+sctm_status sctm_profile(sctm_ctx* ctx, double* ctr_ms, long long* ctr_launches,
+                         long long* ctr_flops, double* svd_ms, long long* svd_calls,
+                         long long* kernel_launches, int reset);
 
 #ifdef __cplusplus
 }

@@ -225,6 +225,7 @@ sctm_status sctm_iterate(sctm_ctx* ctx, int max_it, double tol, int* it_done, do
             for (int m = 0; m < 4; ++m) e.run(net.move[m]);
             e.run(net.spectrum);
             check_cuda("iteration");
+            if (e.profile) e.harvest();
             cuda_ok(cudaMemcpyAsync(&dS, net.dS, sizeof(double), cudaMemcpyDeviceToHost, e.stream),
                     "dS copy");
             cuda_ok(cudaStreamSynchronize(e.stream), "iteration sync");
@@ -401,18 +402,30 @@ sctm_status sctm_local_values(sctm_ctx* ctx, int network, double* out5) {
     API_END(ctx)
 }
 
-sctm_status sctm_profile(sctm_ctx* ctx, double* ctr_ms, double* svd_ms, double* total_ms,
-                         long long* ctr_launches, long long* ctr_flops, int reset) {
+sctm_status sctm_set_profiling(sctm_ctx* ctx, int on) {
+    API_BEGIN(ctx)
+    ctx->eng->harvest();
+    ctx->eng->profile = on != 0;
+    return SCTM_OK;
+    API_END(ctx)
+}
+
+sctm_status sctm_profile(sctm_ctx* ctx, double* ctr_ms, long long* ctr_launches,
+                         long long* ctr_flops, double* svd_ms, long long* svd_calls,
+                         long long* kernel_launches, int reset) {
     API_BEGIN(ctx)
     Engine& e = *ctx->eng;
+    e.harvest();
     if (ctr_ms) *ctr_ms = e.ctr_ms;
-    if (svd_ms) *svd_ms = e.svd_ms;
-    if (total_ms) *total_ms = e.ctr_ms + e.svd_ms;
     if (ctr_launches) *ctr_launches = e.ctr_launches;
     if (ctr_flops) *ctr_flops = e.ctr_flops;
+    if (svd_ms) *svd_ms = e.svd_ms;
+    if (svd_calls) *svd_calls = e.svd_calls;
+    if (kernel_launches) *kernel_launches = e.kernel_launches.load();
     if (reset) {
         e.ctr_ms = e.svd_ms = 0;
-        e.ctr_launches = e.ctr_flops = 0;
+        e.ctr_launches = e.ctr_flops = e.svd_calls = 0;
+        e.kernel_launches = 0;
     }
     return SCTM_OK;
     API_END(ctx)

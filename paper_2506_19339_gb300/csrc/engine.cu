@@ -57,22 +57,17 @@ Ten permute(const Ten& t, const std::vector<int>& perm) {
 // ---------------------------------------------------------------------------------------------
 // steps
 // ---------------------------------------------------------------------------------------------
+enum { KIND_CTR = 0, KIND_SVD = 1 };
+
 struct CtrStep : Step {
     CtrLaunch a;
     size_t partial_need = 0;
     long long flops = 0;
     void run(Engine& e) override {
-        if (e.profile) cudaEventRecord(e.ev0, e.stream);
-        launch_ctr(a, e.stream);
-        if (e.profile) {
-            cudaEventRecord(e.ev1, e.stream);
-            cudaEventSynchronize(e.ev1);
-            float ms = 0;
-            cudaEventElapsedTime(&ms, e.ev0, e.ev1);
-            e.ctr_ms += ms;
-            e.ctr_launches += 1;
-            e.ctr_flops += flops;
-        }
+        const int e0 = e.profile ? e.record(sid) : -1;
+        launch_ctr(a, e.streams[sid]);
+        e.kernel_launches += a.splits > 1 ? 2 : 1;
+        if (e.profile) e.record_done(sid, KIND_CTR, flops, e0);
     }
 };
 
@@ -81,32 +76,64 @@ struct SvdStep : Step {
     int n = 0;
     double* S = nullptr;
     double* U = nullptr;
-    double* VT = nullptr;
+    double* V = nullptr;  // right singular vectors as columns (n x n, column-major)
     bool vectors = true;
     Network* net = nullptr;
     int info_idx = 0;
     void run(Engine& e) override {
-        if (e.profile) cudaEventRecord(e.ev0, e.stream);
-        signed char jobu = vectors ? 'S' : 'N';
-        cusolverStatus_t st = cusolverDnDgesvd(e.solver, jobu, jobu, n, n, M, n, S, U, n, VT, n,
-                                               net->svd_work, net->svd_lwork, net->svd_rwork,
-                                               net->svd_info + info_idx);
+        const int e0 = e.profile ? e.record(sid) : -1;
+        double herr = 0.0;
+        cusolverStatus_t st = cusolverDnXgesvdp(
+            e.solver[sid], e.solver_params,
+            vectors ? CUSOLVER_EIG_MODE_VECTOR : CUSOLVER_EIG_MODE_NOVECTOR, 1, n, n, CUDA_R_64F, M,
+            n, CUDA_R_64F, S, CUDA_R_64F, U, n, CUDA_R_64F, V, n, CUDA_R_64F, net->svd_dwork[sid],
+            net->svd_dbytes, net->svd_hwork[sid].data(), net->svd_hbytes,
+            net->svd_info + info_idx, &herr);
         if (st != CUSOLVER_STATUS_SUCCESS)
-            throw Error(SCTM_ECUSOLVER, "cusolverDnDgesvd failed: " + std::to_string(st));
-        if (e.profile) {
-            cudaEventRecord(e.ev1, e.stream);
-            cudaEventSynchronize(e.ev1);
-            float ms = 0;
-            cudaEventElapsedTime(&ms, e.ev0, e.ev1);
-            e.svd_ms += ms;
-        }
+            throw Error(SCTM_ECUSOLVER, "cusolverDnXgesvdp failed: " + std::to_string(st));
+        if (e.profile) e.record_done(sid, KIND_SVD, 0, e0);
     }
 };
 
 struct FnStep : Step {
     std::function<void(cudaStream_t)> f;
     explicit FnStep(std::function<void(cudaStream_t)> g) : f(std::move(g)) {}
-    void run(Engine& e) override { f(e.stream); }
+    void run(Engine& e) override {
+        f(e.streams[sid]);
+        e.kernel_launches += 1;
+    }
+};
+
+struct ParallelStep : Step {
+    std::vector<Plan> sub;
+    cudaEvent_t fork_ev = nullptr;
+    std::vector<cudaEvent_t> join_ev;
+    void run(Engine& e) override {
+        cudaEventRecord(fork_ev, e.streams[0]);
+        for (size_t i = 0; i < sub.size(); ++i) cudaStreamWaitEvent(e.streams[i + 1], fork_ev, 0);
+        std::vector<std::exception_ptr> errs(sub.size());
+        std::vector<std::thread> th;
+        for (size_t i = 1; i < sub.size(); ++i)
+            th.emplace_back([&, i] {
+                try {
+                    e.run_sub(sub[i]);
+                } catch (...) {
+                    errs[i] = std::current_exception();
+                }
+            });
+        try {
+            if (!sub.empty()) e.run_sub(sub[0]);
+        } catch (...) {
+            errs[0] = std::current_exception();
+        }
+        for (auto& t : th) t.join();
+        for (size_t i = 0; i < sub.size(); ++i) {
+            cudaEventRecord(join_ev[i], e.streams[i + 1]);
+            cudaStreamWaitEvent(e.streams[0], join_ev[i], 0);
+        }
+        for (auto& x : errs)
+            if (x) std::rethrow_exception(x);
+    }
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -116,27 +143,69 @@ Engine::Engine(cudaStream_t s, int prec, double cut) : stream(s), precision(prec
     const char* dr = getenv("SCTM_DRYRUN");
     dry = dr && dr[0] == '1';
     if (dry) return;
-    SOLVER_OK(cusolverDnCreate(&solver));
-    SOLVER_OK(cusolverDnSetStream(solver, stream));
+    streams[0] = s;
+    for (int i = 1; i < kStreams; ++i)
+        CUDA_OK(cudaStreamCreateWithFlags(&streams[i], cudaStreamNonBlocking));
+    for (int i = 0; i < kStreams; ++i) {
+        SOLVER_OK(cusolverDnCreate(&solver[i]));
+        SOLVER_OK(cusolverDnSetStream(solver[i], streams[i]));
+    }
+    SOLVER_OK(cusolverDnCreateParams(&solver_params));
     const char* pf = getenv("SCTM_PROFILE");
     profile = pf && pf[0] == '1';
-    if (profile) {
-        CUDA_OK(cudaEventCreate(&ev0));
-        CUDA_OK(cudaEventCreate(&ev1));
-    }
 }
 
 Engine::~Engine() {
+    for (int i = 0; i < kStreams; ++i)
+        if (streams[i]) cudaStreamSynchronize(streams[i]);
     for (void* p : allocs_) cudaFree(p);
-    if (solver) cusolverDnDestroy(solver);
-    if (ev0) cudaEventDestroy(ev0);
-    if (ev1) cudaEventDestroy(ev1);
+    for (cudaEvent_t ev : owned_events_) cudaEventDestroy(ev);
+    for (int i = 0; i < kStreams; ++i) {
+        for (cudaEvent_t ev : ev_pool[i]) cudaEventDestroy(ev);
+        if (solver[i]) cusolverDnDestroy(solver[i]);
+        if (i > 0 && streams[i]) cudaStreamDestroy(streams[i]);
+    }
+    if (solver_params) cusolverDnDestroyParams(solver_params);
 }
 
-static char dry_base[64];
+int Engine::record(int sid) {
+    if (ev_used[sid] == ev_pool[sid].size()) {
+        cudaEvent_t ev;
+        CUDA_OK(cudaEventCreate(&ev));
+        ev_pool[sid].push_back(ev);
+    }
+    const int idx = (int)ev_used[sid]++;
+    cudaEventRecord(ev_pool[sid][idx], streams[sid]);
+    return idx;
+}
+
+void Engine::record_done(int sid, int kind, long long flops, int e0) {
+    const int e1 = record(sid);
+    ev_recs[sid].push_back({kind, flops, e0, e1});
+}
+
+void Engine::harvest() {
+    for (int sid = 0; sid < kStreams; ++sid) {
+        for (const EvRec& r : ev_recs[sid]) {
+            float ms = 0;
+            CUDA_OK(cudaEventSynchronize(ev_pool[sid][r.e1]));
+            CUDA_OK(cudaEventElapsedTime(&ms, ev_pool[sid][r.e0], ev_pool[sid][r.e1]));
+            if (r.kind == KIND_CTR) {
+                ctr_ms += ms;
+                ctr_launches += 1;
+                ctr_flops += r.flops;
+            } else {
+                svd_ms += ms;
+                svd_calls += 1;
+            }
+        }
+        ev_recs[sid].clear();
+        ev_used[sid] = 0;
+    }
+}
 
 double* Engine::dalloc(long long n) {
-    if (dry) return (double*)dry_base;
+    if (dry) return (double*)dry_base_;
     void* p = nullptr;
     CUDA_OK(cudaMalloc(&p, std::max<long long>(n, 1) * sizeof(double)));
     allocs_.push_back(p);
@@ -145,7 +214,7 @@ double* Engine::dalloc(long long n) {
 }
 
 int* Engine::ialloc(const std::vector<int>& host) {
-    if (dry) return (int*)dry_base;
+    if (dry) return (int*)dry_base_;
     void* p = nullptr;
     size_t bytes = std::max<size_t>(host.size(), 1) * sizeof(int);
     CUDA_OK(cudaMalloc(&p, bytes));
@@ -155,9 +224,32 @@ int* Engine::ialloc(const std::vector<int>& host) {
     return (int*)p;
 }
 
+void Engine::run_sub(Plan& P) {
+    for (auto& s : P) s->run(*this);
+}
+
+void Engine::parallel(Plan& P, std::vector<Plan>&& sub) {
+    if ((int)sub.size() > kStreams - 1) throw Error(SCTM_EINVAL, "too many parallel sub-plans");
+    auto st = std::make_unique<ParallelStep>();
+    st->sub = std::move(sub);
+    st->sid = 0;
+    if (!dry) {
+        CUDA_OK(cudaEventCreateWithFlags(&st->fork_ev, cudaEventDisableTiming));
+        owned_events_.push_back(st->fork_ev);
+        st->join_ev.resize(st->sub.size());
+        for (auto& ev : st->join_ev) {
+            CUDA_OK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+            owned_events_.push_back(ev);
+        }
+    }
+    P.push_back(std::move(st));
+}
+
 void Engine::run(Plan& P) {
     for (auto& s : P) s->run(*this);
 }
+
+
 
 // offsets of a multi-index group (row-major over `labs`) in a tensor with per-label strides
 static std::vector<int> offsets(const std::string& labs, const std::map<char, int>& dims,
@@ -283,8 +375,8 @@ Ten Engine::ctr(Network& net, Plan& P, const std::string& spec, const Ten& X, co
     }
     st->flops = 2LL * a.M * a.N * (long long)a.K * a.nb;
     net.ctr_steps.push_back(st.get());
-    net.splitk_need = std::max(net.splitk_need, st->partial_need);
-    P.push_back(std::move(st));
+    net.splitk_need[cur_stream] = std::max(net.splitk_need[cur_stream], st->partial_need);
+    push(P, std::move(st));
     return O;
 }
 
@@ -329,40 +421,37 @@ Engine::PPair Engine::projector(Network& net, Plan& P, const Ten& U, const Ten& 
     ctr(net, P, Llab + "," + labels + "->" + rlL + rl, L, U, &M);
     double* S = dalloc(n);
     double* Us = dalloc((long long)n * n);
-    double* VT = dalloc((long long)n * n);
+    double* Vs = dalloc((long long)n * n);
     auto sv = std::make_unique<SvdStep>();
     sv->M = M.p;
     sv->n = n;
     sv->S = S;
     sv->U = Us;
-    sv->VT = VT;
+    sv->V = Vs;
     sv->vectors = true;
     sv->net = &net;
     sv->info_idx = net.n_svd++;
     net.svd_nmax = std::max(net.svd_nmax, n);
     net.svd_steps.push_back(sv.get());
-    P.push_back(std::move(sv));
-    P.push_back(std::make_unique<FnStep>([=](cudaStream_t s) { launch_signfix(Us, VT, n, chi, s); }));
+    push(P, std::move(sv));
+    push(P, std::make_unique<FnStep>([=](cudaStream_t s) { launch_signfix(Us, Vs, n, chi, s); }));
     double* scale = dalloc(chi);
     const double cut = cutoff;
-    P.push_back(std::make_unique<FnStep>(
-        [=](cudaStream_t s) { launch_scalevec(S, chi, cut, scale, s); }));
-    // V[r, c] = VT[c + r n]; Us[r', c] = Us[r' + c n]
+    push(P, std::make_unique<FnStep>([=](cudaStream_t s) { launch_scalevec(S, chi, cut, scale, s); }));
+    // V[r, c] = Vs[r + c n] and Us[r', c] = Us[r' + c n] (column-major singular vectors)
     Ten V, Uv;
-    V.p = VT;
+    V.p = Vs;
     Uv.p = Us;
     V.nd = Uv.nd = (int)rl.size() + 1;
     {
         long long s = 1;
         for (int i = (int)rl.size() - 1; i >= 0; --i) {
             V.dim[i] = Uv.dim[i] = rdims[i];
-            V.st[i] = s * n;
-            Uv.st[i] = s;
+            V.st[i] = Uv.st[i] = s;
             s *= rdims[i];
         }
         V.dim[rl.size()] = Uv.dim[rl.size()] = chi;
-        V.st[rl.size()] = 1;
-        Uv.st[rl.size()] = n;
+        V.st[rl.size()] = Uv.st[rl.size()] = n;
     }
     PPair pp;
     pp.PB = ctr(net, P, labels + "," + rl + K + "->" + tl + K, U, V, nullptr, nullptr, scale);
@@ -479,13 +568,25 @@ static void build_left_move(Engine& e, Network& net, Plan& P, const Frame& f) {
     const Ten La = C("xobYar,yYr->xaoby", X, T2k);
 
     // stage 1: bra-related legs of this column (P1, P2, P3) and the mirror-image pairs of the
-    // opposite boundary on the ket-related legs of the next column
-    const Engine::PPair Pa = e.projector(net, P, Ua, La, "xAOBy", "xB");     // [xl, B_v | k]
-    const Engine::PPair Qa = e.projector(net, P, Ua, La, "xAOBy", "yA");     // [xr, A_v | k]
-    const Engine::PPair Pk = e.projector(net, P, Uk, Lk, "xesoby", "xsb");   // [xl, s, B.u | k]
-    const Engine::PPair Qk = e.projector(net, P, Uk, Lk, "xesoby", "yes");   // [xr, A.d, s | k]
-    const Engine::PPair Pi = e.projector(net, P, Ui, Li, "xeftby", "xtb");   // [xl, s', B.u | k]
-    const Engine::PPair Qi = e.projector(net, P, Ui, Li, "xeftby", "yet");   // [xr, A.d, s' | k]
+    // opposite boundary on the ket-related legs of the next column -- six independent SVD
+    // pipelines, each on its own stream
+    Engine::PPair pr1[6];
+    {
+        const Ten* U[6] = {&Ua, &Ua, &Uk, &Uk, &Ui, &Ui};
+        const Ten* L[6] = {&La, &La, &Lk, &Lk, &Li, &Li};
+        const char* lab[6] = {"xAOBy", "xAOBy", "xesoby", "xesoby", "xeftby", "xeftby"};
+        const char* tl[6] = {"xB", "yA", "xsb", "yes", "xtb", "yet"};
+        std::vector<Plan> sub(6);
+        for (int i = 0; i < 6; ++i) {
+            e.cur_stream = i + 1;
+            pr1[i] = e.projector(net, sub[i], *U[i], *L[i], lab[i], tl[i]);
+        }
+        e.cur_stream = 0;
+        e.parallel(P, std::move(sub));
+    }
+    const Engine::PPair &Pa = pr1[0], &Qa = pr1[1];   // [xl, B_v | k], [xr, A_v | k]
+    const Engine::PPair &Pk = pr1[2], &Qk = pr1[3];   // [xl, s, B.u | k], [xr, A.d, s | k]
+    const Engine::PPair &Pi = pr1[4], &Qi = pr1[5];   // [xl, s', B.u | k], [xr, A.d, s' | k]
 
     // stage 2: two-column patches
     // kappa (1 x 2 cells): (k2, A.d, O.u | O.u', B.u', kR)
@@ -545,9 +646,19 @@ static void build_left_move(Engine& e, Network& net, Plan& P, const Frame& f) {
     const Ten Q3 = C("hbMoLypl,ypk->hlLMobk", X, Qa.PB);
     const Ten L2a = C("hkporRS,hrRSOBK->kpoOBK", Q4, Q3);
 
-    const Engine::PPair P4 = e.projector(net, P, U2a, L2a, "abcdef", "abc");
-    const Engine::PPair P5 = e.projector(net, P, U2k, L2k, "abcdef", "abc");
-    const Engine::PPair P6 = e.projector(net, P, U2i, L2i, "abcdef", "abc");
+    Engine::PPair pr2[3];
+    {
+        const Ten* U[3] = {&U2a, &U2k, &U2i};
+        const Ten* L[3] = {&L2a, &L2k, &L2i};
+        std::vector<Plan> sub(3);
+        for (int i = 0; i < 3; ++i) {
+            e.cur_stream = i + 1;
+            pr2[i] = e.projector(net, sub[i], *U[i], *L[i], "abcdef", "abc");
+        }
+        e.cur_stream = 0;
+        e.parallel(P, std::move(sub));
+    }
+    const Engine::PPair &P4 = pr2[0], &P5 = pr2[1], &P6 = pr2[2];
 
     // composite projector of each cut (stage 1 then stage 2)
     const Ten PaB = C("xbK,Kaok->xaobk", Pa.PB, P4.PB);      // [xl, A_v, O_v, B_v, k]
@@ -594,7 +705,7 @@ static void build_left_move(Engine& e, Network& net, Plan& P, const Frame& f) {
         CUDA_OK(cudaMemcpy(dev, items.data(), items.size() * sizeof(NormItem),
                            cudaMemcpyHostToDevice));
     const int cnt = (int)items.size();
-    P.push_back(std::make_unique<FnStep>([=](cudaStream_t s) { launch_normalize(dev, cnt, s); }));
+    e.push(P, std::make_unique<FnStep>([=](cudaStream_t s) { launch_normalize(dev, cnt, s); }));
 }
 
 // convergence check (Sec. III.D): singular values of rho_eff = C1 C2 C3 C4 / Tr
@@ -607,23 +718,23 @@ static void build_spectrum(Engine& e, Network& net) {
     double* work = e.dalloc((long long)chi * chi);
     double* Sraw = e.dalloc(chi);
     double* rho_p = rho.p;
-    P.push_back(std::make_unique<FnStep>(
+    e.push(P, std::make_unique<FnStep>(
         [=](cudaStream_t s) { launch_copy(rho_p, work, (long long)chi * chi, s); }));
     auto sv = std::make_unique<SvdStep>();
     sv->M = work;
     sv->n = chi;
     sv->S = Sraw;
     sv->U = work;
-    sv->VT = work;
+    sv->V = work;
     sv->vectors = false;
     sv->net = &net;
     sv->info_idx = net.n_svd++;
     net.svd_nmax = std::max(net.svd_nmax, chi);
     net.svd_steps.push_back(sv.get());
-    P.push_back(std::move(sv));
+    e.push(P, std::move(sv));
     double* S_old = net.S_old;
     double* dS = net.dS;
-    P.push_back(std::make_unique<FnStep>(
+    e.push(P, std::make_unique<FnStep>(
         [=](cudaStream_t s) { launch_spectrum_update(Sraw, rho_p, chi, S_old, dS, s); }));
 }
 
@@ -681,7 +792,7 @@ static void build_local(Engine& e, Network& net) {
     net.z[1] = z10;
     net.z[2] = z01;
     net.z[3] = z11;
-    P.push_back(std::make_unique<FnStep>(
+    e.push(P, std::make_unique<FnStep>(
         [=](cudaStream_t s) { launch_lnkappa(z00, z10, z01, z11, lnk, s); }));
 }
 
@@ -715,22 +826,31 @@ void Engine::build_network(Network& net) {
 }
 
 void Engine::finalize(Network& net) {
-    if (net.splitk_need > 0) {
-        net.splitk_ws = dalloc((long long)net.splitk_need);
-        for (CtrStep* s : net.ctr_steps)
-            if (s->a.splits > 1) s->a.partial = net.splitk_ws;
-    }
-    int lwork = 0;
-    if (dry) return;
-    SOLVER_OK(cusolverDnDgesvd_bufferSize(solver, net.svd_nmax, net.svd_nmax, &lwork));
-    net.svd_lwork = std::max(lwork, 1);
-    net.svd_work = dalloc(net.svd_lwork);
-    net.svd_rwork = dalloc(net.svd_nmax);
+    for (int k = 0; k < kStreams; ++k)
+        if (net.splitk_need[k] > 0) net.splitk_ws[k] = dalloc((long long)net.splitk_need[k]);
+    for (CtrStep* s : net.ctr_steps)
+        if (s->a.splits > 1) s->a.partial = net.splitk_ws[s->sid];
     void* p = nullptr;
-    CUDA_OK(cudaMalloc(&p, std::max(net.n_svd, 1) * sizeof(int)));
-    allocs_.push_back(p);
-    CUDA_OK(cudaMemset(p, 0, std::max(net.n_svd, 1) * sizeof(int)));
+    if (!dry) {
+        CUDA_OK(cudaMalloc(&p, std::max(net.n_svd, 1) * sizeof(int)));
+        allocs_.push_back(p);
+        CUDA_OK(cudaMemset(p, 0, std::max(net.n_svd, 1) * sizeof(int)));
+    }
     net.svd_info = (int*)p;
+    if (dry) return;
+    const int n = net.svd_nmax;
+    double* A = dalloc((long long)n * n);
+    double* S = dalloc(n);
+    size_t dbytes = 0, hbytes = 0;
+    SOLVER_OK(cusolverDnXgesvdp_bufferSize(solver[0], solver_params, CUSOLVER_EIG_MODE_VECTOR, 1, n,
+                                           n, CUDA_R_64F, A, n, CUDA_R_64F, S, CUDA_R_64F, A, n,
+                                           CUDA_R_64F, A, n, CUDA_R_64F, &dbytes, &hbytes));
+    net.svd_dbytes = std::max<size_t>(dbytes, 8);
+    net.svd_hbytes = std::max<size_t>(hbytes, 8);
+    for (int k = 0; k < kStreams; ++k) {
+        net.svd_dwork[k] = dalloc((long long)(net.svd_dbytes + 7) / 8);
+        net.svd_hwork[k].assign(net.svd_hbytes, 0);
+    }
 }
 
 }  // namespace sctm

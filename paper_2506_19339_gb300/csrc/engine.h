@@ -1,7 +1,10 @@
 // Plan builder and executor of the split-CTMRG runtime.
 #pragma once
 
+#include <atomic>
+#include <functional>
 #include <memory>
+#include <thread>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -34,7 +37,10 @@ Ten permute(const Ten& t, const std::vector<int>& perm);           // out axis k
 
 class Engine;
 
+constexpr int kStreams = 7;  // stream 0 = the caller's stream; 1..6 run independent projectors
+
 struct Step {
+    int sid = 0;  // stream index
     virtual ~Step() = default;
     virtual void run(Engine& e) = 0;
 };
@@ -56,12 +62,13 @@ struct Network {
     Ten E;                    // bra environment, layout of A
     int* svd_info = nullptr;  // one int per SVD step
     int n_svd = 0;
-    // per-network work buffers, sized after the plans are built
-    double* splitk_ws = nullptr;
-    size_t splitk_need = 0;
-    double* svd_work = nullptr;
-    int svd_lwork = 0;
-    double* svd_rwork = nullptr;
+    // per-network, per-stream work buffers, sized after the plans are built
+    double* splitk_ws[kStreams] = {nullptr};
+    size_t splitk_need[kStreams] = {0};
+    void* svd_dwork[kStreams] = {nullptr};
+    size_t svd_dbytes = 0;
+    std::vector<char> svd_hwork[kStreams];
+    size_t svd_hbytes = 0;
     int svd_nmax = 1;
     std::vector<struct CtrStep*> ctr_steps;
     std::vector<struct SvdStep*> svd_steps;
@@ -74,15 +81,28 @@ public:
     Engine(const Engine&) = delete;
     Engine& operator=(const Engine&) = delete;
 
-    cudaStream_t stream;
-    cusolverDnHandle_t solver = nullptr;
+    cudaStream_t stream;                     // == streams[0]
+    cudaStream_t streams[kStreams] = {nullptr};
+    cusolverDnHandle_t solver[kStreams] = {nullptr};
+    cusolverDnParams_t solver_params = nullptr;
     int precision;
     double cutoff;
-    bool profile = false;
     bool dry = false;  // SCTM_DRYRUN=1: build plans with placeholder pointers, no CUDA calls
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    int cur_stream = 0;  // stream index given to steps while a plan is being built
+
+    // timing: events recorded around every contraction and SVD without host synchronisation,
+    // harvested (summed) after each iteration
+    bool profile = false;
+    struct EvRec { int kind; long long flops; int e0, e1; };
+    std::vector<cudaEvent_t> ev_pool[kStreams];
+    size_t ev_used[kStreams] = {0};
+    std::vector<EvRec> ev_recs[kStreams];
     double ctr_ms = 0, svd_ms = 0;
-    long long ctr_launches = 0, ctr_flops = 0;
+    long long ctr_launches = 0, ctr_flops = 0, svd_calls = 0;
+    std::atomic<long long> kernel_launches{0};  // own kernels only (cuSOLVER's are not counted)
+    int record(int sid);                                       // event index in pool sid
+    void record_done(int sid, int kind, long long flops, int e0);
+    void harvest();
 
     double* dalloc(long long n);                   // tracked, zero-filled device buffer
     int* ialloc(const std::vector<int>& host);     // tracked device copy of an int table
@@ -113,9 +133,19 @@ public:
     void finalize(Network& net);
     void run(Plan& P);
     void init_env(Network& net, unsigned long long seed);
+    // Independent sub-plans, each on its own stream and host thread (stream i+1 for sub[i]):
+    // they start after everything already on stream 0 and stream 0 waits for all of them.
+    void parallel(Plan& P, std::vector<Plan>&& sub);
+    void push(Plan& P, std::unique_ptr<Step> st) {
+        st->sid = cur_stream;
+        P.push_back(std::move(st));
+    }
+    void run_sub(Plan& P);
 
 private:
     std::vector<void*> allocs_;
+    std::vector<cudaEvent_t> owned_events_;
+    char dry_base_[64] = {0};
 };
 
 }  // namespace sctm

@@ -225,8 +225,9 @@ void launch_scalevec(const double* S, int k, double cutoff, double* out, cudaStr
 }
 
 // SVD sign gauge: flip (u_c, v_c) so that the largest-magnitude entry of u_c (first index on a
-// tie) is positive.  U and VT are n x n column-major (cuSOLVER layout); one CTA per column.
-__global__ void signfix_kernel(double* U, double* VT, int n) {
+// tie) is positive.  U and V are n x n column-major with the singular vectors as columns (cuSOLVER
+// layout); one CTA per column.
+__global__ void signfix_kernel(double* U, double* V, int n) {
     const int c = blockIdx.x;
     double* u = U + (long long)c * n;
     double best = -1.0;
@@ -255,14 +256,15 @@ __global__ void signfix_kernel(double* U, double* VT, int n) {
     const bool flip = (imax < n) && (u[imax] < 0.0);
     __syncthreads();
     if (!flip) return;
+    double* v = V + (long long)c * n;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         u[i] = -u[i];
-        VT[c + (long long)i * n] = -VT[c + (long long)i * n];
+        v[i] = -v[i];
     }
 }
 
-void launch_signfix(double* U, double* VT, int n, int k, cudaStream_t s) {
-    signfix_kernel<<<k, 256, 0, s>>>(U, VT, n);
+void launch_signfix(double* U, double* V, int n, int k, cudaStream_t s) {
+    signfix_kernel<<<k, 256, 0, s>>>(U, V, n);
 }
 
 __global__ void copy_kernel(const double* src, double* dst, long long n) {

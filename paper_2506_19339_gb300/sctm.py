@@ -67,7 +67,9 @@ def load():
         'sctm_move': (I, [P, I, I]),
         'sctm_spectrum': (I, [P, I, P]),
         'sctm_local_values': (I, [P, I, P]),
-        'sctm_profile': (I, [P, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D),
+        'sctm_set_profiling': (I, [P, I]),
+        'sctm_profile': (I, [P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong),
+                             ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(D),
                              ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
                              I]),
     }
@@ -171,13 +173,17 @@ def sctm_local_values(ctx, network):
     return st, out
 
 
+def sctm_set_profiling(ctx, on):
+    return load().sctm_set_profiling(ctx, int(bool(on)))
+
+
 def sctm_profile(ctx, reset=False):
-    v = [ctypes.c_double(0), ctypes.c_double(0), ctypes.c_double(0)]
-    n = [ctypes.c_longlong(0), ctypes.c_longlong(0)]
-    st = load().sctm_profile(ctx, *[ctypes.byref(x) for x in v], *[ctypes.byref(x) for x in n],
-                             int(reset))
-    return st, {'ctr_ms': v[0].value, 'svd_ms': v[1].value, 'total_ms': v[2].value,
-                'ctr_launches': n[0].value, 'ctr_flops': n[1].value}
+    ctr_ms, svd_ms = ctypes.c_double(0), ctypes.c_double(0)
+    cl, cf, sc_, kl = (ctypes.c_longlong(0) for _ in range(4))
+    st = load().sctm_profile(ctx, ctypes.byref(ctr_ms), ctypes.byref(cl), ctypes.byref(cf),
+                             ctypes.byref(svd_ms), ctypes.byref(sc_), ctypes.byref(kl), int(reset))
+    return st, {'ctr_ms': ctr_ms.value, 'ctr_launches': cl.value, 'ctr_flops': cf.value,
+                'svd_ms': svd_ms.value, 'svd_calls': sc_.value, 'kernel_launches': kl.value}
 
 
 def unpack_env(buf, chi, D, d):
