@@ -38,6 +38,8 @@ def parse():
     ap.add_argument('--tol', type=float, default=1e-10)
     ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
     ap.add_argument('--no-cpu-baseline', action='store_true')
+    ap.add_argument('--svd', default='qr', choices=['qr', 'polar'],
+                    help='FP64 SVD of the projectors: cuSOLVER gesvd (qr) or gesvdp (polar)')
     return ap.parse_args()
 
 
@@ -202,6 +204,7 @@ def run_ours(args):
     st, o = sctm.sctm_default_opts()
     o.T, o.D, o.p, o.d = w['T'], w['D'], 2, 2
     o.cuda_stream = stream.cuda_stream
+    o.svd_mode = sctm.SCTM_SVD_POLAR if args.svd == 'polar' else sctm.SCTM_SVD_QR
     A_dev = torch.from_numpy(A_host).to(dev)
     st, ctx = sctm.sctm_create(A_dev, np.ascontiguousarray(O), w['chi'], o)
     if st != sctm.SCTM_OK:
@@ -319,7 +322,8 @@ def run_ours(args):
         'data': 'synthetic',
         'config': {'workload': workload_name(args.iters), 'D': w['D'], 'chi': w['chi'],
                    'T': w['T'], 'seed': w['seed'], 'iterations_per_eval': args.iters,
-                   'precision': 'FP64 contractions, FP64 SVD', 'parallelism': 'replicas',
+                   'precision': 'FP64 contractions, FP64 SVD (%s)' % ('cuSOLVER gesvdp' if args.svd == 'polar' else 'cuSOLVER gesvd'),
+                   'parallelism': 'replicas',
                    'l2': 'flushed before every step (256 MiB write, outside the step events)'},
         'iterations_per_s': total_its * world / (ms * 1e-3),
         'f': fs[-1], 'status': [sctm.STATUS_NAMES[s] for s in statuses][-1],

@@ -100,6 +100,7 @@ sctm_status sctm_default_opts(sctm_opts* o) {
     o->init_seed = 0;
     o->batch = 1;
     o->cuda_stream = nullptr;
+    o->svd_mode = SCTM_SVD_QR;
     return SCTM_OK;
 }
 
@@ -132,7 +133,8 @@ sctm_status sctm_create(const double* peps, const double* pepo, int chi, const s
     if (o) opts = *o; else sctm_default_opts(&opts);
     if (chi < 1 || chi > 4096 || opts.D < 1 || opts.p < 1 || opts.d < 1 || opts.batch != 1 ||
         opts.precision != SCTM_PREC_FP64 || opts.grad_mode != SCTM_GRAD_ENV ||
-        !(opts.svd_cutoff >= 0.0) || opts.D > 64 || opts.d > 64 || opts.p > 64)
+        !(opts.svd_cutoff >= 0.0) || opts.D > 64 || opts.d > 64 || opts.p > 64 ||
+        (opts.svd_mode != SCTM_SVD_QR && opts.svd_mode != SCTM_SVD_POLAR))
         return SCTM_EINVAL;
     std::unique_ptr<sctm_ctx> c(new sctm_ctx());
     c->opts = opts;
@@ -140,6 +142,7 @@ sctm_status sctm_create(const double* peps, const double* pepo, int chi, const s
     try {
         cudaStream_t s = (cudaStream_t)opts.cuda_stream;
         c->eng.reset(new Engine(s, opts.precision, opts.svd_cutoff));
+        c->eng->svd_mode = opts.svd_mode;
         Engine& e = *c->eng;
         const long long na = peps_size(opts), no = pepo_size(opts);
         c->A_dev = e.dalloc(na);

@@ -76,21 +76,29 @@ struct SvdStep : Step {
     int n = 0;
     double* S = nullptr;
     double* U = nullptr;
-    double* V = nullptr;  // right singular vectors as columns (n x n, column-major)
+    double* V = nullptr;  // right singular vectors: columns (polar) or rows = V^T (QR)
     bool vectors = true;
     Network* net = nullptr;
     int info_idx = 0;
     void run(Engine& e) override {
         const int e0 = e.profile ? e.record(sid) : -1;
-        double herr = 0.0;
-        cusolverStatus_t st = cusolverDnXgesvdp(
-            e.solver[sid], e.solver_params,
-            vectors ? CUSOLVER_EIG_MODE_VECTOR : CUSOLVER_EIG_MODE_NOVECTOR, 1, n, n, CUDA_R_64F, M,
-            n, CUDA_R_64F, S, CUDA_R_64F, U, n, CUDA_R_64F, V, n, CUDA_R_64F, net->svd_dwork[sid],
-            net->svd_dbytes, net->svd_hwork[sid].data(), net->svd_hbytes,
-            net->svd_info + info_idx, &herr);
+        cusolverStatus_t st;
+        if (e.svd_mode == SCTM_SVD_POLAR) {
+            double herr = 0.0;
+            st = cusolverDnXgesvdp(e.solver[sid], e.solver_params,
+                                   vectors ? CUSOLVER_EIG_MODE_VECTOR : CUSOLVER_EIG_MODE_NOVECTOR, 1,
+                                   n, n, CUDA_R_64F, M, n, CUDA_R_64F, S, CUDA_R_64F, U, n,
+                                   CUDA_R_64F, V, n, CUDA_R_64F, net->svd_dwork[sid],
+                                   net->svd_dbytes, net->svd_hwork[sid].data(), net->svd_hbytes,
+                                   net->svd_info + info_idx, &herr);
+        } else {  // gesvd writes V^T into V
+            const signed char job = vectors ? 'S' : 'N';
+            st = cusolverDnDgesvd(e.solver[sid], job, job, n, n, M, n, S, U, n, V, n,
+                                  (double*)net->svd_dwork[sid], net->svd_lwork, net->svd_rwork[sid],
+                                  net->svd_info + info_idx);
+        }
         if (st != CUSOLVER_STATUS_SUCCESS)
-            throw Error(SCTM_ECUSOLVER, "cusolverDnXgesvdp failed: " + std::to_string(st));
+            throw Error(SCTM_ECUSOLVER, "cuSOLVER SVD failed: " + std::to_string(st));
         if (e.profile) e.record_done(sid, KIND_SVD, 0, e0);
     }
 };
@@ -434,11 +442,13 @@ Engine::PPair Engine::projector(Network& net, Plan& P, const Ten& U, const Ten& 
     net.svd_nmax = std::max(net.svd_nmax, n);
     net.svd_steps.push_back(sv.get());
     push(P, std::move(sv));
-    push(P, std::make_unique<FnStep>([=](cudaStream_t s) { launch_signfix(Us, Vs, n, chi, s); }));
+    const int vt = svd_mode == SCTM_SVD_POLAR ? 0 : 1;  // gesvd returns V^T
+    push(P, std::make_unique<FnStep>(
+        [=](cudaStream_t s) { launch_signfix(Us, Vs, n, chi, vt, s); }));
     double* scale = dalloc(chi);
     const double cut = cutoff;
     push(P, std::make_unique<FnStep>([=](cudaStream_t s) { launch_scalevec(S, chi, cut, scale, s); }));
-    // V[r, c] = Vs[r + c n] and Us[r', c] = Us[r' + c n] (column-major singular vectors)
+    // Us[r', c] = Us[r' + c n]; V[r, c] = Vs[r + c n] (polar) or Vs[c + r n] (QR: V^T)
     Ten V, Uv;
     V.p = Vs;
     Uv.p = Us;
@@ -447,11 +457,13 @@ Engine::PPair Engine::projector(Network& net, Plan& P, const Ten& U, const Ten& 
         long long s = 1;
         for (int i = (int)rl.size() - 1; i >= 0; --i) {
             V.dim[i] = Uv.dim[i] = rdims[i];
-            V.st[i] = Uv.st[i] = s;
+            Uv.st[i] = s;
+            V.st[i] = vt ? s * n : s;
             s *= rdims[i];
         }
         V.dim[rl.size()] = Uv.dim[rl.size()] = chi;
-        V.st[rl.size()] = Uv.st[rl.size()] = n;
+        Uv.st[rl.size()] = n;
+        V.st[rl.size()] = vt ? 1 : n;
     }
     PPair pp;
     pp.PB = ctr(net, P, labels + "," + rl + K + "->" + tl + K, U, V, nullptr, nullptr, scale);
@@ -845,10 +857,14 @@ void Engine::finalize(Network& net) {
     SOLVER_OK(cusolverDnXgesvdp_bufferSize(solver[0], solver_params, CUSOLVER_EIG_MODE_VECTOR, 1, n,
                                            n, CUDA_R_64F, A, n, CUDA_R_64F, S, CUDA_R_64F, A, n,
                                            CUDA_R_64F, A, n, CUDA_R_64F, &dbytes, &hbytes));
-    net.svd_dbytes = std::max<size_t>(dbytes, 8);
+    int lwork = 0;
+    SOLVER_OK(cusolverDnDgesvd_bufferSize(solver[0], n, n, &lwork));
+    net.svd_lwork = std::max(lwork, 1);
+    net.svd_dbytes = std::max<size_t>(std::max<size_t>(dbytes, 8), (size_t)net.svd_lwork * 8);
     net.svd_hbytes = std::max<size_t>(hbytes, 8);
     for (int k = 0; k < kStreams; ++k) {
         net.svd_dwork[k] = dalloc((long long)(net.svd_dbytes + 7) / 8);
+        net.svd_rwork[k] = dalloc(n);
         net.svd_hwork[k].assign(net.svd_hbytes, 0);
     }
 }

@@ -67,6 +67,8 @@ struct Network {
     size_t splitk_need[kStreams] = {0};
     void* svd_dwork[kStreams] = {nullptr};
     size_t svd_dbytes = 0;
+    int svd_lwork = 0;                        // gesvd workspace in doubles (inside svd_dwork)
+    double* svd_rwork[kStreams] = {nullptr};  // gesvd rwork
     std::vector<char> svd_hwork[kStreams];
     size_t svd_hbytes = 0;
     int svd_nmax = 1;
@@ -87,6 +89,7 @@ public:
     cusolverDnParams_t solver_params = nullptr;
     int precision;
     double cutoff;
+    int svd_mode = SCTM_SVD_QR;
     bool dry = false;  // SCTM_DRYRUN=1: build plans with placeholder pointers, no CUDA calls
     int cur_stream = 0;  // stream index given to steps while a plan is being built
 

@@ -227,7 +227,7 @@ void launch_scalevec(const double* S, int k, double cutoff, double* out, cudaStr
 // SVD sign gauge: flip (u_c, v_c) so that the largest-magnitude entry of u_c (first index on a
 // tie) is positive.  U and V are n x n column-major with the singular vectors as columns (cuSOLVER
 // layout); one CTA per column.
-__global__ void signfix_kernel(double* U, double* V, int n) {
+__global__ void signfix_kernel(double* U, double* V, int n, int vt) {
     const int c = blockIdx.x;
     double* u = U + (long long)c * n;
     double best = -1.0;
@@ -256,15 +256,16 @@ __global__ void signfix_kernel(double* U, double* V, int n) {
     const bool flip = (imax < n) && (u[imax] < 0.0);
     __syncthreads();
     if (!flip) return;
-    double* v = V + (long long)c * n;
+    // right vector c: column c of V, or row c of V^T (gesvd layout, column-major)
+    const long long v0 = vt ? c : (long long)c * n, vs = vt ? n : 1;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         u[i] = -u[i];
-        v[i] = -v[i];
+        V[v0 + i * vs] = -V[v0 + i * vs];
     }
 }
 
-void launch_signfix(double* U, double* V, int n, int k, cudaStream_t s) {
-    signfix_kernel<<<k, 256, 0, s>>>(U, V, n);
+void launch_signfix(double* U, double* V, int n, int k, int vt, cudaStream_t s) {
+    signfix_kernel<<<k, 256, 0, s>>>(U, V, n, vt);
 }
 
 __global__ void copy_kernel(const double* src, double* dst, long long n) {

@@ -56,7 +56,8 @@ void launch_normalize(const NormItem* items_dev, int count, cudaStream_t s);
 void launch_splitmix_fill(double* p, long long n, unsigned long long seed, unsigned long long slot,
                           cudaStream_t s);
 void launch_scalevec(const double* S, int k, double cutoff, double* out, cudaStream_t s);
-void launch_signfix(double* U, double* V, int n, int k, cudaStream_t s);
+// vt = 1: V holds V^T (gesvd layout); vt = 0: V holds the right vectors as columns
+void launch_signfix(double* U, double* V, int n, int k, int vt, cudaStream_t s);
 void launch_copy(const double* src, double* dst, long long n, cudaStream_t s);
 void launch_zero(double* p, long long n, cudaStream_t s);
 // flag[0] = 1 if any of p[0..n) is NaN or infinite, else 0

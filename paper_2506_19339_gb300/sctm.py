@@ -18,6 +18,7 @@ STATUS_NAMES = ['SCTM_OK', 'SCTM_EINVAL', 'SCTM_ECUDA', 'SCTM_ECUSOLVER', 'SCTM_
                 'SCTM_ENOCONV', 'SCTM_ENUMERIC', 'SCTM_ETIMEOUT']
 SCTM_PREC_FP64, SCTM_PREC_TF32, SCTM_PREC_TF32X3, SCTM_PREC_BF16, SCTM_PREC_BF16X3 = range(5)
 SCTM_GRAD_ENV, SCTM_GRAD_ADJOINT = 0, 1
+SCTM_SVD_QR, SCTM_SVD_POLAR = 0, 1
 SCTM_NET_NUM, SCTM_NET_DEN = 0, 1
 SCTM_MOVE_LEFT, SCTM_MOVE_RIGHT, SCTM_MOVE_UP, SCTM_MOVE_DOWN = range(4)
 
@@ -26,7 +27,8 @@ class SctmOpts(ctypes.Structure):
     _fields_ = [('T', ctypes.c_double), ('D', ctypes.c_int), ('p', ctypes.c_int),
                 ('d', ctypes.c_int), ('precision', ctypes.c_int), ('grad_mode', ctypes.c_int),
                 ('svd_cutoff', ctypes.c_double), ('init_seed', ctypes.c_ulonglong),
-                ('batch', ctypes.c_int), ('cuda_stream', ctypes.c_void_p)]
+                ('batch', ctypes.c_int), ('cuda_stream', ctypes.c_void_p),
+                ('svd_mode', ctypes.c_int)]
 
 
 class SctmError(RuntimeError):
@@ -205,11 +207,13 @@ def unpack_env(buf, chi, D, d):
 class SplitCTMRG:
     """Convenience owner of one context: create / iterate / f / g / destroy."""
 
-    def __init__(self, peps, pepo, chi, T, precision=SCTM_PREC_FP64, cutoff=1e-12, seed=0):
+    def __init__(self, peps, pepo, chi, T, precision=SCTM_PREC_FP64, cutoff=1e-12, seed=0,
+                 svd_mode=SCTM_SVD_QR):
         st, o = sctm_default_opts()
         p, D = peps.shape[0], peps.shape[1]
         o.T, o.D, o.p, o.d = float(T), D, p, pepo.shape[2]
         o.precision, o.svd_cutoff, o.init_seed = precision, cutoff, seed
+        o.svd_mode = svd_mode
         self.chi, self.D, self.p, self.d = chi, D, p, pepo.shape[2]
         st, self.ctx = sctm_create(np.ascontiguousarray(peps, dtype=np.float64),
                                    np.ascontiguousarray(pepo, dtype=np.float64), chi, o)

@@ -196,3 +196,20 @@ def test_chi_one_and_d1():
     f, g, *_ = _run(A, T, 1, 3)
     ref = _oracle(A, T, 1, 3)
     assert abs(f - ref['f']) <= 1e-10 * abs(ref['f'])
+
+
+def test_polar_svd_mode():
+    """SCTM_SVD_POLAR (cuSOLVER gesvdp) against the oracle's LAPACK SVD on the contractive
+    D=2, chi=16 case: same singular values, less accurate small-s vectors, hence looser bounds."""
+    T, chi, iters = 4.6, 16, 40
+    A = inputs.perturbed_product_peps(2, 7)
+    st, O = sctm.sctm_ising_pepo(T)
+    r = sctm.SplitCTMRG(A, O, chi, T, svd_mode=sctm.SCTM_SVD_POLAR)
+    try:
+        r.iterate(iters)
+        f, g = r.free_energy(), r.grad()
+    finally:
+        r.close()
+    ref = _oracle(A, T, chi, iters)
+    assert abs(f - ref['f']) <= 1e-8 * abs(ref['f']), (f, ref['f'])
+    assert _rel(g, ref['g']) <= 1e-5
