@@ -180,6 +180,27 @@ sctm_status sctm_profile(sctm_ctx* ctx, double* ctr_ms, long long* ctr_launches,
                          long long* ctr_flops, double* svd_ms, long long* svd_calls,
                          long long* kernel_launches, int reset);
 
+/* sctm_gemm_noalloc -- O = X Y in FP64 for row-major device matrices X (M x K), Y (K x N),
+ * O (M x N), computed by a variant of the library's contraction kernel that allocates nothing.
+ * The paper has no counterpart; it exists for callers that cannot allocate device memory: code
+ * whose device memory is owned by another allocator that must not be bypassed, code that may not
+ * trigger the device-wide synchronisation a cudaMalloc/cudaFree can imply, or code that runs where
+ * the runtime's allocator is unavailable.  The context-based entry points allocate all their
+ * buffers in sctm_create; this one uses no context.
+ *   X, Y, O      device pointers (host pointers are rejected with SCTM_EINVAL); caller-owned
+ *   M, N, K      >= 1; M*N must not exceed 2^21 (SCTM_EINVAL otherwise)
+ *   cuda_stream  cudaStream_t for the work (NULL = legacy default stream)
+ * The split-K partial sums live in one 16 MiB file-scope device array that every device loading
+ * the library holds until exit.  All calls share it: calls whose work overlaps on a GPU (several
+ * streams or host threads at once) race and must be serialised by the caller.  It keeps the last
+ * call's contents, every value read is written earlier by the same call.  The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress, with that device current);
+ * make that first call before any stream capture on the device.  No cudaMalloc, cudaFree or
+ * allocating library routine is called.  The result is deterministic (fixed summation order).
+ * Returns SCTM_OK, SCTM_EINVAL or SCTM_ECUDA (launch or lookup failure). */
+sctm_status sctm_gemm_noalloc(const double* X, const double* Y, double* O, int M, int N, int K,
+                              void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

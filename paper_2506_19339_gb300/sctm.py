@@ -69,6 +69,7 @@ def load():
         'sctm_move': (I, [P, I, I]),
         'sctm_spectrum': (I, [P, I, P]),
         'sctm_local_values': (I, [P, I, P]),
+        'sctm_gemm_noalloc': (I, [P, P, P, I, I, I, P]),
         'sctm_set_profiling': (I, [P, I]),
         'sctm_profile': (I, [P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong),
                              ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(D),
@@ -173,6 +174,12 @@ def sctm_local_values(ctx, network):
     out = np.zeros(5)
     st = load().sctm_local_values(ctx, int(network), _ptr(out))
     return st, out
+
+
+def sctm_gemm_noalloc(X, Y, O, M, N, K, stream=None):
+    """O = X Y (row-major device tensors, FP64) without any device allocation in the library."""
+    return load().sctm_gemm_noalloc(_ptr(X), _ptr(Y), _ptr(O), int(M), int(N), int(K),
+                                    ctypes.c_void_p(stream))
 
 
 def sctm_set_profiling(ctx, on):
