@@ -3,6 +3,7 @@
 #include <cstring>
 #include <memory>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "engine.h"
@@ -21,7 +22,12 @@ struct sctm_ctx {
     double* f_dev = nullptr;
     double* g_dev = nullptr;
     int* flag_dev = nullptr;
+    cudaEvent_t lane_fork = nullptr, lane_join = nullptr;
     std::string err;
+    ~sctm_ctx() {
+        if (lane_fork) cudaEventDestroy(lane_fork);
+        if (lane_join) cudaEventDestroy(lane_join);
+    }
     bool converged = true;
 };
 
@@ -181,6 +187,8 @@ sctm_status sctm_create(const double* peps, const double* pepo, int chi, const s
             c.reset();
             return SCTM_OK;
         }
+        cuda_ok(cudaEventCreateWithFlags(&c->lane_fork, cudaEventDisableTiming), "event");
+        cuda_ok(cudaEventCreateWithFlags(&c->lane_join, cudaEventDisableTiming), "event");
         cuda_ok(cudaDeviceSynchronize(), "plan build");
         for (int n = 0; n < 2; ++n) e.init_env(c->net[n], opts.init_seed);
         cuda_ok(cudaStreamSynchronize(s), "cold start");
@@ -217,32 +225,54 @@ sctm_status sctm_iterate(sctm_ctx* ctx, int max_it, double tol, int* it_done, do
     API_BEGIN(ctx)
     if (max_it < 0) throw Error(SCTM_EINVAL, "max_it < 0");
     Engine& e = *ctx->eng;
-    int it_max = 0;
-    double dS_max = 0.0;
-    bool conv = true;
-    for (int n = 0; n < 2; ++n) {
-        Network& net = ctx->net[n];
-        double dS = INFINITY;
-        int it = 0;
-        for (it = 1; it <= max_it; ++it) {
-            for (int m = 0; m < 4; ++m) e.run(net.move[m]);
-            e.run(net.spectrum);
-            check_cuda("iteration");
-            if (e.profile) e.harvest();
-            cuda_ok(cudaMemcpyAsync(&dS, net.dS, sizeof(double), cudaMemcpyDeviceToHost, e.stream),
-                    "dS copy");
-            cuda_ok(cudaStreamSynchronize(e.stream), "iteration sync");
-            if (!std::isfinite(dS)) throw Error(SCTM_ENUMERIC, "non-finite spectrum change");
-            if (tol > 0.0 && dS < tol) break;
+    // The two networks are independent: the norm network runs on lane 1 from a second host
+    // thread, ordered after everything already on the caller's stream and joined back into it.
+    int its[2] = {0, 0};
+    double dss[2] = {0.0, 0.0};
+    std::exception_ptr errs[2];
+    auto drive = [&](int n) {
+        try {
+            Engine::cur_lane = n;
+            Network& net = ctx->net[n];
+            cudaStream_t s0 = e.lane().streams[0];
+            double dS = INFINITY;
+            int it = 0;
+            for (it = 1; it <= max_it; ++it) {
+                for (int m = 0; m < 4; ++m) e.run(net.move[m]);
+                e.run(net.spectrum);
+                check_cuda("iteration");
+                cuda_ok(cudaMemcpyAsync(&dS, net.dS, sizeof(double), cudaMemcpyDeviceToHost, s0),
+                        "dS copy");
+                cuda_ok(cudaStreamSynchronize(s0), "iteration sync");
+                if (!std::isfinite(dS)) throw Error(SCTM_ENUMERIC, "non-finite spectrum change");
+                if (tol > 0.0 && dS < tol) break;
+            }
+            its[n] = std::min(it, max_it);
+            dss[n] = dS;
+        } catch (...) {
+            errs[n] = std::current_exception();
         }
-        if (it > max_it) it = max_it;
-        if (tol > 0.0 && !(dS < tol)) conv = false;
-        it_max = std::max(it_max, it);
-        if (std::isfinite(dS)) dS_max = std::max(dS_max, dS);
-    }
+        Engine::cur_lane = 0;
+    };
+    cuda_ok(cudaEventRecord(ctx->lane_fork, e.stream), "fork");
+    cuda_ok(cudaStreamWaitEvent(e.lanes[1].streams[0], ctx->lane_fork, 0), "fork wait");
+    std::thread t1(drive, 1);
+    drive(0);
+    t1.join();
+    cuda_ok(cudaEventRecord(ctx->lane_join, e.lanes[1].streams[0]), "join");
+    cuda_ok(cudaStreamWaitEvent(e.stream, ctx->lane_join, 0), "join wait");
+    for (auto& x : errs)
+        if (x) std::rethrow_exception(x);
+    if (e.profile) e.harvest();
     check_svd_info(ctx);
+    bool conv = true;
+    double dS_max = 0.0;
+    for (int n = 0; n < 2; ++n) {
+        if (tol > 0.0 && !(dss[n] < tol)) conv = false;
+        if (std::isfinite(dss[n])) dS_max = std::max(dS_max, dss[n]);
+    }
     ctx->converged = conv;
-    if (it_done) *it_done = it_max;
+    if (it_done) *it_done = std::max(its[0], its[1]);
     if (last_dS) *last_dS = dS_max;
     if (!conv) {
         ctx->err = "iteration limit reached before convergence";

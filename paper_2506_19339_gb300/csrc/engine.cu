@@ -65,7 +65,7 @@ struct CtrStep : Step {
     long long flops = 0;
     void run(Engine& e) override {
         const int e0 = e.profile ? e.record(sid) : -1;
-        launch_ctr(a, e.streams[sid]);
+        launch_ctr(a, e.lane().streams[sid]);
         e.kernel_launches += a.splits > 1 ? 2 : 1;
         if (e.profile) e.record_done(sid, KIND_CTR, flops, e0);
     }
@@ -85,7 +85,7 @@ struct SvdStep : Step {
         cusolverStatus_t st;
         if (e.svd_mode == SCTM_SVD_POLAR) {
             double herr = 0.0;
-            st = cusolverDnXgesvdp(e.solver[sid], e.solver_params,
+            st = cusolverDnXgesvdp(e.lane().solver[sid], e.solver_params,
                                    vectors ? CUSOLVER_EIG_MODE_VECTOR : CUSOLVER_EIG_MODE_NOVECTOR, 1,
                                    n, n, CUDA_R_64F, M, n, CUDA_R_64F, S, CUDA_R_64F, U, n,
                                    CUDA_R_64F, V, n, CUDA_R_64F, net->svd_dwork[sid],
@@ -93,7 +93,7 @@ struct SvdStep : Step {
                                    net->svd_info + info_idx, &herr);
         } else {  // gesvd writes V^T into V
             const signed char job = vectors ? 'S' : 'N';
-            st = cusolverDnDgesvd(e.solver[sid], job, job, n, n, M, n, S, U, n, V, n,
+            st = cusolverDnDgesvd(e.lane().solver[sid], job, job, n, n, M, n, S, U, n, V, n,
                                   (double*)net->svd_dwork[sid], net->svd_lwork, net->svd_rwork[sid],
                                   net->svd_info + info_idx);
         }
@@ -107,7 +107,7 @@ struct FnStep : Step {
     std::function<void(cudaStream_t)> f;
     explicit FnStep(std::function<void(cudaStream_t)> g) : f(std::move(g)) {}
     void run(Engine& e) override {
-        f(e.streams[sid]);
+        f(e.lane().streams[sid]);
         e.kernel_launches += 1;
     }
 };
@@ -117,12 +117,15 @@ struct ParallelStep : Step {
     cudaEvent_t fork_ev = nullptr;
     std::vector<cudaEvent_t> join_ev;
     void run(Engine& e) override {
-        cudaEventRecord(fork_ev, e.streams[0]);
-        for (size_t i = 0; i < sub.size(); ++i) cudaStreamWaitEvent(e.streams[i + 1], fork_ev, 0);
+        Engine::Lane& L = e.lane();
+        const int lane = Engine::cur_lane;
+        cudaEventRecord(fork_ev, L.streams[0]);
+        for (size_t i = 0; i < sub.size(); ++i) cudaStreamWaitEvent(L.streams[i + 1], fork_ev, 0);
         std::vector<std::exception_ptr> errs(sub.size());
         std::vector<std::thread> th;
         for (size_t i = 1; i < sub.size(); ++i)
-            th.emplace_back([&, i] {
+            th.emplace_back([&, i, lane] {
+                Engine::cur_lane = lane;
                 try {
                     e.run_sub(sub[i]);
                 } catch (...) {
@@ -136,8 +139,8 @@ struct ParallelStep : Step {
         }
         for (auto& t : th) t.join();
         for (size_t i = 0; i < sub.size(); ++i) {
-            cudaEventRecord(join_ev[i], e.streams[i + 1]);
-            cudaStreamWaitEvent(e.streams[0], join_ev[i], 0);
+            cudaEventRecord(join_ev[i], L.streams[i + 1]);
+            cudaStreamWaitEvent(L.streams[0], join_ev[i], 0);
         }
         for (auto& x : errs)
             if (x) std::rethrow_exception(x);
@@ -147,16 +150,22 @@ struct ParallelStep : Step {
 // ---------------------------------------------------------------------------------------------
 // engine
 // ---------------------------------------------------------------------------------------------
+thread_local int Engine::cur_lane = 0;
+
 Engine::Engine(cudaStream_t s, int prec, double cut) : stream(s), precision(prec), cutoff(cut) {
     const char* dr = getenv("SCTM_DRYRUN");
     dry = dr && dr[0] == '1';
     if (dry) return;
-    streams[0] = s;
-    for (int i = 1; i < kStreams; ++i)
-        CUDA_OK(cudaStreamCreateWithFlags(&streams[i], cudaStreamNonBlocking));
-    for (int i = 0; i < kStreams; ++i) {
-        SOLVER_OK(cusolverDnCreate(&solver[i]));
-        SOLVER_OK(cusolverDnSetStream(solver[i], streams[i]));
+    for (int l = 0; l < kLanes; ++l) {
+        Lane& L = lanes[l];
+        for (int i = 0; i < kStreams; ++i) {
+            if (l == 0 && i == 0)
+                L.streams[i] = s;
+            else
+                CUDA_OK(cudaStreamCreateWithFlags(&L.streams[i], cudaStreamNonBlocking));
+            SOLVER_OK(cusolverDnCreate(&L.solver[i]));
+            SOLVER_OK(cusolverDnSetStream(L.solver[i], L.streams[i]));
+        }
     }
     SOLVER_OK(cusolverDnCreateParams(&solver_params));
     const char* pf = getenv("SCTM_PROFILE");
@@ -164,51 +173,59 @@ Engine::Engine(cudaStream_t s, int prec, double cut) : stream(s), precision(prec
 }
 
 Engine::~Engine() {
-    for (int i = 0; i < kStreams; ++i)
-        if (streams[i]) cudaStreamSynchronize(streams[i]);
+    for (int l = 0; l < kLanes; ++l)
+        for (int i = 0; i < kStreams; ++i)
+            if (lanes[l].streams[i]) cudaStreamSynchronize(lanes[l].streams[i]);
     for (void* p : allocs_) cudaFree(p);
     for (cudaEvent_t ev : owned_events_) cudaEventDestroy(ev);
-    for (int i = 0; i < kStreams; ++i) {
-        for (cudaEvent_t ev : ev_pool[i]) cudaEventDestroy(ev);
-        if (solver[i]) cusolverDnDestroy(solver[i]);
-        if (i > 0 && streams[i]) cudaStreamDestroy(streams[i]);
+    for (int l = 0; l < kLanes; ++l) {
+        Lane& L = lanes[l];
+        for (int i = 0; i < kStreams; ++i) {
+            for (cudaEvent_t ev : L.ev_pool[i]) cudaEventDestroy(ev);
+            if (L.solver[i]) cusolverDnDestroy(L.solver[i]);
+            if (!(l == 0 && i == 0) && L.streams[i]) cudaStreamDestroy(L.streams[i]);
+        }
     }
     if (solver_params) cusolverDnDestroyParams(solver_params);
 }
 
 int Engine::record(int sid) {
-    if (ev_used[sid] == ev_pool[sid].size()) {
+    Lane& L = lane();
+    if (L.ev_used[sid] == L.ev_pool[sid].size()) {
         cudaEvent_t ev;
         CUDA_OK(cudaEventCreate(&ev));
-        ev_pool[sid].push_back(ev);
+        L.ev_pool[sid].push_back(ev);
     }
-    const int idx = (int)ev_used[sid]++;
-    cudaEventRecord(ev_pool[sid][idx], streams[sid]);
+    const int idx = (int)L.ev_used[sid]++;
+    cudaEventRecord(L.ev_pool[sid][idx], L.streams[sid]);
     return idx;
 }
 
 void Engine::record_done(int sid, int kind, long long flops, int e0) {
     const int e1 = record(sid);
-    ev_recs[sid].push_back({kind, flops, e0, e1});
+    lane().ev_recs[sid].push_back({kind, flops, e0, e1});
 }
 
 void Engine::harvest() {
-    for (int sid = 0; sid < kStreams; ++sid) {
-        for (const EvRec& r : ev_recs[sid]) {
-            float ms = 0;
-            CUDA_OK(cudaEventSynchronize(ev_pool[sid][r.e1]));
-            CUDA_OK(cudaEventElapsedTime(&ms, ev_pool[sid][r.e0], ev_pool[sid][r.e1]));
-            if (r.kind == KIND_CTR) {
-                ctr_ms += ms;
-                ctr_launches += 1;
-                ctr_flops += r.flops;
-            } else {
-                svd_ms += ms;
-                svd_calls += 1;
+    for (int l = 0; l < kLanes; ++l) {
+        Lane& L = lanes[l];
+        for (int sid = 0; sid < kStreams; ++sid) {
+            for (const EvRec& r : L.ev_recs[sid]) {
+                float ms = 0;
+                CUDA_OK(cudaEventSynchronize(L.ev_pool[sid][r.e1]));
+                CUDA_OK(cudaEventElapsedTime(&ms, L.ev_pool[sid][r.e0], L.ev_pool[sid][r.e1]));
+                if (r.kind == KIND_CTR) {
+                    ctr_ms += ms;
+                    ctr_launches += 1;
+                    ctr_flops += r.flops;
+                } else {
+                    svd_ms += ms;
+                    svd_calls += 1;
+                }
             }
+            L.ev_recs[sid].clear();
+            L.ev_used[sid] = 0;
         }
-        ev_recs[sid].clear();
-        ev_used[sid] = 0;
     }
 }
 
@@ -365,8 +382,10 @@ Ten Engine::ctr(Network& net, Plan& P, const std::string& spec, const Ten& X, co
     a.rowscale = rowscale;
     a.colscale = colscale;
     a.precision = precision;
-    // split K when the output tile grid cannot fill the GPU
-    const long long tiles = (long long)((a.M + 63) / 64) * ((a.N + 63) / 64) * a.nb;
+    // 32 x 32 tiles when 64 x 64 tiles cannot fill the 152 SMs; split K when even those cannot
+    const long long tiles64 = (long long)((a.M + 63) / 64) * ((a.N + 63) / 64) * a.nb;
+    a.tile = tiles64 < 152 ? 32 : 64;
+    const long long tiles = (long long)((a.M + a.tile - 1) / a.tile) * ((a.N + a.tile - 1) / a.tile) * a.nb;
     a.splits = 1;
     a.kchunk = std::max(a.K, 1);
     if (tiles < 152 && a.K > 256) {
@@ -854,11 +873,11 @@ void Engine::finalize(Network& net) {
     double* A = dalloc((long long)n * n);
     double* S = dalloc(n);
     size_t dbytes = 0, hbytes = 0;
-    SOLVER_OK(cusolverDnXgesvdp_bufferSize(solver[0], solver_params, CUSOLVER_EIG_MODE_VECTOR, 1, n,
+    SOLVER_OK(cusolverDnXgesvdp_bufferSize(lanes[0].solver[0], solver_params, CUSOLVER_EIG_MODE_VECTOR, 1, n,
                                            n, CUDA_R_64F, A, n, CUDA_R_64F, S, CUDA_R_64F, A, n,
                                            CUDA_R_64F, A, n, CUDA_R_64F, &dbytes, &hbytes));
     int lwork = 0;
-    SOLVER_OK(cusolverDnDgesvd_bufferSize(solver[0], n, n, &lwork));
+    SOLVER_OK(cusolverDnDgesvd_bufferSize(lanes[0].solver[0], n, n, &lwork));
     net.svd_lwork = std::max(lwork, 1);
     net.svd_dbytes = std::max<size_t>(std::max<size_t>(dbytes, 8), (size_t)net.svd_lwork * 8);
     net.svd_hbytes = std::max<size_t>(hbytes, 8);

@@ -38,6 +38,11 @@ Ten permute(const Ten& t, const std::vector<int>& perm);           // out axis k
 class Engine;
 
 constexpr int kStreams = 7;  // stream 0 = the caller's stream; 1..6 run independent projectors
+struct EvRec {
+    int kind;
+    long long flops;
+    int e0, e1;
+};
 
 struct Step {
     int sid = 0;  // stream index
@@ -83,9 +88,20 @@ public:
     Engine(const Engine&) = delete;
     Engine& operator=(const Engine&) = delete;
 
-    cudaStream_t stream;                     // == streams[0]
-    cudaStream_t streams[kStreams] = {nullptr};
-    cusolverDnHandle_t solver[kStreams] = {nullptr};
+    cudaStream_t stream;  // the caller's stream == lanes[0].streams[0]
+    // Two lanes of streams and solver handles, so that the numerator and norm networks can be
+    // driven from two host threads at once; the lane used is the calling thread's cur_lane.
+    struct Lane {
+        cudaStream_t streams[kStreams] = {nullptr};
+        cusolverDnHandle_t solver[kStreams] = {nullptr};
+        std::vector<cudaEvent_t> ev_pool[kStreams];
+        size_t ev_used[kStreams] = {0};
+        std::vector<struct EvRec> ev_recs[kStreams];
+    };
+    static constexpr int kLanes = 2;
+    Lane lanes[kLanes];
+    static thread_local int cur_lane;
+    Lane& lane() { return lanes[cur_lane]; }
     cusolverDnParams_t solver_params = nullptr;
     int precision;
     double cutoff;
@@ -96,10 +112,7 @@ public:
     // timing: events recorded around every contraction and SVD without host synchronisation,
     // harvested (summed) after each iteration
     bool profile = false;
-    struct EvRec { int kind; long long flops; int e0, e1; };
-    std::vector<cudaEvent_t> ev_pool[kStreams];
-    size_t ev_used[kStreams] = {0};
-    std::vector<EvRec> ev_recs[kStreams];
+
     double ctr_ms = 0, svd_ms = 0;
     long long ctr_launches = 0, ctr_flops = 0, svd_calls = 0;
     std::atomic<long long> kernel_launches{0};  // own kernels only (cuSOLVER's are not counted)

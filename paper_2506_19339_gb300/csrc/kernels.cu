@@ -8,17 +8,22 @@
 namespace sctm {
 
 // ---------------------------------------------------------------------------------------------
-// FP64 contraction: 64x64 output tile per CTA, 256 threads, 4x4 register tile per thread, K in
-// chunks of 16.  Operand tiles are gathered through the offset tables into shared memory, so the
+// FP64 contraction: 64x64 (or 32x32) output tile per CTA, 256 threads, 4x4 (2x2) register tile
+// per thread, K in chunks of 16.  Operand tiles are gathered through the offset tables into shared memory, so the
 // leg permutation of each operand is paid inside the load (Sec. III's contractions have every
 // operand in a different leg order).  Split-K writes partial tiles that a second kernel sums in
 // a fixed order (deterministic, no atomics).
 // ---------------------------------------------------------------------------------------------
 namespace {
-constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+constexpr int BK = 16, NT = 256;
 }
 
+// TM x TN outputs per thread on a 16 x 16 thread grid: a (16 TM) x (16 TN) tile per CTA.  Every
+// output element accumulates over K in the same order (chunks of 16, then sequentially) whatever
+// the tile size, so the tile choice does not change the result.
+template <int TM, int TN>
 __global__ void __launch_bounds__(NT) ctr_f64_kernel(const CtrLaunch a) {
+    constexpr int BM = 16 * TM, BN = 16 * TN;
     __shared__ double As[BK][BM + 1];
     __shared__ double Bs[BK][BN + 1];
     __shared__ int sxm[BM];
@@ -42,17 +47,17 @@ __global__ void __launch_bounds__(NT) ctr_f64_kernel(const CtrLaunch a) {
 
     const int kbeg = sp * a.kchunk;
     const int kend = min(a.K, kbeg + a.kchunk);
-    double acc[4][4];
+    double acc[TM][TN];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+        for (int j = 0; j < TN; ++j) acc[i][j] = 0.0;
 
     for (int k0 = kbeg; k0 < kend; k0 += BK) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < BM * BK / NT; ++q) {
             const int e = tid + NT * q;
-            const int kk = e & (BK - 1), mm = e >> 4;
+            const int kk = e % BK, mm = e / BK;
             const int k = k0 + kk;
             const int om_ = sxm[mm];
             double v = 0.0;
@@ -60,9 +65,9 @@ __global__ void __launch_bounds__(NT) ctr_f64_kernel(const CtrLaunch a) {
             As[kk][mm] = v;
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < BN * BK / NT; ++q) {
             const int e = tid + NT * q;
-            const int nn = e & (BN - 1), kk = e >> 6;
+            const int nn = e % BN, kk = e / BN;
             const int k = k0 + kk;
             const int on_ = syn[nn];
             double v = 0.0;
@@ -72,15 +77,15 @@ __global__ void __launch_bounds__(NT) ctr_f64_kernel(const CtrLaunch a) {
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
-            double av[4], bv[4];
+            double av[TM], bv[TN];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) av[i] = As[kk][ty + 16 * i];
+            for (int i = 0; i < TM; ++i) av[i] = As[kk][ty + 16 * i];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
+            for (int j = 0; j < TN; ++j) bv[j] = Bs[kk][tx + 16 * j];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < TM; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+                for (int j = 0; j < TN; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
         }
         __syncthreads();
     }
@@ -88,11 +93,11 @@ __global__ void __launch_bounds__(NT) ctr_f64_kernel(const CtrLaunch a) {
     if (a.splits > 1) {
         double* P = a.partial + (long long)z * a.M * a.N;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < TM; ++i) {
             const int m = m0 + ty + 16 * i;
             if (m >= a.M) continue;
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
+            for (int j = 0; j < TN; ++j) {
                 const int n = n0 + tx + 16 * j;
                 if (n < a.N) P[(long long)m * a.N + n] = acc[i][j];
             }
@@ -101,13 +106,13 @@ __global__ void __launch_bounds__(NT) ctr_f64_kernel(const CtrLaunch a) {
     }
     const long long obo = a.ob ? a.ob[b] : 0;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < TM; ++i) {
         const int m = m0 + ty + 16 * i;
         if (m >= a.M) continue;
         const double rs = a.rowscale ? a.rowscale[m] : 1.0;
         const long long om_ = obo + a.om[m];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < TN; ++j) {
             const int n = n0 + tx + 16 * j;
             if (n >= a.N) continue;
             double v = acc[i][j] * rs;
@@ -136,8 +141,12 @@ __global__ void ctr_splitk_reduce_kernel(const CtrLaunch a) {
 }
 
 void launch_ctr(const CtrLaunch& a, cudaStream_t s) {
-    dim3 grid((a.N + BN - 1) / BN, (a.M + BM - 1) / BM, a.nb * a.splits);
-    ctr_f64_kernel<<<grid, NT, 0, s>>>(a);
+    const int bm = a.tile, bn = a.tile;
+    dim3 grid((a.N + bn - 1) / bn, (a.M + bm - 1) / bm, a.nb * a.splits);
+    if (a.tile == 32)
+        ctr_f64_kernel<2, 2><<<grid, NT, 0, s>>>(a);
+    else
+        ctr_f64_kernel<4, 4><<<grid, NT, 0, s>>>(a);
     if (a.splits > 1) {
         const long long total = (long long)a.M * a.N * a.nb;
         int blocks = (int)std::min<long long>((total + 255) / 256, 4096);

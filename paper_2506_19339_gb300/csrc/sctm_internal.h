@@ -38,6 +38,7 @@ struct CtrLaunch {
     int splits = 1;
     int kchunk = 1;
     int precision = 0;                 // SCTM_PREC_*
+    int tile = 64;                     // CTA output tile: 64 x 64 or 32 x 32
 };
 
 void launch_ctr(const CtrLaunch& a, cudaStream_t s);
