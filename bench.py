@@ -38,6 +38,9 @@ def parse():
     ap.add_argument('--tol', type=float, default=1e-10)
     ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
     ap.add_argument('--no-cpu-baseline', action='store_true')
+    ap.add_argument('--batch', type=int, default=0,
+                    help='batched sweep: B contexts (T uniform in [4.40, 4.62], seeds 100..) '
+                         'iterated concurrently; 0 = the single-instance workload')
     ap.add_argument('--svd', default='qr', choices=['qr', 'polar'],
                     help='FP64 SVD of the projectors: cuSOLVER gesvd (qr) or gesvdp (polar)')
     return ap.parse_args()
@@ -346,8 +349,80 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args):
+    """The batched sweep: B independent evaluations of (D=4, chi=64) at B temperatures, iterated
+    concurrently through sctm_iterate_batch; value = evaluations per second of the whole batch."""
+    import torch
+    from paper_2506_19339_gb300 import build, inputs, sctm
+    w = WORKLOAD
+    B = args.batch
+    dev = torch.device('cuda', 0)
+    build.build()
+    sctm.load()
+    Ts = inputs.temperature_sweep(B)
+    streams = [torch.cuda.Stream(dev) for _ in range(B)]
+    ctxs, As, gs = [], [], []
+    for i, T in enumerate(Ts):
+        A = torch.from_numpy(inputs.random_peps(w['D'], 100 + i)).to(dev)
+        st, O = sctm.sctm_ising_pepo(T)
+        st, o = sctm.sctm_default_opts()
+        o.T, o.D, o.p, o.d = float(T), w['D'], 2, 2
+        o.cuda_stream = streams[i].cuda_stream
+        o.svd_mode = sctm.SCTM_SVD_POLAR if args.svd == 'polar' else sctm.SCTM_SVD_QR
+        st, ctx = sctm.sctm_create(A, np.ascontiguousarray(O), w['chi'], o)
+        if st != sctm.SCTM_OK:
+            raise RuntimeError('sctm_create failed for batch member %d: %s' % (i, sctm.STATUS_NAMES[st]))
+        ctxs.append(ctx)
+        As.append(A)
+        gs.append(torch.zeros_like(A))
+    mem = sum(sctm.sctm_device_bytes(c) for c in ctxs)
+
+    def step():
+        for c, A in zip(ctxs, As):
+            assert sctm.sctm_set_peps(c, A, 1) == sctm.SCTM_OK
+        st, sts, its, dss = sctm.sctm_iterate_batch(ctxs, args.iters, args.tol)
+        for c, g in zip(ctxs, gs):
+            sctm.sctm_free_energy(c)
+            sctm.sctm_grad(c, g)
+        return its
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(0)
+    clocks.start()
+    ms = []
+    for _ in range(args.steps):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        its = step()
+        torch.cuda.synchronize(dev)
+        ms.append(1000.0 * (time.perf_counter() - t0))
+    clk = clocks.stop()
+    for c in ctxs:
+        sctm.sctm_destroy(c)
+    total = float(np.sum(ms))
+    line = {
+        'metric': METRIC, 'value': B * args.steps / (total * 1e-3), 'unit': 'evals/s', 'n_gpus': 1,
+        'steps': args.steps, 'warmup': args.warmup, 'ms_per_step': total / args.steps,
+        'higher_is_better': True, 'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f64',
+        'data': 'synthetic',
+        'config': {'workload': 'batched sweep: %d contexts, T uniform in [4.40, 4.62], PEPS D=%d '
+                               'N(0,1) seeds 100..%d, chi=%d, %d iterations per evaluation, '
+                               'FP64, iterated concurrently (one host thread and stream set '
+                               'per context)' % (B, w['D'], 99 + B, w['chi'], args.iters),
+                   'batch': B, 'iterations_per_eval': args.iters, 'device_bytes': mem,
+                   'timing': 'host wall clock around each step with device synchronisation'},
+        'clocks': clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.batch > 0:
+        run_batch(args)
+        return
     if args.impl == 'reference':
         run_reference(args)
     else:

@@ -159,6 +159,18 @@ sctm_status sctm_move(sctm_ctx* ctx, int network, int direction);
  * into a host buffer of chi doubles. */
 sctm_status sctm_spectrum(sctm_ctx* ctx, int network, double* S);
 
+/* sctm_iterate_batch -- sctm_iterate on `count` independent contexts at once (the batched
+ * sweep: several temperatures or PEPS of one (D, chi)).  Each context is driven from its own host
+ * thread on its own streams (give each context its own cuda_stream at creation, otherwise their
+ * work serialises on the shared stream).  status[i], it_done[i], last_dS[i] (host arrays of
+ * `count`, any may be NULL) receive each context's results.  Returns SCTM_OK if every context
+ * returned SCTM_OK, SCTM_ENOCONV if the worst was ENOCONV, else the first error status. */
+sctm_status sctm_iterate_batch(sctm_ctx* const* ctxs, int count, int max_it, double tol,
+                               int* status, int* it_done, double* last_dS);
+
+/* sctm_device_bytes -- device memory held by the context (all of it is allocated at create). */
+size_t sctm_device_bytes(const sctm_ctx* ctx);
+
 /* sctm_local_values -- the local contractions of one network from its current environment
  * (Sec. II, Fig. 4(b)): out[0..3] = Z00, Z10, Z01, Z11 and out[4] = ln kappa,
  * kappa = Z11 Z00 / (Z10 Z01) (NaN when kappa <= 0).  Host buffer of 5 doubles.  Each Z depends

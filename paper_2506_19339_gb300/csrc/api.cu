@@ -435,6 +435,32 @@ sctm_status sctm_local_values(sctm_ctx* ctx, int network, double* out5) {
     API_END(ctx)
 }
 
+sctm_status sctm_iterate_batch(sctm_ctx* const* ctxs, int count, int max_it, double tol,
+                               int* status, int* it_done, double* last_dS) {
+    if (!ctxs || count < 0) return SCTM_EINVAL;
+    for (int i = 0; i < count; ++i)
+        if (!ctxs[i]) return SCTM_EINVAL;
+    std::vector<int> st(count, SCTM_OK), it(count, 0);
+    std::vector<double> ds(count, 0.0);
+    std::vector<std::thread> th;
+    for (int i = 0; i < count; ++i)
+        th.emplace_back([&, i] { st[i] = sctm_iterate(ctxs[i], max_it, tol, &it[i], &ds[i]); });
+    for (auto& t : th) t.join();
+    sctm_status worst = SCTM_OK;
+    for (int i = 0; i < count; ++i) {
+        if (status) status[i] = st[i];
+        if (it_done) it_done[i] = it[i];
+        if (last_dS) last_dS[i] = ds[i];
+        if (st[i] != SCTM_OK && st[i] != SCTM_ENOCONV && worst == SCTM_OK) worst = (sctm_status)st[i];
+    }
+    if (worst != SCTM_OK) return worst;
+    for (int i = 0; i < count; ++i)
+        if (st[i] == SCTM_ENOCONV) return SCTM_ENOCONV;
+    return SCTM_OK;
+}
+
+size_t sctm_device_bytes(const sctm_ctx* ctx) { return ctx && ctx->eng ? ctx->eng->bytes : 0; }
+
 sctm_status sctm_set_profiling(sctm_ctx* ctx, int on) {
     API_BEGIN(ctx)
     ctx->eng->harvest();

@@ -234,6 +234,7 @@ double* Engine::dalloc(long long n) {
     void* p = nullptr;
     CUDA_OK(cudaMalloc(&p, std::max<long long>(n, 1) * sizeof(double)));
     allocs_.push_back(p);
+    bytes += std::max<long long>(n, 1) * sizeof(double);
     CUDA_OK(cudaMemset(p, 0, std::max<long long>(n, 1) * sizeof(double)));
     return (double*)p;
 }
@@ -244,6 +245,7 @@ int* Engine::ialloc(const std::vector<int>& host) {
     size_t bytes = std::max<size_t>(host.size(), 1) * sizeof(int);
     CUDA_OK(cudaMalloc(&p, bytes));
     allocs_.push_back(p);
+    this->bytes += bytes;
     if (!host.empty())
         CUDA_OK(cudaMemcpy(p, host.data(), host.size() * sizeof(int), cudaMemcpyHostToDevice));
     return (int*)p;

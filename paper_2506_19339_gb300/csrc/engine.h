@@ -120,6 +120,7 @@ public:
     void record_done(int sid, int kind, long long flops, int e0);
     void harvest();
 
+    size_t bytes = 0;                              // device bytes allocated
     double* dalloc(long long n);                   // tracked, zero-filled device buffer
     int* ialloc(const std::vector<int>& host);     // tracked device copy of an int table
     Ten alloc(const std::vector<int>& dims) { return view(dalloc(prod(dims)), dims); }

@@ -70,6 +70,9 @@ def load():
         'sctm_spectrum': (I, [P, I, P]),
         'sctm_local_values': (I, [P, I, P]),
         'sctm_gemm_noalloc': (I, [P, P, P, I, I, I, P]),
+        'sctm_iterate_batch': (I, [ctypes.POINTER(P), I, I, D, ctypes.POINTER(I),
+                                   ctypes.POINTER(I), ctypes.POINTER(D)]),
+        'sctm_device_bytes': (S, [P]),
         'sctm_set_profiling': (I, [P, I]),
         'sctm_profile': (I, [P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong),
                              ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(D),
@@ -180,6 +183,20 @@ def sctm_gemm_noalloc(X, Y, O, M, N, K, stream=None):
     """O = X Y (row-major device tensors, FP64) without any device allocation in the library."""
     return load().sctm_gemm_noalloc(_ptr(X), _ptr(Y), _ptr(O), int(M), int(N), int(K),
                                     ctypes.c_void_p(stream))
+
+
+def sctm_iterate_batch(ctxs, max_it, tol):
+    n = len(ctxs)
+    arr = (ctypes.c_void_p * n)(*[c.value if isinstance(c, ctypes.c_void_p) else c for c in ctxs])
+    st = (ctypes.c_int * n)()
+    it = (ctypes.c_int * n)()
+    ds = (ctypes.c_double * n)()
+    s = load().sctm_iterate_batch(arr, n, int(max_it), float(tol), st, it, ds)
+    return s, list(st), list(it), list(ds)
+
+
+def sctm_device_bytes(ctx):
+    return int(load().sctm_device_bytes(ctx))
 
 
 def sctm_set_profiling(ctx, on):

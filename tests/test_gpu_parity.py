@@ -242,3 +242,35 @@ def test_polar_svd_mode():
     ref = _oracle(A, T, chi, iters)
     assert abs(f - ref['f']) <= 1e-8 * abs(ref['f']), (f, ref['f'])
     assert _rel(g, ref['g']) <= 1e-5
+
+
+def test_batched_sweep_matches_single_runs():
+    """sctm_iterate_batch over contexts at several temperatures (the batched sweep) gives, for
+    each context, the same bits as iterating that context alone."""
+    import torch
+    D, chi = 2, 8
+    Ts = inputs.temperature_sweep(3)
+    runs, alone = [], []
+    streams = [torch.cuda.Stream() for _ in Ts]
+    try:
+        for i, T in enumerate(Ts):
+            A = inputs.perturbed_product_peps(D, 100 + i)
+            st, O = sctm.sctm_ising_pepo(T)
+            st, o = sctm.sctm_default_opts()
+            o.T, o.D, o.p, o.d = T, D, 2, 2
+            o.cuda_stream = streams[i].cuda_stream
+            st, ctx = sctm.sctm_create(A, O, chi, o)
+            assert st == sctm.SCTM_OK
+            runs.append(ctx)
+            r = sctm.SplitCTMRG(A, O, chi, T)
+            r.iterate(5)
+            alone.append(r.free_energy())
+            r.close()
+        st, sts, its, dss = sctm.sctm_iterate_batch(runs, 5, 0.0)
+        assert st == sctm.SCTM_OK and its == [5, 5, 5]
+        for ctx, f_alone in zip(runs, alone):
+            st, f = sctm.sctm_free_energy(ctx)
+            assert f == f_alone
+    finally:
+        for ctx in runs:
+            sctm.sctm_destroy(ctx)
