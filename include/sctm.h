@@ -40,7 +40,7 @@ typedef enum {
     SCTM_ENOMEM = 4,     /* device memory allocation failed                                      */
     SCTM_ENOCONV = 5,    /* iteration limit reached before ||S[i+1]-S[i]||_2 < tol (Sec. III.D)  */
     SCTM_ENUMERIC = 6,   /* kappa <= 0, a non-finite value, or an all-zero spectrum              */
-    SCTM_ETIMEOUT = 7    /* reserved: a bounded device-side wait ran out                         */
+    SCTM_ETIMEOUT = 7    /* a bounded device-side wait ran out (tensor-core kernels)             */
 } sctm_status;
 
 /* Arithmetic of the contraction kernels.  SVDs, normalisations and the free-energy ratio are
@@ -191,6 +191,21 @@ sctm_status sctm_set_profiling(sctm_ctx* ctx, int on);
 sctm_status sctm_profile(sctm_ctx* ctx, double* ctr_ms, long long* ctr_launches,
                          long long* ctr_flops, double* svd_ms, long long* svd_calls,
                          long long* kernel_launches, int reset);
+
+/* sctm_gemm -- O = X Y for row-major device matrices X (M x K), Y (K x N), O (M x N), run by the
+ * library's contraction kernels in the arithmetic `precision` (SCTM_PREC_*): the FP64 kernel, or
+ * the tensor-core kernel with TF32 / BF16 operands (optionally hi/lo split) and FP32
+ * accumulation, the forms the move contractions of Sec. III take in the mixed modes.  The
+ * elementwise error is bounded by c (|X||Y|)_ij with c about 2^-11 (TF32), 2^-8 (BF16), 2^-21
+ * (TF32X3), 2^-16 (BF16X3) and the FP64 rounding for SCTM_PREC_FP64.
+ *   X, Y, O      device pointers (host pointers: SCTM_EINVAL); caller-owned
+ *   M, N, K      >= 1, M*N*... each below 2^31 elements
+ *   cuda_stream  cudaStream_t (NULL = legacy default); the call synchronises it before
+ *                returning (it allocates and frees its index tables and split-K buffer)
+ * Returns SCTM_OK, SCTM_EINVAL, SCTM_ENOMEM, SCTM_ECUDA, or SCTM_ETIMEOUT if a bounded wait of
+ * the tensor-core kernel ran out (the result is then invalid). */
+sctm_status sctm_gemm(const double* X, const double* Y, double* O, int M, int N, int K,
+                      int precision, void* cuda_stream);
 
 /* sctm_gemm_noalloc -- O = X Y in FP64 for row-major device matrices X (M x K), Y (K x N),
  * O (M x N), computed by a variant of the library's contraction kernel that allocates nothing.

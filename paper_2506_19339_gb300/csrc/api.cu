@@ -138,7 +138,8 @@ sctm_status sctm_create(const double* peps, const double* pepo, int chi, const s
     sctm_opts opts;
     if (o) opts = *o; else sctm_default_opts(&opts);
     if (chi < 1 || chi > 4096 || opts.D < 1 || opts.p < 1 || opts.d < 1 || opts.batch != 1 ||
-        opts.precision != SCTM_PREC_FP64 || opts.grad_mode != SCTM_GRAD_ENV ||
+        opts.precision < SCTM_PREC_FP64 || opts.precision > SCTM_PREC_BF16X3 ||
+        opts.grad_mode != SCTM_GRAD_ENV ||
         !(opts.svd_cutoff >= 0.0) || opts.D > 64 || opts.d > 64 || opts.p > 64 ||
         (opts.svd_mode != SCTM_SVD_QR && opts.svd_mode != SCTM_SVD_POLAR))
         return SCTM_EINVAL;
@@ -237,18 +238,40 @@ sctm_status sctm_iterate(sctm_ctx* ctx, int max_it, double tol, int* it_done, do
             cudaStream_t s0 = e.lane().streams[0];
             double dS = INFINITY;
             int it = 0;
+            // Mixed forms: iterate in the tensor-core form while the spectrum change still
+            // falls, then polish in FP64; convergence is only declared on FP64 iterations.
+            const int form = ctx->opts.precision;
+            e.set_precision(net, form);
+            double best = INFINITY;
+            int stall = 0;
             for (it = 1; it <= max_it; ++it) {
                 for (int m = 0; m < 4; ++m) e.run(net.move[m]);
                 e.run(net.spectrum);
                 check_cuda("iteration");
+                int err = 0;
                 cuda_ok(cudaMemcpyAsync(&dS, net.dS, sizeof(double), cudaMemcpyDeviceToHost, s0),
                         "dS copy");
+                cuda_ok(cudaMemcpyAsync(&err, e.dev_err, sizeof(int), cudaMemcpyDeviceToHost, s0),
+                        "error flag copy");
                 cuda_ok(cudaStreamSynchronize(s0), "iteration sync");
+                if (err) throw Error(SCTM_ETIMEOUT, "tensor-core contraction wait timed out");
                 if (!std::isfinite(dS)) throw Error(SCTM_ENUMERIC, "non-finite spectrum change");
+                if (net.precision != SCTM_PREC_FP64) {
+                    if (dS < 0.5 * best) {
+                        best = dS;
+                        stall = 0;
+                    } else {
+                        ++stall;
+                    }
+                    if (dS < Engine::cutoff_floor(form) || stall >= 3)
+                        e.set_precision(net, SCTM_PREC_FP64);
+                    continue;
+                }
                 if (tol > 0.0 && dS < tol) break;
             }
             its[n] = std::min(it, max_it);
-            dss[n] = dS;
+            // a spectrum change measured on a mixed-form iteration never counts as converged
+            dss[n] = net.precision == SCTM_PREC_FP64 ? dS : std::max(dS, tol > 0.0 ? 2.0 * tol : dS);
         } catch (...) {
             errs[n] = std::current_exception();
         }
@@ -491,3 +514,94 @@ sctm_status sctm_profile(sctm_ctx* ctx, double* ctr_ms, long long* ctr_launches,
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// sctm_gemm: one plain row-major contraction through the library's kernels, in any form
+// ---------------------------------------------------------------------------------------------
+static bool on_device(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+sctm_status sctm_gemm(const double* X, const double* Y, double* O, int M, int N, int K,
+                      int precision, void* cuda_stream) {
+    if (!X || !Y || !O || M < 1 || N < 1 || K < 1) return SCTM_EINVAL;
+    if (precision < SCTM_PREC_FP64 || precision > SCTM_PREC_BF16X3) return SCTM_EINVAL;
+    if ((long long)M * K >= (1LL << 31) || (long long)K * N >= (1LL << 31) ||
+        (long long)M * N >= (1LL << 31))
+        return SCTM_EINVAL;
+    if (!on_device(X) || !on_device(Y) || !on_device(O)) return SCTM_EINVAL;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    std::vector<int> xm(M), xk(K), yk(K), yn(N), om(M), on(N);
+    for (int m = 0; m < M; ++m) xm[m] = m * K, om[m] = m * N;
+    for (int k = 0; k < K; ++k) xk[k] = k, yk[k] = k * N;
+    for (int n = 0; n < N; ++n) yn[n] = n, on[n] = n;
+    CtrLaunch a;
+    a.X = X;
+    a.Y = Y;
+    a.O = O;
+    a.M = M;
+    a.N = N;
+    a.K = K;
+    a.precision = precision;
+    // the engine's split-K rule, for the kernel this precision runs on
+    const bool tc = precision != SCTM_PREC_FP64;
+    const int bm = tc ? 128 : 64, bn = 64, align = tc ? 32 : 16;
+    const long long tiles = (long long)((M + bm - 1) / bm) * ((N + bn - 1) / bn);
+    int splits = 1, kchunk = K;
+    if (tiles < 152 && K > 256) {
+        int want = (int)std::min<long long>(std::max<long long>(304 / tiles, 1), (K + 127) / 128);
+        want = std::max(1, std::min(want, 128));
+        int kc = (K + want - 1) / want;
+        kc = ((kc + align - 1) / align) * align;
+        if ((K + kc - 1) / kc > 1) {
+            splits = (K + kc - 1) / kc;
+            kchunk = kc;
+        }
+    }
+    a.tile = 64;
+    a.splits = a.tc_splits = splits;
+    a.kchunk = a.tc_kchunk = kchunk;
+    std::vector<void*> bufs;
+    auto dev_copy = [&](const std::vector<int>& v) -> int* {
+        void* p = nullptr;
+        if (cudaMalloc(&p, v.size() * sizeof(int)) != cudaSuccess) return nullptr;
+        bufs.push_back(p);
+        if (cudaMemcpy(p, v.data(), v.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+            return nullptr;
+        return (int*)p;
+    };
+    sctm_status st = SCTM_OK;
+    int err_host = 0;
+    a.xm = dev_copy(xm);
+    a.xk = dev_copy(xk);
+    a.yk = dev_copy(yk);
+    a.yn = dev_copy(yn);
+    a.om = dev_copy(om);
+    a.on = dev_copy(on);
+    a.err = dev_copy({0});
+    if (!a.xm || !a.xk || !a.yk || !a.yn || !a.om || !a.on || !a.err) st = SCTM_ENOMEM;
+    if (st == SCTM_OK && splits > 1) {
+        void* p = nullptr;
+        if (cudaMalloc(&p, (size_t)splits * M * N * sizeof(double)) != cudaSuccess)
+            st = SCTM_ENOMEM;
+        else
+            bufs.push_back(p), a.partial = (double*)p;
+    }
+    if (st == SCTM_OK) {
+        launch_ctr(a, s);
+        if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+            st = SCTM_ECUDA;
+        else if (cudaMemcpy(&err_host, a.err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+            st = SCTM_ECUDA;
+        else if (err_host)
+            st = SCTM_ETIMEOUT;
+    }
+    cudaGetLastError();
+    for (void* p : bufs) cudaFree(p);
+    return st;
+}

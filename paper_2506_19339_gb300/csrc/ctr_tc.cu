@@ -1,0 +1,337 @@
+// Tensor-core (tcgen05) variant of the gather-table contraction, for the mixed-precision forms:
+// TF32 or BF16 operands with FP32 accumulation in tensor memory, optionally with hi/lo split
+// products (x = hi + lo; hi*hi + hi*lo + lo*hi) that recover most of the FP32 input precision.
+//
+// One CTA = 128 threads = 4 warps computes a 128 x 64 output tile (one tcgen05.mma of M=128,
+// N=64 per K-step).  Per K chunk of 32: every thread gathers FP64 operand elements through the
+// offset tables (the leg permutation is folded into the load, as in the FP64 kernel), splits them
+// into hi/lo, and stores them to shared memory in the K-major, no-swizzle canonical layout
+// (8-row x 16-byte core matrices: K-adjacent core matrices 128 B apart, M/N-adjacent ones
+// (32 * elem / 16) * 128 B apart); one thread issues the MMAs and commits them to an mbarrier that
+// every thread waits on before the shared tiles are reused.  The epilogue reads the accumulator
+// with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31 = tile rows) and scatters FP64 results
+// through the output tables.  Every wait is bounded: on timeout the kernel records an error,
+// drains, frees its tensor memory and returns.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "sctm_internal.h"
+
+namespace sctm {
+
+namespace {
+
+constexpr int TBM = 128, TBN = 64, TBK = 32, TNT = 128;
+constexpr int kTmemCols = 64;                 // FP32 accumulator columns (= TBN)
+constexpr long long kSpinLimit = 1LL << 26;   // bounded mbarrier wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor: start >> 4 (bits 0-13), leading (K) byte offset >> 4
+// (16-29), stride (M/N) byte offset >> 4 (32-45), descriptor version 1 (46-47), no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFF);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// Instruction descriptor of kind::tf32 / kind::f16: D = F32 (bits 4-5 = 1), A and B format
+// (bits 7-9, 10-12: F16 0, BF16 1, TF32 2), both K-major, N >> 3 at bits 17-22, M >> 4 at 24-28.
+__host__ __device__ constexpr uint32_t instr_desc(uint32_t fmt, uint32_t M, uint32_t N) {
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+
+template <bool BF16>
+struct Op {
+    using T = uint32_t;  // tf32 bits
+    static constexpr int kElem = 4;
+    static constexpr uint32_t kFmt = 2;
+    static constexpr int kMmaK = 8;
+    __device__ static void split(double x, uint32_t& hi, uint32_t& lo) {
+        const float f = (float)x;
+        uint32_t h;
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(f));
+        h &= 0xFFFFE000u;  // keep sign, exponent and the 10 TF32 mantissa bits
+        const float r = (float)(x - (double)__uint_as_float(h));
+        uint32_t l;
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(r));
+        hi = h;
+        lo = l & 0xFFFFE000u;
+    }
+};
+
+template <>
+struct Op<true> {
+    using T = unsigned short;  // bf16 bits
+    static constexpr int kElem = 2;
+    static constexpr uint32_t kFmt = 1;
+    static constexpr int kMmaK = 16;
+    __device__ static void split(double x, unsigned short& hi, unsigned short& lo) {
+        const __nv_bfloat16 h = __double2bfloat16(x);
+        const __nv_bfloat16 l = __double2bfloat16(x - (double)__bfloat162float(h));
+        hi = *reinterpret_cast<const unsigned short*>(&h);
+        lo = *reinterpret_cast<const unsigned short*>(&l);
+    }
+};
+
+// Row r and K index k of element e of a (rows x TBK) K-major tile stored in the canonical
+// no-swizzle core-matrix layout, where element e sits at byte e * E:
+//   byte(r, k) = ((r / 8) * CHUNKS + k / T) * 128 + (r % 8) * 16 + (k % T) * E,
+// T = 16 / E elements per 16-byte core-matrix row, CHUNKS = TBK / T core matrices along K.
+template <int E>
+__device__ __forceinline__ void tile_pos(int e, int& r, int& k) {
+    constexpr int T = 16 / E;
+    constexpr int CHUNKS = TBK / T;
+    const int kin = e % T, rin = (e / T) % 8, chunk = (e / (8 * T)) % CHUNKS,
+              group = e / (8 * T * CHUNKS);
+    r = group * 8 + rin;
+    k = chunk * T + kin;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (long long i = 0; i < kSpinLimit; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// one tcgen05.mma (single-thread issue): D[tmem] (+)= A[da] * B[db]^T, accumulate iff acc != 0
+template <bool BF16>
+__device__ __forceinline__ void mma(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc,
+                                    uint32_t acc);
+template <>
+__device__ __forceinline__ void mma<false>(uint32_t tmem, uint64_t da, uint64_t db,
+                                           uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+        "l"(da), "l"(db), "r"(idesc), "r"(acc));
+}
+template <>
+__device__ __forceinline__ void mma<true>(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc,
+                                          uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+        "l"(da), "l"(db), "r"(idesc), "r"(acc));
+}
+
+}  // namespace
+
+template <bool BF16, bool X3>
+__global__ void __launch_bounds__(TNT) ctr_tc_kernel(const CtrLaunch a) {
+    using O = Op<BF16>;
+    using T = typename O::T;
+    constexpr int E = O::kElem;
+    constexpr uint32_t A_BYTES = TBM * TBK * E, B_BYTES = TBN * TBK * E;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* a_hi = smem;
+    unsigned char* a_lo = smem + A_BYTES;
+    unsigned char* b_hi = smem + 2 * A_BYTES;
+    unsigned char* b_lo = smem + 2 * A_BYTES + B_BYTES;
+    __shared__ int sxm[TBM];
+    __shared__ int syn[TBN];
+    __shared__ __align__(8) unsigned long long mbar;
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_fail;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.y * TBM, n0 = blockIdx.x * TBN;
+    const int z = blockIdx.z;
+    const int b = z / a.splits, sp = z % a.splits;
+    const long long xbo = a.xb ? a.xb[b] : 0;
+    const long long ybo = a.yb ? a.yb[b] : 0;
+
+    if (tid < TBM) sxm[tid] = (m0 + tid < a.M) ? a.xm[m0 + tid] : -1;
+    if (tid < TBN) syn[tid] = (n0 + tid < a.N) ? a.yn[n0 + tid] : -1;
+    if (tid == 0) {
+        s_fail = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_base)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_base;
+    const uint32_t bar = smem_u32(&mbar);
+
+    const int kbeg = sp * a.kchunk;
+    const int kend = min(a.K, kbeg + a.kchunk);
+    constexpr uint32_t idesc = instr_desc(O::kFmt, TBM, TBN);
+    constexpr uint32_t LBO = 128, A_SBO = (TBK * E / 16) * 128, B_SBO = A_SBO;
+    uint32_t phase = 0, fail_phase = 0;
+    bool first = true;
+    bool ok = true;
+
+    for (int k0 = kbeg; k0 < kend && ok; k0 += TBK) {
+        // gather, split, stage.  Element e of a tile goes to byte e * E of its shared-memory
+        // image: e runs over the 16-byte core-matrix rows first (T elements along K), then the 8
+        // rows of a core matrix, then the core matrices along K, then the 8-row groups, so a warp
+        // writes contiguous bytes and reads T consecutive k of 32 / T rows.
+        for (int e = tid; e < TBM * TBK; e += TNT) {
+            int mm, kk;
+            tile_pos<E>(e, mm, kk);
+            const int k = k0 + kk;
+            const int om_ = sxm[mm];
+            const double v = (om_ >= 0 && k < kend) ? a.X[xbo + om_ + a.xk[k]] : 0.0;
+            T hi, lo;
+            O::split(v, hi, lo);
+            *reinterpret_cast<T*>(a_hi + e * E) = hi;
+            if (X3) *reinterpret_cast<T*>(a_lo + e * E) = lo;
+        }
+        for (int e = tid; e < TBN * TBK; e += TNT) {
+            int nn, kk;
+            tile_pos<E>(e, nn, kk);
+            const int k = k0 + kk;
+            const int on_ = syn[nn];
+            const double v = (on_ >= 0 && k < kend) ? a.Y[ybo + a.yk[k] + on_] : 0.0;
+            T hi, lo;
+            O::split(v, hi, lo);
+            *reinterpret_cast<T*>(b_hi + e * E) = hi;
+            if (X3) *reinterpret_cast<T*>(b_lo + e * E) = lo;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t ah = smem_u32(a_hi), al = smem_u32(a_lo);
+            const uint32_t bh = smem_u32(b_hi), bl = smem_u32(b_lo);
+#pragma unroll
+            for (int s = 0; s < TBK / O::kMmaK; ++s) {
+                const uint32_t step = s * (O::kMmaK * E / 16) * 128;  // core matrices per K-step
+                const uint64_t dah = smem_desc(ah + step, LBO, A_SBO);
+                const uint64_t dbh = smem_desc(bh + step, LBO, B_SBO);
+                mma<BF16>(tmem, dah, dbh, idesc, first ? 0u : 1u);
+                first = false;
+                if (X3) {
+                    const uint64_t dal = smem_desc(al + step, LBO, A_SBO);
+                    const uint64_t dbl = smem_desc(bl + step, LBO, B_SBO);
+                    mma<BF16>(tmem, dah, dbl, idesc, 1u);
+                    mma<BF16>(tmem, dal, dbh, idesc, 1u);
+                }
+            }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    bar)
+                : "memory");
+        }
+        first = false;
+        // every thread waits for the MMAs before the tiles are overwritten
+        if (!mbar_wait(bar, phase)) {
+            ok = false;
+            s_fail = 1;
+            fail_phase = phase;
+        }
+        phase ^= 1u;
+        __syncthreads();
+        if (s_fail) ok = false;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;");
+
+    if (ok && !first) {
+        // epilogue: warp w reads TMEM lanes 32w..32w+31 (tile rows), 16 columns at a time
+        const int m = m0 + warp * 32 + lane;
+        const bool mrow = m < a.M;
+        const double rs = (mrow && a.rowscale) ? a.rowscale[m] : 1.0;
+        const long long obo = a.ob ? a.ob[b] : 0;
+#pragma unroll
+        for (int c0 = 0; c0 < TBN; c0 += 16) {
+            uint32_t r[16];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
+                "%10, %11, %12, %13, %14, %15}, [%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                  "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                  "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (mrow) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int n = n0 + c0 + j;
+                    if (n >= a.N) continue;
+                    const double v = (double)__uint_as_float(r[j]);
+                    if (a.splits > 1) {
+                        a.partial[((long long)z * a.M + m) * a.N + n] = v;
+                    } else {
+                        double w = v * rs;
+                        if (a.colscale) w *= a.colscale[n];
+                        a.O[obo + a.om[m] + a.on[n]] = w;
+                    }
+                }
+            }
+        }
+    } else if (ok && first) {
+        // empty K range: the contraction (or this split's part of it) is zero
+        const int m = m0 + warp * 32 + lane;
+        if (m < a.M) {
+            const long long obo = a.ob ? a.ob[b] : 0;
+            for (int n = n0; n < min(a.N, n0 + TBN); ++n) {
+                if (a.splits > 1)
+                    a.partial[((long long)z * a.M + m) * a.N + n] = 0.0;
+                else
+                    a.O[obo + a.om[m] + a.on[n]] = 0.0;
+            }
+        }
+    }
+    if (!ok) {
+        // drain: wait (bounded) for the MMAs still in flight before the tensor memory is freed
+        mbar_wait(bar, fail_phase);
+        if (tid == 0 && a.err) atomicExch(a.err, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kTmemCols));
+    }
+}
+
+template <bool BF16, bool X3>
+static void launch_tc(const CtrLaunch& a, cudaStream_t s) {
+    constexpr int E = BF16 ? 2 : 4;
+    // hi and lo tiles of A and B; at least 32 KB so that at most 7 CTAs share an SM and their
+    // 64-column tensor-memory allocations (7 x 64 <= 512) never wait on one another
+    const size_t smem = std::max<size_t>(2 * (size_t)(TBM + TBN) * TBK * E, 32768);
+    static std::once_flag attr_once;
+    std::call_once(attr_once, [&] {
+        cudaFuncSetAttribute(ctr_tc_kernel<BF16, X3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    });
+    dim3 grid((a.N + TBN - 1) / TBN, (a.M + TBM - 1) / TBM, a.nb * a.splits);
+    ctr_tc_kernel<BF16, X3><<<grid, TNT, smem, s>>>(a);
+}
+
+void launch_ctr_tc(const CtrLaunch& a, cudaStream_t s) {
+    switch (a.precision) {
+        case SCTM_PREC_TF32: launch_tc<false, false>(a, s); break;
+        case SCTM_PREC_TF32X3: launch_tc<false, true>(a, s); break;
+        case SCTM_PREC_BF16: launch_tc<true, false>(a, s); break;
+        default: launch_tc<true, true>(a, s); break;
+    }
+}
+
+}  // namespace sctm

@@ -63,10 +63,12 @@ struct CtrStep : Step {
     CtrLaunch a;
     size_t partial_need = 0;
     long long flops = 0;
+    bool mixed_ok = false;  // may run in a tensor-core form
     void run(Engine& e) override {
         const int e0 = e.profile ? e.record(sid) : -1;
         launch_ctr(a, e.lane().streams[sid]);
-        e.kernel_launches += a.splits > 1 ? 2 : 1;
+        const int splits = a.precision == SCTM_PREC_FP64 ? a.splits : a.tc_splits;
+        e.kernel_launches += splits > 1 ? 2 : 1;
         if (e.profile) e.record_done(sid, KIND_CTR, flops, e0);
     }
 };
@@ -155,6 +157,7 @@ thread_local int Engine::cur_lane = 0;
 Engine::Engine(cudaStream_t s, int prec, double cut) : stream(s), precision(prec), cutoff(cut) {
     const char* dr = getenv("SCTM_DRYRUN");
     dry = dr && dr[0] == '1';
+    dev_err = ialloc({0});
     if (dry) return;
     for (int l = 0; l < kLanes; ++l) {
         Lane& L = lanes[l];
@@ -383,25 +386,34 @@ Ten Engine::ctr(Network& net, Plan& P, const std::string& spec, const Ten& X, co
     }
     a.rowscale = rowscale;
     a.colscale = colscale;
-    a.precision = precision;
-    // 32 x 32 tiles when 64 x 64 tiles cannot fill the 152 SMs; split K when even those cannot
+    st->mixed_ok = mixed_build;
+    a.precision = mixed_build ? precision : SCTM_PREC_FP64;
+    a.err = dev_err;
+    // FP64 kernel: 32 x 32 tiles when 64 x 64 tiles cannot fill the 152 SMs; split K when even
+    // those cannot.  Tensor-core kernel: 128 x 64 tiles, split K the same way (chunks of 32).
     const long long tiles64 = (long long)((a.M + 63) / 64) * ((a.N + 63) / 64) * a.nb;
     a.tile = tiles64 < 152 ? 32 : 64;
-    const long long tiles = (long long)((a.M + a.tile - 1) / a.tile) * ((a.N + a.tile - 1) / a.tile) * a.nb;
-    a.splits = 1;
-    a.kchunk = std::max(a.K, 1);
-    if (tiles < 152 && a.K > 256) {
-        int want = (int)std::min<long long>(std::max<long long>(304 / tiles, 1), (a.K + 127) / 128);
-        want = std::max(1, std::min(want, 128));
-        int kchunk = (a.K + want - 1) / want;
-        kchunk = ((kchunk + 15) / 16) * 16;
-        a.kchunk = kchunk;
-        a.splits = (a.K + kchunk - 1) / kchunk;
-        if (a.splits > 1)
-            st->partial_need = (size_t)a.nb * a.splits * (size_t)a.M * a.N;
-        else
-            a.kchunk = std::max(a.K, 1);
-    }
+    auto split_k = [&](long long tiles, int align, int& splits, int& kchunk) {
+        splits = 1;
+        kchunk = std::max(a.K, 1);
+        if (tiles < 152 && a.K > 256) {
+            int want = (int)std::min<long long>(std::max<long long>(304 / tiles, 1), (a.K + 127) / 128);
+            want = std::max(1, std::min(want, 128));
+            int kc = (a.K + want - 1) / want;
+            kc = ((kc + align - 1) / align) * align;
+            const int sp = (a.K + kc - 1) / kc;
+            if (sp > 1) {
+                splits = sp;
+                kchunk = kc;
+            }
+        }
+    };
+    split_k((long long)((a.M + a.tile - 1) / a.tile) * ((a.N + a.tile - 1) / a.tile) * a.nb, 16,
+            a.splits, a.kchunk);
+    split_k((long long)((a.M + 127) / 128) * ((a.N + 63) / 64) * a.nb, 32, a.tc_splits,
+            a.tc_kchunk);
+    const int max_splits = mixed_build ? std::max(a.splits, a.tc_splits) : a.splits;
+    if (max_splits > 1) st->partial_need = (size_t)a.nb * max_splits * (size_t)a.M * a.N;
     st->flops = 2LL * a.M * a.N * (long long)a.K * a.nb;
     net.ctr_steps.push_back(st.get());
     net.splitk_need[cur_stream] = std::max(net.splitk_need[cur_stream], st->partial_need);
@@ -467,8 +479,9 @@ Engine::PPair Engine::projector(Network& net, Plan& P, const Ten& U, const Ten& 
     push(P, std::make_unique<FnStep>(
         [=](cudaStream_t s) { launch_signfix(Us, Vs, n, chi, vt, s); }));
     double* scale = dalloc(chi);
-    const double cut = cutoff;
-    push(P, std::make_unique<FnStep>([=](cudaStream_t s) { launch_scalevec(S, chi, cut, scale, s); }));
+    const Network* np = &net;  // the cutoff is read at launch time: it follows set_precision
+    push(P, std::make_unique<FnStep>(
+        [=](cudaStream_t s) { launch_scalevec(S, chi, np->cutoff_now, scale, s); }));
     // Us[r', c] = Us[r' + c n]; V[r, c] = Vs[r + c n] (polar) or Vs[c + r n] (QR: V^T)
     Ten V, Uv;
     V.p = Vs;
@@ -487,8 +500,11 @@ Engine::PPair Engine::projector(Network& net, Plan& P, const Ten& U, const Ten& 
         V.st[rl.size()] = vt ? 1 : n;
     }
     PPair pp;
+    const bool mixed = mixed_build;
+    mixed_build = false;  // projector formation stays FP64
     pp.PB = ctr(net, P, labels + "," + rl + K + "->" + tl + K, U, V, nullptr, nullptr, scale);
     pp.PT = ctr(net, P, rlL + K + "," + Llab + "->" + K + tl, Uv, L, nullptr, scale, nullptr);
+    mixed_build = mixed;
     return pp;
 }
 
@@ -852,17 +868,36 @@ void Engine::build_network(Network& net) {
     net.dS = dalloc(1);
     net.lnk = dalloc(2);
     net.E = alloc({net.p, D, D, D, D});
+    mixed_build = true;
     for (int m = 0; m < 4; ++m) build_left_move(*this, net, net.move[m], make_frame(net, m));
+    mixed_build = false;
     build_spectrum(*this, net);
     build_local(*this, net);
     finalize(net);
+    set_precision(net, precision);
+}
+
+double Engine::cutoff_floor(int prec) {
+    switch (prec) {
+        case SCTM_PREC_TF32: return 1e-3;    // 11-bit significand
+        case SCTM_PREC_BF16: return 1e-2;    // 8-bit significand
+        case SCTM_PREC_TF32X3:
+        case SCTM_PREC_BF16X3: return 1e-6;  // hi/lo: about FP32 (FP32 accumulation)
+        default: return 0.0;
+    }
+}
+
+void Engine::set_precision(Network& net, int prec) {
+    for (CtrStep* s : net.ctr_steps) s->a.precision = s->mixed_ok ? prec : SCTM_PREC_FP64;
+    net.precision = prec;
+    net.cutoff_now = std::max(cutoff, cutoff_floor(prec));
 }
 
 void Engine::finalize(Network& net) {
     for (int k = 0; k < kStreams; ++k)
         if (net.splitk_need[k] > 0) net.splitk_ws[k] = dalloc((long long)net.splitk_need[k]);
     for (CtrStep* s : net.ctr_steps)
-        if (s->a.splits > 1) s->a.partial = net.splitk_ws[s->sid];
+        if (s->partial_need > 0) s->a.partial = net.splitk_ws[s->sid];
     void* p = nullptr;
     if (!dry) {
         CUDA_OK(cudaMalloc(&p, std::max(net.n_svd, 1) * sizeof(int)));

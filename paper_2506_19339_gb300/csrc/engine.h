@@ -78,6 +78,8 @@ struct Network {
     size_t svd_hbytes = 0;
     int svd_nmax = 1;
     std::vector<struct CtrStep*> ctr_steps;
+    int precision = SCTM_PREC_FP64;  // form of the mixed-eligible contractions (set_precision)
+    double cutoff_now = 0.0;         // pseudo-inverse cutoff in use (raised for mixed forms)
     std::vector<struct SvdStep*> svd_steps;
 };
 
@@ -103,8 +105,17 @@ public:
     static thread_local int cur_lane;
     Lane& lane() { return lanes[cur_lane]; }
     cusolverDnParams_t solver_params = nullptr;
-    int precision;
+    int precision;      // SCTM_PREC_* currently set on the move plans' contractions
     double cutoff;
+    int* dev_err = nullptr;  // device flag: a tensor-core contraction's bounded wait ran out
+    bool mixed_build = false;  // contractions built now may run in a mixed-precision form
+    // Arithmetic of the move plans' mixed-eligible contractions (absorption, half patches,
+    // rho_B rho_T, renormalisation); projector formation, the spectrum and the local
+    // contractions stay FP64.
+    void set_precision(Network& net, int prec);
+    // Smallest useful pseudo-inverse cutoff s_k/s_1 for a contraction form: below it the
+    // singular values of rho_B rho_T are rounding noise of that form.
+    static double cutoff_floor(int prec);
     int svd_mode = SCTM_SVD_QR;
     bool dry = false;  // SCTM_DRYRUN=1: build plans with placeholder pointers, no CUDA calls
     int cur_stream = 0;  // stream index given to steps while a plan is being built

@@ -140,7 +140,20 @@ __global__ void ctr_splitk_reduce_kernel(const CtrLaunch a) {
     }
 }
 
-void launch_ctr(const CtrLaunch& a, cudaStream_t s) {
+void launch_ctr(const CtrLaunch& a0, cudaStream_t s) {
+    if (a0.precision != SCTM_PREC_FP64) {
+        CtrLaunch a = a0;
+        a.splits = a0.tc_splits;
+        a.kchunk = a0.tc_kchunk;
+        launch_ctr_tc(a, s);
+        if (a.splits > 1) {
+            const long long total = (long long)a.M * a.N * a.nb;
+            int blocks = (int)std::min<long long>((total + 255) / 256, 4096);
+            ctr_splitk_reduce_kernel<<<blocks, 256, 0, s>>>(a);
+        }
+        return;
+    }
+    const CtrLaunch& a = a0;
     const int bm = a.tile, bn = a.tile;
     dim3 grid((a.N + bn - 1) / bn, (a.M + bm - 1) / bm, a.nb * a.splits);
     if (a.tile == 32)

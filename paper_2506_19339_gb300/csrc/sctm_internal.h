@@ -38,10 +38,14 @@ struct CtrLaunch {
     int splits = 1;
     int kchunk = 1;
     int precision = 0;                 // SCTM_PREC_*
-    int tile = 64;                     // CTA output tile: 64 x 64 or 32 x 32
+    int tile = 64;                     // CTA output tile: 64 x 64 or 32 x 32 (FP64 kernel)
+    int* err = nullptr;                // set to 1 by the tensor-core kernel on a wait timeout
+    int tc_splits = 1, tc_kchunk = 1;  // split-K of the tensor-core kernel (128 x 64 tiles)
 };
 
 void launch_ctr(const CtrLaunch& a, cudaStream_t s);
+// tensor-core variant (a.precision = SCTM_PREC_TF32 / TF32X3 / BF16 / BF16X3), 128 x 64 tiles
+void launch_ctr_tc(const CtrLaunch& a, cudaStream_t s);
 
 // ---------------------------------------------------------------------------------------------
 // auxiliary kernels

@@ -33,3 +33,9 @@ def product_plus_peps(D=1, p=2):
 def temperature_sweep(n=32, lo=4.40, hi=4.62):
     """n temperatures uniform in [lo, hi] (linspace)."""
     return np.linspace(lo, hi, n)
+
+
+def random_matrix(rows, cols, seed):
+    """A (rows x cols) matrix with i.i.d. N(0,1) entries (numpy PCG64 stream `seed`), the operand
+    recipe of the plain contraction tests."""
+    return np.random.default_rng(seed).standard_normal((rows, cols))

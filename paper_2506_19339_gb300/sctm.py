@@ -70,6 +70,7 @@ def load():
         'sctm_spectrum': (I, [P, I, P]),
         'sctm_local_values': (I, [P, I, P]),
         'sctm_gemm_noalloc': (I, [P, P, P, I, I, I, P]),
+        'sctm_gemm': (I, [P, P, P, I, I, I, I, P]),
         'sctm_iterate_batch': (I, [ctypes.POINTER(P), I, I, D, ctypes.POINTER(I),
                                    ctypes.POINTER(I), ctypes.POINTER(D)]),
         'sctm_device_bytes': (S, [P]),
@@ -183,6 +184,12 @@ def sctm_gemm_noalloc(X, Y, O, M, N, K, stream=None):
     """O = X Y (row-major device tensors, FP64) without any device allocation in the library."""
     return load().sctm_gemm_noalloc(_ptr(X), _ptr(Y), _ptr(O), int(M), int(N), int(K),
                                     ctypes.c_void_p(stream))
+
+
+def sctm_gemm(X, Y, O, M, N, K, precision, stream=None):
+    """O = X Y (row-major device matrices) in the given SCTM_PREC_* form; returns the status."""
+    return load().sctm_gemm(_ptr(X), _ptr(Y), _ptr(O), int(M), int(N), int(K), int(precision),
+                            ctypes.c_void_p(stream))
 
 
 def sctm_iterate_batch(ctxs, max_it, tol):

@@ -1,0 +1,125 @@
+"""GPU: the mixed-precision forms of the contractions (tensor cores, tcgen05) against FP64.
+
+The kernel test bounds the elementwise error by c (|X||Y|)_ij, c from the operand format: the hi
+part of x keeps the format's significand (11 bits TF32, 8 bits BF16), the hi/lo pair about twice
+that, and the FP32 accumulator adds ~sqrt(K) 2^-24 on random data.  The iteration tests check
+that a mixed-form run followed by the FP64 polish reaches the FP64 fixed point (f to 1e-10), and
+that a run of mixed-form iterations alone lands within the form's error of the FP64 one."""
+import numpy as np
+import pytest
+
+from oracle import ising, split_ctmrg as sc
+from paper_2506_19339_gb300 import build, inputs, sctm
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip('torch')
+
+FORMS = {
+    # precision: (elementwise c in |O - XY| <= c |X||Y|, relative Frobenius error bound)
+    sctm.SCTM_PREC_FP64: (1e-13, 1e-14),
+    sctm.SCTM_PREC_TF32: (2e-3, 1e-3),
+    sctm.SCTM_PREC_TF32X3: (2e-5, 2e-6),
+    sctm.SCTM_PREC_BF16: (1.6e-2, 8e-3),
+    sctm.SCTM_PREC_BF16X3: (1e-4, 3e-5),
+}
+
+
+@pytest.fixture(scope='module', autouse=True)
+def lib():
+    build.build()
+    return sctm.load()
+
+
+def _gemm(X, Y, prec):
+    M, K = X.shape
+    N = Y.shape[1]
+    dX = torch.from_numpy(X).cuda()
+    dY = torch.from_numpy(Y).cuda()
+    dO = torch.full((M, N), float('nan'), dtype=torch.float64, device='cuda')
+    torch.cuda.synchronize()
+    st = sctm.sctm_gemm(dX, dY, dO, M, N, K, prec, torch.cuda.current_stream().cuda_stream)
+    assert st == sctm.SCTM_OK, st
+    return dO.cpu().numpy()
+
+
+@pytest.mark.parametrize('M,N,K', [
+    (1, 1, 1),          # one element, one partial K chunk
+    (129, 65, 33),      # ragged in every dimension: two M tiles, two N tiles, two K chunks
+    (300, 200, 1000),   # several tiles and K chunks
+    (64, 64, 5000),     # one tile: K split across CTAs, FP64 split-K reduction
+    (1000, 1000, 64),   # grid of 8 x 16 tiles, short K
+])
+@pytest.mark.parametrize('prec', sorted(FORMS))
+def test_gemm_forms(M, N, K, prec):
+    X = inputs.random_matrix(M, K, 11)
+    Y = inputs.random_matrix(K, N, 12)
+    O = _gemm(X, Y, prec)
+    ref = X @ Y
+    bound = np.abs(X) @ np.abs(Y)
+    c, rel = FORMS[prec]
+    assert np.all(np.isfinite(O))
+    assert np.all(np.abs(O - ref) <= c * bound + 1e-300), np.max(np.abs(O - ref) / bound)
+    assert np.linalg.norm(O - ref) <= rel * np.linalg.norm(ref)
+
+
+def test_split_products_are_used():
+    """The hi/lo forms must be far more accurate than the plain ones (the lo terms are added)."""
+    X = inputs.random_matrix(256, 512, 21)
+    Y = inputs.random_matrix(512, 192, 22)
+    ref = X @ Y
+    err = {p: np.linalg.norm(_gemm(X, Y, p) - ref) / np.linalg.norm(ref) for p in FORMS}
+    assert err[sctm.SCTM_PREC_TF32X3] < err[sctm.SCTM_PREC_TF32] / 100
+    assert err[sctm.SCTM_PREC_BF16X3] < err[sctm.SCTM_PREC_BF16] / 50
+    assert err[sctm.SCTM_PREC_TF32] < err[sctm.SCTM_PREC_BF16]
+    assert err[sctm.SCTM_PREC_FP64] < 1e-14
+
+
+def test_gemm_rejects_bad_arguments():
+    X = torch.zeros(4, 4, dtype=torch.float64, device='cuda')
+    h = np.zeros((4, 4))
+    assert sctm.sctm_gemm(X, X, X, 4, 4, 4, 7, None) == sctm.SCTM_EINVAL
+    assert sctm.sctm_gemm(X, X, X, 0, 4, 4, 0, None) == sctm.SCTM_EINVAL
+    assert sctm.sctm_gemm(h, X, X, 4, 4, 4, 0, None) == sctm.SCTM_EINVAL
+
+
+def _ctx(A, T, chi, prec):
+    st, O = sctm.sctm_ising_pepo(T)
+    return sctm.SplitCTMRG(A, O, chi, T, precision=prec)
+
+
+@pytest.mark.parametrize('prec', [sctm.SCTM_PREC_TF32, sctm.SCTM_PREC_TF32X3,
+                                  sctm.SCTM_PREC_BF16, sctm.SCTM_PREC_BF16X3])
+def test_mixed_then_polish_reaches_fp64_fixed_point(prec):
+    """Mixed-form iterations until the spectrum change stalls, then FP64 iterations to the
+    tolerance: the converged f equals the oracle's converged f (contractive input)."""
+    T, D, chi = 4.6, 2, 16
+    A = inputs.perturbed_product_peps(D, 7)
+    r = _ctx(A, T, chi, prec)
+    try:
+        st, it, ds = r.iterate(300, 1e-11)
+        assert st == sctm.SCTM_OK and ds < 1e-11, (st, it, ds)
+        f = r.free_energy()
+    finally:
+        r.close()
+    ref = sc.evaluate(A, ising.ising_pepo(1 / T), ising.identity_pepo(), T, chi, 300, 1e-11)
+    assert abs(f - ref['f']) <= 1e-10 * abs(ref['f']), (f, ref['f'])
+
+
+@pytest.mark.parametrize('prec,tol', [(sctm.SCTM_PREC_TF32X3, 1e-6), (sctm.SCTM_PREC_BF16X3, 1e-5),
+                                      (sctm.SCTM_PREC_TF32, 1e-3), (sctm.SCTM_PREC_BF16, 1e-2)])
+def test_mixed_iterations_alone(prec, tol):
+    """Four iterations in the mixed form only (no FP64 polish: the spectrum change still falls)
+    against the same four FP64 iterations: f differs by the form's error, and not by zero (the
+    tensor-core kernel ran)."""
+    T, D, chi = 4.6, 2, 16
+    A = inputs.perturbed_product_peps(D, 7)
+    fs = {}
+    for p in (sctm.SCTM_PREC_FP64, prec):
+        r = _ctx(A, T, chi, p)
+        try:
+            r.iterate(4, 0.0)
+            fs[p] = r.free_energy()
+        finally:
+            r.close()
+    d = abs(fs[prec] - fs[sctm.SCTM_PREC_FP64]) / abs(fs[sctm.SCTM_PREC_FP64])
+    assert 0.0 < d <= tol, d
