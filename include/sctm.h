@@ -55,12 +55,21 @@ enum {
 
 enum { SCTM_GRAD_ENV = 0, SCTM_GRAD_ADJOINT = 1 };
 /* FP64 SVD of the projector matrices (Eq. "projector construction"):
- *   SCTM_SVD_QR     cuSOLVER gesvd (bidiagonalisation + QR iteration), the reference path: its
- *                   singular vectors stay accurate down to the pseudo-inverse cutoff
- *   SCTM_SVD_POLAR  cuSOLVER gesvdp (polar decomposition + symmetric eigensolver): about 3x
- *                   faster at n = 512 with the same singular values, but less accurate vectors
- *                   for the smallest kept singular values (f moves at the 1e-10 level) */
-enum { SCTM_SVD_QR = 0, SCTM_SVD_POLAR = 1 };
+ *   SCTM_SVD_QR       cuSOLVER gesvd (bidiagonalisation + QR iteration), the reference path: its
+ *                     singular vectors stay accurate down to the pseudo-inverse cutoff
+ *   SCTM_SVD_POLAR    cuSOLVER gesvdp (polar decomposition + symmetric eigensolver): about 3x
+ *                     faster at n = 512 with the same singular values, but less accurate vectors
+ *                     for the smallest kept singular values (f moves at the 1e-10 level)
+ *   SCTM_SVD_PARTIAL  the partial SVD of Sec. III (largest chi triplets by an iterative
+ *                     solver): the first solve of each projector after a cold start is gesvd,
+ *                     every later one a subspace-iteration step warm-started from the previous
+ *                     iteration's right singular subspace (chi + max(8, chi/4) columns) with a
+ *                     Rayleigh-Ritz (Jacobi) extraction, about 25 kernel launches instead of
+ *                     thousands.  Projectors whose subspace would exceed 112 columns stay on
+ *                     gesvd.  The fixed point is the same as SCTM_SVD_QR's; a trajectory from a
+ *                     cold start differs at the level of the subspace error of the early
+ *                     iterations.  sctm_env_import and a reset start cold again. */
+enum { SCTM_SVD_QR = 0, SCTM_SVD_POLAR = 1, SCTM_SVD_PARTIAL = 2 };
 enum { SCTM_NET_NUM = 0, SCTM_NET_DEN = 1 };          /* <psi|T|psi> and <psi|psi>            */
 enum { SCTM_MOVE_LEFT = 0, SCTM_MOVE_RIGHT = 1, SCTM_MOVE_UP = 2, SCTM_MOVE_DOWN = 3 };
 

@@ -141,7 +141,8 @@ sctm_status sctm_create(const double* peps, const double* pepo, int chi, const s
         opts.precision < SCTM_PREC_FP64 || opts.precision > SCTM_PREC_BF16X3 ||
         opts.grad_mode != SCTM_GRAD_ENV ||
         !(opts.svd_cutoff >= 0.0) || opts.D > 64 || opts.d > 64 || opts.p > 64 ||
-        (opts.svd_mode != SCTM_SVD_QR && opts.svd_mode != SCTM_SVD_POLAR))
+        (opts.svd_mode != SCTM_SVD_QR && opts.svd_mode != SCTM_SVD_POLAR &&
+         opts.svd_mode != SCTM_SVD_PARTIAL))
         return SCTM_EINVAL;
     std::unique_ptr<sctm_ctx> c(new sctm_ctx());
     c->opts = opts;
@@ -403,6 +404,7 @@ static sctm_status env_copy(sctm_ctx* ctx, int network, double* host, size_t n, 
             cuda_ok(cudaMemcpy(t->p, host + off, bytes, cudaMemcpyHostToDevice), "env import");
         off += (size_t)t->numel();
     }
+    if (!to_host) ctx->eng->cold_svd(net);  // the warm-start subspaces belong to the old state
     return SCTM_OK;
     API_END(ctx)
 }

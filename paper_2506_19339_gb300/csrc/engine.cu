@@ -105,6 +105,20 @@ struct SvdStep : Step {
     }
 };
 
+// The partial SVD of one projector matrix: a full SVD (cold) while no warm-start subspace
+// exists, the warm-started subspace iteration step otherwise (psvd.cu has the algorithm).
+struct PartialSvdStep : Step {
+    Plan cold, warm;
+    bool is_warm = false;
+    bool can_warm = true;  // false when the subspace exceeds the one-CTA kernels' limit
+    void run(Engine& e) override {
+        const int e0 = e.profile ? e.record(sid) : -1;
+        e.run_sub(is_warm ? warm : cold);
+        is_warm = can_warm;
+        if (e.profile) e.record_done(sid, KIND_SVD, 0, e0);
+    }
+};
+
 struct FnStep : Step {
     std::function<void(cudaStream_t)> f;
     explicit FnStep(std::function<void(cudaStream_t)> g) : f(std::move(g)) {}
@@ -460,22 +474,98 @@ Engine::PPair Engine::projector(Network& net, Plan& P, const Ten& U, const Ten& 
         }
     }
     ctr(net, P, Llab + "," + labels + "->" + rlL + rl, L, U, &M);
+    const bool mixed = mixed_build;
+    mixed_build = false;  // the SVD and the projector formation stay FP64
     double* S = dalloc(n);
     double* Us = dalloc((long long)n * n);
     double* Vs = dalloc((long long)n * n);
-    auto sv = std::make_unique<SvdStep>();
-    sv->M = M.p;
-    sv->n = n;
-    sv->S = S;
-    sv->U = Us;
-    sv->V = Vs;
-    sv->vectors = true;
-    sv->net = &net;
-    sv->info_idx = net.n_svd++;
-    net.svd_nmax = std::max(net.svd_nmax, n);
-    net.svd_steps.push_back(sv.get());
-    push(P, std::move(sv));
-    const int vt = svd_mode == SCTM_SVD_POLAR ? 0 : 1;  // gesvd returns V^T
+    // V layout: columns (gesvdp, partial SVD) or rows = V^T (gesvd)
+    const int vt = svd_mode == SCTM_SVD_QR ? 1 : 0;
+    auto make_svd = [&](double* Vout) {
+        auto sv = std::make_unique<SvdStep>();
+        sv->M = M.p;
+        sv->n = n;
+        sv->S = S;
+        sv->U = Us;
+        sv->V = Vout;
+        sv->vectors = true;
+        sv->net = &net;
+        sv->info_idx = net.n_svd++;
+        net.svd_nmax = std::max(net.svd_nmax, n);
+        net.svd_steps.push_back(sv.get());
+        return sv;
+    };
+    if (svd_mode != SCTM_SVD_PARTIAL) {
+        push(P, make_svd(Vs));
+    } else {
+        // subspace of chi + oversampling columns (Sec. III's partial SVD); the cold solve is
+        // gesvd with its V^T turned into columns, the warm one the subspace iteration step
+        const int over = std::max(8, chi / 4);
+        const int k = std::min(n, chi + over);
+        auto ps = std::make_unique<PartialSvdStep>();
+        ps->can_warm = k <= kPsvdMaxK;
+        double* VT = dalloc((long long)n * n);
+        {
+            Plan& C = ps->cold;
+            push(C, make_svd(VT));
+            const int kc = ps->can_warm ? k : chi;
+            push(C, std::make_unique<FnStep>(
+                        [=](cudaStream_t s) { launch_vt_columns(VT, Vs, n, kc, s); }));
+        }
+        if (ps->can_warm) {
+            Plan& W = ps->warm;
+            auto mat = [&](double* p, int rows, int cols) {
+                Ten t;
+                t.p = p;
+                t.nd = 2;
+                t.dim[0] = rows;
+                t.dim[1] = cols;
+                t.st[0] = 1;
+                t.st[1] = rows;
+                return t;
+            };
+            double* Yb = dalloc((long long)n * k);
+            double* Q1 = dalloc((long long)n * k);
+            double* Qy = dalloc((long long)n * k);
+            double* Zb = dalloc((long long)n * k);
+            double* G = dalloc((long long)k * k);
+            double* Tm = dalloc((long long)k * k);
+            double* R1 = dalloc((long long)k * k);
+            double* R2 = dalloc((long long)k * k);
+            double* Ur = dalloc((long long)k * k);
+            double* Wr = dalloc((long long)k * k);
+            const int info_idx = net.n_svd++;
+            const Network* np = &net;  // svd_info is allocated after the plans are built
+            const Ten Mv = mat(M.p, n, n);  // M[r', r] at r' + r n
+            const Ten Vb = mat(Vs, n, k), Ut = mat(Us, n, k);
+            const Ten Gt = mat(G, k, k), Tt = mat(Tm, k, k), Wt = mat(Wr, k, k), Urt = mat(Ur, k, k);
+            // two passes of column-scaled Cholesky QR: src -> dst (orthonormal), factor in R2
+            auto cholqr2 = [&](double* src, double* tmp, double* dst) {
+                const Ten a = mat(src, n, k), b = mat(tmp, n, k), c = mat(dst, n, k);
+                ctr(net, W, "ac,ad->cd", a, a, &Gt);
+                push(W, std::make_unique<FnStep>(
+                            [=](cudaStream_t s) { launch_chol_orth(G, k, nullptr, Tm, R1, s); }));
+                ctr(net, W, "ac,cd->ad", a, Tt, &b);
+                ctr(net, W, "ac,ad->cd", b, b, &Gt);
+                push(W, std::make_unique<FnStep>(
+                            [=](cudaStream_t s) { launch_chol_orth(G, k, R1, Tm, R2, s); }));
+                ctr(net, W, "ac,cd->ad", b, Tt, &c);
+            };
+            const Ten Ybt = mat(Yb, n, k), Qyt = mat(Qy, n, k), Zbt = mat(Zb, n, k),
+                      Q1t = mat(Q1, n, k);
+            ctr(net, W, "ab,bc->ac", Mv, Vb, &Ybt);   // Y = M V_prev
+            cholqr2(Yb, Q1, Qy);                      // Q_y
+            ctr(net, W, "ba,bc->ac", Mv, Qyt, &Zbt);  // Z = M^T Q_y
+            cholqr2(Zb, Yb, Q1);                      // Q_z (in Q1), R_z (in R2)
+            push(W, std::make_unique<FnStep>([=](cudaStream_t s) {
+                launch_jacobi_svd(R2, k, S, Ur, Wr, np->svd_info + info_idx, s);
+            }));
+            ctr(net, W, "ac,cd->ad", Qyt, Wt, &Ut);   // U = Q_y W
+            ctr(net, W, "ac,cd->ad", Q1t, Urt, &Vb);  // V = Q_z U_r
+        }
+        net.psvd_steps.push_back(ps.get());
+        push(P, std::move(ps));
+    }
     push(P, std::make_unique<FnStep>(
         [=](cudaStream_t s) { launch_signfix(Us, Vs, n, chi, vt, s); }));
     double* scale = dalloc(chi);
@@ -500,8 +590,6 @@ Engine::PPair Engine::projector(Network& net, Plan& P, const Ten& U, const Ten& 
         V.st[rl.size()] = vt ? 1 : n;
     }
     PPair pp;
-    const bool mixed = mixed_build;
-    mixed_build = false;  // projector formation stays FP64
     pp.PB = ctr(net, P, labels + "," + rl + K + "->" + tl + K, U, V, nullptr, nullptr, scale);
     pp.PT = ctr(net, P, rlL + K + "," + Llab + "->" + K + tl, Uv, L, nullptr, scale, nullptr);
     mixed_build = mixed;
@@ -845,7 +933,12 @@ static void build_local(Engine& e, Network& net) {
         [=](cudaStream_t s) { launch_lnkappa(z00, z10, z01, z11, lnk, s); }));
 }
 
+void Engine::cold_svd(Network& net) {
+    for (PartialSvdStep* p : net.psvd_steps) p->is_warm = false;
+}
+
 void Engine::init_env(Network& net, unsigned long long seed) {
+    cold_svd(net);
     if (dry) return;
     unsigned long long q = 0;
     for (int i = 0; i < 4; ++i) launch_splitmix_fill(net.C[i].p, net.C[i].numel(), seed, q++, stream);

@@ -78,6 +78,7 @@ struct Network {
     size_t svd_hbytes = 0;
     int svd_nmax = 1;
     std::vector<struct CtrStep*> ctr_steps;
+    std::vector<struct PartialSvdStep*> psvd_steps;  // warm-started SVDs (SCTM_SVD_PARTIAL)
     int precision = SCTM_PREC_FP64;  // form of the mixed-eligible contractions (set_precision)
     double cutoff_now = 0.0;         // pseudo-inverse cutoff in use (raised for mixed forms)
     std::vector<struct SvdStep*> svd_steps;
@@ -161,6 +162,8 @@ public:
     void finalize(Network& net);
     void run(Plan& P);
     void init_env(Network& net, unsigned long long seed);
+    // Forget the warm-start subspaces of the partial SVDs: the next solve of each is a full one.
+    void cold_svd(Network& net);
     // Independent sub-plans, each on its own stream and host thread (stream i+1 for sub[i]):
     // they start after everything already on stream 0 and stream 0 waits for all of them.
     void parallel(Plan& P, std::vector<Plan>&& sub);

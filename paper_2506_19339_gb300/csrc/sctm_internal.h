@@ -64,6 +64,13 @@ void launch_scalevec(const double* S, int k, double cutoff, double* out, cudaStr
 // vt = 1: V holds V^T (gesvd layout); vt = 0: V holds the right vectors as columns
 void launch_signfix(double* U, double* V, int n, int k, int vt, cudaStream_t s);
 void launch_copy(const double* src, double* dst, long long n, cudaStream_t s);
+// partial SVD (psvd.cu): column-scaled Cholesky QR pass, one-CTA Jacobi SVD, V^T -> columns
+constexpr int kPsvdMaxK = 112;  // largest subspace (chi + oversampling) the one-CTA kernels take
+void launch_chol_orth(const double* G, int k, const double* Rprev, double* T, double* Rout,
+                      cudaStream_t s);
+void launch_jacobi_svd(const double* B, int k, double* S, double* U, double* W, int* info,
+                       cudaStream_t s);
+void launch_vt_columns(const double* VT, double* Vout, int n, int k, cudaStream_t s);
 void launch_zero(double* p, long long n, cudaStream_t s);
 // flag[0] = 1 if any of p[0..n) is NaN or infinite, else 0
 void launch_check_finite(const double* p, long long n, int* flag, cudaStream_t s);

@@ -95,13 +95,14 @@ def test_mixed_then_polish_reaches_fp64_fixed_point(prec):
     change below tol does not bound f's distance to the fixed point as tightly: the oracle's own f
     moves by 6.4e-11 (relative) between stopping at ||dS|| < 1e-11 and < 1e-13 on this input, and
     a trajectory that comes from the mixed form approaches along other directions, so the two
-    converged values are compared at 1e-9."""
+    converged values are compared at 1e-9.  The GPU run stops at 1e-11: its FP64 spectrum change
+    levels off near 1e-12 on this input."""
     T, D, chi = 4.6, 2, 16
     A = inputs.perturbed_product_peps(D, 7)
     r = _ctx(A, T, chi, prec)
     try:
-        st, it, ds = r.iterate(400, 1e-12)
-        assert st == sctm.SCTM_OK and ds < 1e-12, (st, it, ds)
+        st, it, ds = r.iterate(400, 1e-11)
+        assert st == sctm.SCTM_OK and ds < 1e-11, (st, it, ds)
         f = r.free_energy()
     finally:
         r.close()
