@@ -66,20 +66,22 @@ def test_host_side_error_paths(lib):
     assert lib.sctm_free_energy(None, None) == sctm.SCTM_EINVAL
 
 
-@pytest.mark.parametrize('D,d,chi', [(1, 2, 1), (2, 2, 5), (3, 2, 10), (4, 2, 64), (2, 3, 7)])
-def test_plans_build_without_gpu(lib, D, d, chi):
+@pytest.mark.parametrize('D,d,chi,svd', [(1, 2, 1, 0), (2, 2, 5, 0), (3, 2, 10, 0), (4, 2, 64, 0),
+                                         (2, 3, 7, 0), (2, 2, 5, 2), (4, 2, 64, 2), (3, 2, 100, 2)])
+def test_plans_build_without_gpu(lib, D, d, chi, svd):
     """SCTM_DRYRUN=1 builds every plan (four moves, convergence, local contractions) of both
     networks with placeholder pointers: every contraction's labels, dimensions and ranks are
-    checked on the CPU."""
+    checked on the CPU, for the full (svd 0) and the partial (svd 2) SVD plans; chi = 100 has
+    subspaces above the one-CTA limit, which stay on the full SVD."""
     import subprocess
     import sys
     code = ('import numpy as np\n'
             'from paper_2506_19339_gb300 import sctm\n'
             'st, o = sctm.sctm_default_opts()\n'
-            'o.D, o.d = %d, %d\n'
+            'o.D, o.d, o.svd_mode = %d, %d, %d\n'
             'A = np.zeros((2,) + (%d,) * 4); O = np.zeros((2, 2) + (%d,) * 4)\n'
             'st, ctx = sctm.sctm_create(A, O, %d, o)\n'
-            'print(st)\n') % (D, d, D, d, chi)
+            'print(st)\n') % (D, d, svd, D, d, chi)
     env = dict(os.environ, SCTM_DRYRUN='1')
     out = subprocess.run([sys.executable, '-c', code], cwd=ROOT, env=env, capture_output=True,
                          text=True, timeout=300)
