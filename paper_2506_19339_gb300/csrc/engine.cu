@@ -528,10 +528,10 @@ Engine::PPair Engine::projector(Network& net, Plan& P, const Ten& U, const Ten& 
             double* Q1 = dalloc((long long)n * k);
             double* Qy = dalloc((long long)n * k);
             double* Zb = dalloc((long long)n * k);
+            double* Qz = dalloc((long long)n * k);
             double* G = dalloc((long long)k * k);
             double* Tm = dalloc((long long)k * k);
             double* R1 = dalloc((long long)k * k);
-            double* R2 = dalloc((long long)k * k);
             double* Ur = dalloc((long long)k * k);
             double* Wr = dalloc((long long)k * k);
             const int info_idx = net.n_svd++;
@@ -539,29 +539,36 @@ Engine::PPair Engine::projector(Network& net, Plan& P, const Ten& U, const Ten& 
             const Ten Mv = mat(M.p, n, n);  // M[r', r] at r' + r n
             const Ten Vb = mat(Vs, n, k), Ut = mat(Us, n, k);
             const Ten Gt = mat(G, k, k), Tt = mat(Tm, k, k), Wt = mat(Wr, k, k), Urt = mat(Ur, k, k);
-            // two passes of column-scaled Cholesky QR: src -> dst (orthonormal), factor in R2
-            auto cholqr2 = [&](double* src, double* tmp, double* dst) {
-                const Ten a = mat(src, n, k), b = mat(tmp, n, k), c = mat(dst, n, k);
-                ctr(net, W, "ac,ad->cd", a, a, &Gt);
-                push(W, std::make_unique<FnStep>(
-                            [=](cudaStream_t s) { launch_chol_orth(G, k, nullptr, Tm, R1, s); }));
-                ctr(net, W, "ac,cd->ad", a, Tt, &b);
-                ctr(net, W, "ac,ad->cd", b, b, &Gt);
-                push(W, std::make_unique<FnStep>(
-                            [=](cudaStream_t s) { launch_chol_orth(G, k, R1, Tm, R2, s); }));
-                ctr(net, W, "ac,cd->ad", b, Tt, &c);
+            // shifted Cholesky QR shift for the unit-diagonal scaled Gram matrix
+            const double shift = 11.0 * ((double)n * k + (double)k * (k + 1)) * 0x1.0p-53;
+            // three passes of column-scaled Cholesky QR (shifted, shifted, plain): a -> b -> c -> dst
+            auto cholqr3 = [&](double* a, double* b, double* c, double* dst) {
+                double* from[3] = {a, b, c};
+                double* to[3] = {b, c, dst};
+                for (int pass = 0; pass < 3; ++pass) {
+                    const Ten x = mat(from[pass], n, k), y = mat(to[pass], n, k);
+                    ctr(net, W, "ac,ad->cd", x, x, &Gt);
+                    const double sh = pass < 2 ? shift : 0.0;
+                    push(W, std::make_unique<FnStep>(
+                                [=](cudaStream_t s) { launch_chol_orth(G, k, sh, Tm, s); }));
+                    ctr(net, W, "ac,cd->ad", x, Tt, &y);
+                }
             };
             const Ten Ybt = mat(Yb, n, k), Qyt = mat(Qy, n, k), Zbt = mat(Zb, n, k),
-                      Q1t = mat(Q1, n, k);
+                      Qzt = mat(Qz, n, k), Bt = mat(R1, k, k);
             ctr(net, W, "ab,bc->ac", Mv, Vb, &Ybt);   // Y = M V_prev
-            cholqr2(Yb, Q1, Qy);                      // Q_y
+            cholqr3(Yb, Q1, Zb, Qy);                  // Q_y
             ctr(net, W, "ba,bc->ac", Mv, Qyt, &Zbt);  // Z = M^T Q_y
-            cholqr2(Zb, Yb, Q1);                      // Q_z (in Q1), R_z (in R2)
+            cholqr3(Zb, Yb, Q1, Qz);                  // Q_z
+            ctr(net, W, "ac,ad->cd", Zbt, Qzt, &Bt);  // B = Z^T Q_z = Q_y^T M Q_z
             push(W, std::make_unique<FnStep>([=](cudaStream_t s) {
-                launch_jacobi_svd(R2, k, S, Ur, Wr, np->svd_info + info_idx, s);
+                launch_jacobi_svd(R1, k, S, Ur, Wr, np->svd_info + info_idx, s);
             }));
-            ctr(net, W, "ac,cd->ad", Qyt, Wt, &Ut);   // U = Q_y W
-            ctr(net, W, "ac,cd->ad", Q1t, Urt, &Vb);  // V = Q_z U_r
+            ctr(net, W, "ac,cd->ad", Qyt, Urt, &Ut);  // U = Q_y U_B
+            ctr(net, W, "ac,cd->ad", Qzt, Wt, &Vb);   // V = Q_z V_B
+            const unsigned long long salt = 0x5EEDull * (unsigned long long)(info_idx + 1);
+            push(W, std::make_unique<FnStep>(
+                        [=](cudaStream_t s) { launch_refill(Vs, n, k, S, salt, s); }));
         }
         net.psvd_steps.push_back(ps.get());
         push(P, std::move(ps));

@@ -5,22 +5,29 @@
 // right singular subspace of the previous iteration (k = chi + oversampling columns) is a warm
 // start.  One warm solve is a two-sided subspace iteration step with a Rayleigh-Ritz
 // extraction:
-//     Y = M V_prev,  Y = Q_y R_y          (Q_y: orthonormal basis of the left subspace)
-//     Z = M^T Q_y,   Z = Q_z R_z          (Q_z: improved right subspace)
-//     Q_y^T M Q_z = R_z^T;  R_z = U_r S W^T (k x k SVD)
-//     M ~ (Q_y W) S (Q_z U_r)^T           left vectors Q_y W, right vectors Q_z U_r.
-// The products with M and the basis updates run on the contraction kernel; the two kernels here
-// do the k x k work in one CTA each:
+//     Y = M V_prev,    Q_y = orth(Y)       (left subspace)
+//     Z = M^T Q_y,     Q_z = orth(Z)       (right subspace, one step of M^T M further)
+//     B = Z^T Q_z = Q_y^T M Q_z  (k x k),  B = U_B S V_B^T
+//     M ~ (Q_y U_B) S (Q_z V_B)^T.
+// The products with M, the Gram matrices and the basis updates run on the contraction kernel;
+// the kernels here do the k x k work in one CTA each:
 //   * chol_orth_kernel: one pass of column-scaled Cholesky QR.  With G = Y^T Y and D the column
-//     norms, G = D (R^T R) D; it returns T = D^-1 R^-1 (so that Y T is orthonormal) and the
-//     triangular factor R D (times the previous pass's factor).  The columns of Y are close to
-//     orthogonal in the warm regime (Y ~ U S), so the scaled Gram matrix is close to the identity
-//     and the factorisation keeps the relative accuracy of small columns; a second pass restores
-//     orthogonality to rounding.  Columns whose scaled pivot falls below 1e-20 are dependent:
-//     their basis column and factor row are set to zero.
-//   * jacobi_svd_kernel: one-sided (Hestenes) Jacobi SVD of the k x k factor, round-robin
-//     ordering of the k(k-1)/2 column pairs, sweeps until no pair is rotated (bounded), output
-//     sorted by decreasing singular value.
+//     norms, D^-1 G D^-1 + shift I = R^T R; it returns T = D^-1 R^-1, so that Y T is orthonormal
+//     up to the shift and rounding.  Column scaling keeps the relative accuracy of small
+//     columns (Y ~ U S in the warm regime).  Columns of the tail directions are dominated by the
+//     change of M since the last iteration and can be numerically dependent; the shift
+//     (Fukaya et al.'s shifted Cholesky QR: 11 (n k + k (k + 1)) u on the unit-diagonal scaled
+//     Gram matrix) keeps the factorisation positive definite, so three passes -- shifted,
+//     shifted, plain -- give an orthonormal basis without dropping columns.  A column that is
+//     exactly zero stays zero (pivot below 1e-20); refill_kernel puts a pseudo-random vector in
+//     its place before the next solve.
+//   * jacobi_svd_kernel: one-sided (Hestenes) Jacobi SVD of B, round-robin ordering of the
+//     k(k-1)/2 column pairs.  FP64 arithmetic is scarce on this GPU (about 1/64 of FP32), so the
+//     sweeps run first in FP32 (which converges W to about 1e-6), W is re-orthonormalised in FP64
+//     (Cholesky of W^T W), A = B W is formed in FP64 and FP64 sweeps finish from there: Jacobi
+//     converges quadratically, so one or two FP64 sweeps reach rounding level.  B's columns are
+//     the rows of the triangular factor of Z, graded by the singular values, which is the
+//     ordering under which one-sided Jacobi converges fastest.
 #include <algorithm>
 #include <mutex>
 
@@ -31,7 +38,8 @@ namespace sctm {
 namespace {
 
 constexpr int kPsvdThreads = 512;
-constexpr int kJacobiMaxSweeps = 40;
+constexpr int kJacobiMaxSweeps32 = 12;
+constexpr int kJacobiMaxSweeps64 = 20;
 constexpr double kPivotFloor = 1e-20;
 
 __device__ __forceinline__ double warp_allsum(double v) {
@@ -39,19 +47,102 @@ __device__ __forceinline__ double warp_allsum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
+__device__ __forceinline__ float warp_allsum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// In-place right-looking Cholesky of the symmetric k x k matrix in R (row-major, upper triangle
+// used).  Rows are left unscaled: on return the upper factor is F[j][c] = R[j][c] * rinv[j]
+// (c >= j), F[j][j] = R[j][j] * rinv[j] = sqrt(pivot j).  Pivots at or below kPivotFloor give
+// rinv = 0 (a zero row).  One barrier per column.  All threads call.
+__device__ void block_cholesky(double* R, double* rinv, int k) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int j = 0; j < k; ++j) {
+        const double piv = R[j * k + j];
+        const double ri = piv > kPivotFloor ? 1.0 / sqrt(piv) : 0.0;
+        if (tid == 0) rinv[j] = ri;
+        const double r2 = ri * ri;
+        const int m = k - j - 1;
+        for (int e = tid; e < m * m; e += nt) {
+            const int a = j + 1 + e / m, b = j + 1 + e % m;
+            if (b >= a) R[a * k + b] -= R[j * k + a] * R[j * k + b] * r2;
+        }
+        __syncthreads();
+    }
+}
+
+// One sweep of one-sided Jacobi rotations over all column pairs (circle-method rounds) of the
+// kp x kp column-major A, accumulating into the columns of V.  Pairs with
+// |a_i . a_j| <= tol |a_i| |a_j| are left alone.  Returns (to every thread) the largest
+// |a_i . a_j| / (|a_i| |a_j|) seen.
+template <typename F>
+__device__ float jacobi_sweep(F* A, F* V, int kp, F tol, float* s_max) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    if (tid == 0) *s_max = 0.0f;
+    __syncthreads();
+    float wmax = 0.0f;
+    for (int round = 0; round < kp - 1; ++round) {
+        for (int q = warp; q < kp / 2; q += nw) {
+            const int p0 = q, p1 = kp - 1 - q;
+            const int i = p0 == 0 ? 0 : 1 + (p0 - 1 + round) % (kp - 1);
+            const int j = 1 + (p1 - 1 + round) % (kp - 1);
+            F* ai = A + (long long)i * kp;
+            F* aj = A + (long long)j * kp;
+            F al = 0, be = 0, ga = 0;
+            for (int r = lane; r < kp; r += 32) {
+                const F x = ai[r], y = aj[r];
+                al = fma(x, x, al);
+                be = fma(y, y, be);
+                ga = fma(x, y, ga);
+            }
+            al = warp_allsum(al);
+            be = warp_allsum(be);
+            ga = warp_allsum(ga);
+            if (al > F(0) && be > F(0)) {
+                const F nrm = sqrt(al) * sqrt(be);
+                const F rel = fabs(ga) / nrm;
+                wmax = fmaxf(wmax, (float)rel);
+                if (rel > tol) {
+                    const F zeta = (be - al) / (F(2) * ga);
+                    const F t = (zeta >= F(0) ? F(1) : F(-1)) / (fabs(zeta) + sqrt(F(1) + zeta * zeta));
+                    const F c = F(1) / sqrt(F(1) + t * t), s = c * t;
+                    F* vi = V + (long long)i * kp;
+                    F* vj = V + (long long)j * kp;
+                    for (int r = lane; r < kp; r += 32) {
+                        const F x = ai[r], y = aj[r];
+                        ai[r] = c * x - s * y;
+                        aj[r] = s * x + c * y;
+                        const F u = vi[r], w = vj[r];
+                        vi[r] = c * u - s * w;
+                        vj[r] = s * u + c * w;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // relative values are non-negative, so their float bits order as integers
+    if (lane == 0) atomicMax((int*)s_max, __float_as_int(wmax));
+    __syncthreads();
+    const float r = *s_max;
+    __syncthreads();
+    return r;
+}
 
 }  // namespace
 
 // G (k x k, column-major G[i + j k]) -> T (k x k, column-major, upper triangular) with Y T
-// orthonormal for the Y that gave G = Y^T Y, and Rout = R D Rprev (Rprev == nullptr: R D).
-// Shared memory: 2 k^2 + k doubles.
+// orthonormal (up to the shift) for the Y that gave G = Y^T Y.  Shared memory: 2 k^2 + 2 k
+// doubles.
 __global__ void __launch_bounds__(kPsvdThreads)
-    chol_orth_kernel(const double* __restrict__ G, int k, const double* __restrict__ Rprev,
-                     double* __restrict__ T, double* __restrict__ Rout) {
+    chol_orth_kernel(const double* __restrict__ G, int k, double shift, double* __restrict__ T) {
     extern __shared__ double sm[];
-    double* R = sm;              // row-major k x k: scaled Gram, then the Cholesky factor (upper)
-    double* X = sm + k * k;      // row-major k x k: R^-1
+    double* R = sm;              // row-major k x k: scaled Gram, then the unscaled factor rows
+    double* X = sm + k * k;      // row-major k x k: F^-1
     double* d = sm + 2 * k * k;  // column norms
+    double* rinv = d + k;        // reciprocal pivots
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int i = tid; i < k; i += nt) {
         const double g = G[i + (long long)i * k];
@@ -61,125 +152,134 @@ __global__ void __launch_bounds__(kPsvdThreads)
     for (int e = tid; e < k * k; e += nt) {
         const int i = e / k, j = e % k;
         const double di = d[i], dj = d[j];
-        R[e] = (di > 0.0 && dj > 0.0) ? G[i + (long long)j * k] / (di * dj) : 0.0;
+        R[e] = (di > 0.0 && dj > 0.0) ? G[i + (long long)j * k] / (di * dj) + (i == j ? shift : 0.0)
+                                       : 0.0;
     }
     __syncthreads();
-    // right-looking Cholesky, upper factor in the upper triangle of R (row j = R_j,:)
-    for (int j = 0; j < k; ++j) {
-        const double piv = R[j * k + j];
-        const double rjj = piv > kPivotFloor ? sqrt(piv) : 0.0;
-        __syncthreads();
-        for (int c = j + tid; c < k; c += nt) R[j * k + c] = rjj > 0.0 ? R[j * k + c] / rjj : 0.0;
-        __syncthreads();
-        const int m = k - j - 1;  // trailing (j+1..k-1)^2 block, upper part
-        for (int e = tid; e < m * m; e += nt) {
-            const int a = j + 1 + e / m, b = j + 1 + e % m;
-            if (b >= a) R[a * k + b] -= R[j * k + a] * R[j * k + b];
-        }
-        __syncthreads();
-    }
-    // X = R^-1 by back substitution, one column per thread; rows of dependent columns are zero
+    block_cholesky(R, rinv, k);
+    // X = F^-1 by back substitution, one column per thread (F[r][l] = R[r][l] rinv[r]):
+    // x_r = (delta_rc - sum_l F[r][l] x_l) / F[r][r] = rinv[r] (delta_rc - rinv[r] sum_l R[r][l] x_l) / (R[r][r] rinv[r]^2)
+    // simplified with F[r][r] = 1 / rinv[r]:  x_r = rinv[r] * (delta_rc - rinv[r] * sum_l R[r][l] x_l)
     for (int c = tid; c < k; c += nt) {
         for (int r = k - 1; r >= 0; --r) {
             double x = 0.0;
-            if (r <= c && R[r * k + r] > 0.0) {
-                double acc = (r == c) ? 1.0 : 0.0;
-                for (int l = r + 1; l <= c; ++l) acc -= R[r * k + l] * X[l * k + c];
-                x = acc / R[r * k + r];
+            const double ri = rinv[r];
+            if (r <= c && ri > 0.0) {
+                double acc = 0.0;
+                for (int l = r + 1; l <= c; ++l) acc = fma(R[r * k + l], X[l * k + c], acc);
+                x = ri * ((r == c ? 1.0 : 0.0) - ri * acc);
             }
             X[r * k + c] = x;
         }
     }
     __syncthreads();
-    // T = D^-1 R^-1 ; Rout = R D Rprev
-    for (int e = tid; e < k * k; e += nt) {
-        const int i = e % k, j = e / k;  // column-major output index
+    for (int e = tid; e < k * k; e += nt) {  // T = D^-1 F^-1, column-major
+        const int i = e % k, j = e / k;
         T[e] = (d[i] > 0.0 && j >= i) ? X[i * k + j] / d[i] : 0.0;
-        double v = 0.0;
-        if (Rprev) {
-            for (int l = i; l < k; ++l) v += R[i * k + l] * d[l] * Rprev[l + (long long)j * k];
-        } else if (j >= i) {
-            v = R[i * k + j] * d[j];
-        }
-        Rout[e] = v;
     }
 }
 
-// One-sided Jacobi SVD of B (k x k, column-major): B W = A with orthogonal columns, B = U S W^T,
-// U = A S^-1.  Writes S (k, decreasing), U and W (k x k, column-major, columns in the order of
-// S).  info: 0, or 1 if the sweep limit was reached.  Shared memory: 2 kp^2 + 2 kp doubles,
+// SVD of B (k x k, column-major): B W = A with orthogonal columns, B = U S W^T, U = A S^-1.
+// Writes S (k, decreasing), U and W (k x k, column-major, columns in the order of S).
+// info: 0, or 1 if a sweep limit was reached.  Shared memory: 2 kp^2 + kp doubles + kp ints,
 // kp = k rounded up to even (an odd k gets a zero column that is never rotated).
 __global__ void __launch_bounds__(kPsvdThreads)
     jacobi_svd_kernel(const double* __restrict__ B, int k, double* __restrict__ S,
                       double* __restrict__ U, double* __restrict__ W, int* info) {
     extern __shared__ double sm[];
     const int kp = k + (k & 1);
-    double* A = sm;                // column j at A + j kp
-    double* V = sm + kp * kp;      // column j at V + j kp
+    double* A = sm;                // FP64 phase: column j at A + j kp
+    double* V = sm + kp * kp;      // W, column j at V + j kp
+    float* A32 = (float*)A;        // FP32 phase: both FP32 matrices inside A's space
+    float* V32 = A32 + kp * kp;
     double* sig = sm + 2 * kp * kp;
     int* rank = (int*)(sig + kp);
-    __shared__ int s_rot;
+    __shared__ float s_max;
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5,
               nw = nt >> 5;
+    __shared__ int s_exp;
+    int bad = 0;
+
+    // 0. scale: B 2^-ex has entries below 1 in magnitude (exact; FP32 squares stay in range)
+    {
+        __shared__ double s_wmax[kPsvdThreads / 32];
+        double m = 0.0;
+        for (int e = tid; e < k * k; e += nt) m = fmax(m, fabs(B[e]));
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) s_wmax[warp] = m;
+        __syncthreads();
+        if (tid == 0) {
+            double mm = 0.0;
+            for (int w = 0; w < nw; ++w) mm = fmax(mm, s_wmax[w]);
+            int e2 = 0;
+            if (mm > 0.0 && isfinite(mm)) frexp(mm, &e2);  // mm < 2^e2
+            s_exp = e2;
+        }
+        __syncthreads();
+    }
+    const int ex = s_exp;
+    // 1. FP32 sweeps on B 2^-ex
     for (int e = tid; e < kp * kp; e += nt) {
         const int r = e % kp, c = e / kp;
-        A[e] = (r < k && c < k) ? B[r + (long long)c * k] : 0.0;
-        V[e] = (r == c) ? 1.0 : 0.0;
+        A32[e] = (r < k && c < k) ? (float)ldexp(B[r + (long long)c * k], -ex) : 0.0f;
+        V32[e] = (r == c) ? 1.0f : 0.0f;
     }
     __syncthreads();
-    // a pair is rotated while |a_i . a_j| > tol |a_i| |a_j|; tol = 4 sqrt(kp) eps sits above the
-    // rounding level of the dot products of orthogonal columns, so the sweeps terminate
-    const double tol = 4.0 * sqrt((double)kp) * 2.220446049250313e-16;
-    int sweep = 0;
-    for (; sweep < kJacobiMaxSweeps; ++sweep) {
-        if (tid == 0) s_rot = 0;
-        __syncthreads();
-        for (int round = 0; round < kp - 1; ++round) {
-            // circle method: position 0 fixed, positions 1..kp-1 rotate by `round`
-            for (int q = warp; q < kp / 2; q += nw) {
-                const int p0 = q, p1 = kp - 1 - q;
-                const int i = p0 == 0 ? 0 : 1 + (p0 - 1 + round) % (kp - 1);
-                const int j = 1 + (p1 - 1 + round) % (kp - 1);
-                double* ai = A + (long long)i * kp;
-                double* aj = A + (long long)j * kp;
-                double al = 0.0, be = 0.0, ga = 0.0;
-                for (int r = lane; r < kp; r += 32) {
-                    const double x = ai[r], y = aj[r];
-                    al = fma(x, x, al);
-                    be = fma(y, y, be);
-                    ga = fma(x, y, ga);
-                }
-                al = warp_allsum(al);
-                be = warp_allsum(be);
-                ga = warp_allsum(ga);
-                if (ga != 0.0 && al > 0.0 && be > 0.0 && fabs(ga) > tol * sqrt(al * be)) {
-                    const double zeta = (be - al) / (2.0 * ga);
-                    const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                    const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
-                    double* vi = V + (long long)i * kp;
-                    double* vj = V + (long long)j * kp;
-                    for (int r = lane; r < kp; r += 32) {
-                        const double x = ai[r], y = aj[r];
-                        ai[r] = c * x - s * y;
-                        aj[r] = s * x + c * y;
-                        const double u = vi[r], w = vj[r];
-                        vi[r] = c * u - s * w;
-                        vj[r] = s * u + c * w;
-                    }
-                    if (lane == 0) s_rot = 1;
-                }
-            }
-            __syncthreads();
-        }
-        if (s_rot == 0) break;
-        __syncthreads();
+    // stop once no pair is above the FP32 rounding level of a kp-term dot product
+    const float tol32 = 4.0f * (float)kp * 5.9604645e-8f;
+    {
+        int sw = 0;
+        for (; sw < kJacobiMaxSweeps32; ++sw)
+            if (jacobi_sweep<float>(A32, V32, kp, tol32, &s_max) <= tol32) break;
     }
-    // singular values = column norms, ranks by decreasing value (ties: lower index first)
+    // 2. W = V32 in FP64, re-orthonormalised: W <- W R^-1 with R^T R = W^T W
+    for (int e = tid; e < kp * kp; e += nt) V[e] = (double)V32[e];
+    __syncthreads();
+    for (int e = tid; e < kp * kp; e += nt) {  // A (row-major) = W^T W; A32/V32 are dead now
+        const int i = e / kp, j = e % kp;
+        double v = 0.0;
+        for (int l = 0; l < kp; ++l) v = fma(V[i * kp + l], V[j * kp + l], v);
+        A[e] = v;
+    }
+    __syncthreads();
+    double* rinv = sig;  // reciprocal pivots, until the singular values are written
+    block_cholesky(A, rinv, kp);
+    // row r of W: x F = w_r in place (forward substitution), F[i][j] = A[i][j] rinv[i]
+    for (int r = tid; r < kp; r += nt) {
+        for (int j = 0; j < kp; ++j) {
+            double acc = V[j * kp + r];
+            for (int i = 0; i < j; ++i) acc -= V[i * kp + r] * (A[i * kp + j] * rinv[i]);
+            V[j * kp + r] = acc * rinv[j];
+        }
+    }
+    __syncthreads();
+    // 3. A = B W in FP64
+    for (int e = tid; e < kp * kp; e += nt) {
+        const int r = e % kp, c = e / kp;
+        double v = 0.0;
+        if (r < k)
+            for (int l = 0; l < k; ++l) v = fma(B[r + (long long)l * k], V[c * kp + l], v);
+        A[e] = ldexp(v, -ex);
+    }
+    __syncthreads();
+    // 4. FP64 sweeps; tol64 = kp eps is the rounding level of a kp-term dot product.  Jacobi
+    //    converges quadratically, so a sweep whose largest relative off-diagonal value was below
+    //    1e-7 leaves them near 1e-14: it is the last
+    const double tol64 = (double)kp * 2.220446049250313e-16;
+    {
+        int sw = 0;
+        for (; sw < kJacobiMaxSweeps64; ++sw) {
+            const float mx = jacobi_sweep<double>(A, V, kp, tol64, &s_max);
+            if (mx <= tol64 || mx < 1e-7f) break;
+        }
+        if (sw >= kJacobiMaxSweeps64) bad = 1;
+    }
+    // 5. singular values = column norms, ranks by decreasing value (ties: lower index first)
     for (int c = warp; c < k; c += nw) {
         double v = 0.0;
         for (int r = lane; r < kp; r += 32) v = fma(A[c * kp + r], A[c * kp + r], v);
         v = warp_allsum(v);
-        if (lane == 0) sig[c] = sqrt(v);
+        if (lane == 0) sig[c] = sqrt(v);  // of B 2^-ex
     }
     __syncthreads();
     for (int c = tid; c < k; c += nt) {
@@ -196,8 +296,8 @@ __global__ void __launch_bounds__(kPsvdThreads)
         U[dst] = sc > 0.0 ? A[c * kp + r] / sc : 0.0;
         W[dst] = V[c * kp + r];
     }
-    for (int c = tid; c < k; c += nt) S[rank[c]] = sig[c];
-    if (tid == 0 && info) *info = sweep >= kJacobiMaxSweeps ? 1 : 0;
+    for (int c = tid; c < k; c += nt) S[rank[c]] = ldexp(sig[c], ex);
+    if (tid == 0 && info) *info = bad;
 }
 
 // Vout[r + c n] = VT[c + r n] for c < k: the first k right singular vectors of gesvd's V^T as
@@ -212,21 +312,40 @@ __global__ void vt_columns_kernel(const double* __restrict__ VT, double* __restr
     }
 }
 
-size_t chol_orth_smem(int k) { return (size_t)(2 * k * k + k) * sizeof(double); }
+// Columns c with S[c] == 0 (a zero column of the subspace basis) get uniform [-1, 1) entries
+// from SplitMix64 (Steele, Lea, Flood 2014) at counter seed + c n + r.
+__global__ void refill_kernel(double* __restrict__ V, int n, int k, const double* __restrict__ S,
+                              unsigned long long seed) {
+    const int c = blockIdx.x;
+    if (c >= k || S[c] != 0.0) return;
+    for (int r = threadIdx.x; r < n; r += blockDim.x) {
+        unsigned long long z = seed + ((unsigned long long)c * n + r + 1ULL) * 0x9E3779B97F4A7C15ULL;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+        z ^= z >> 31;
+        V[r + (long long)c * n] = 2.0 * ((double)(z >> 11) * 0x1.0p-53) - 1.0;
+    }
+}
+
+void launch_refill(double* V, int n, int k, const double* S, unsigned long long seed,
+                   cudaStream_t s) {
+    refill_kernel<<<k, 256, 0, s>>>(V, n, k, S, seed);
+}
+
+size_t chol_orth_smem(int k) { return (size_t)(2 * k * k + 2 * k) * sizeof(double); }
 size_t jacobi_svd_smem(int k) {
     const int kp = k + (k & 1);
     return (size_t)(2 * kp * kp + kp) * sizeof(double) + (size_t)kp * sizeof(int);
 }
 
-void launch_chol_orth(const double* G, int k, const double* Rprev, double* T, double* Rout,
-                      cudaStream_t s) {
+void launch_chol_orth(const double* G, int k, double shift, double* T, cudaStream_t s) {
     const size_t smem = chol_orth_smem(k);
     static std::once_flag once;
     std::call_once(once, [] {
         cudaFuncSetAttribute(chol_orth_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)chol_orth_smem(kPsvdMaxK));
     });
-    chol_orth_kernel<<<1, kPsvdThreads, smem, s>>>(G, k, Rprev, T, Rout);
+    chol_orth_kernel<<<1, kPsvdThreads, smem, s>>>(G, k, shift, T);
 }
 
 void launch_jacobi_svd(const double* B, int k, double* S, double* U, double* W, int* info,

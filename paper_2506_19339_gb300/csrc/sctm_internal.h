@@ -66,8 +66,9 @@ void launch_signfix(double* U, double* V, int n, int k, int vt, cudaStream_t s);
 void launch_copy(const double* src, double* dst, long long n, cudaStream_t s);
 // partial SVD (psvd.cu): column-scaled Cholesky QR pass, one-CTA Jacobi SVD, V^T -> columns
 constexpr int kPsvdMaxK = 112;  // largest subspace (chi + oversampling) the one-CTA kernels take
-void launch_chol_orth(const double* G, int k, const double* Rprev, double* T, double* Rout,
-                      cudaStream_t s);
+void launch_chol_orth(const double* G, int k, double shift, double* T, cudaStream_t s);
+void launch_refill(double* V, int n, int k, const double* S, unsigned long long seed,
+                   cudaStream_t s);
 void launch_jacobi_svd(const double* B, int k, double* S, double* U, double* W, int* info,
                        cudaStream_t s);
 void launch_vt_columns(const double* VT, double* Vout, int n, int k, cudaStream_t s);
