@@ -56,13 +56,17 @@ __device__ __forceinline__ float warp_allsum(float v) {
 // In-place right-looking Cholesky of the symmetric k x k matrix in R (row-major, upper triangle
 // used).  Rows are left unscaled: on return the upper factor is F[j][c] = R[j][c] * rinv[j]
 // (c >= j), F[j][j] = R[j][j] * rinv[j] = sqrt(pivot j).  Pivots at or below kPivotFloor give
-// rinv = 0 (a zero row).  One barrier per column.  All threads call.
+// rinv = 0 (a zero row).  The reciprocal square root is taken by one thread: FP64 is scarce on
+// this GPU and a redundant evaluation by every thread costs as much as the update.
 __device__ void block_cholesky(double* R, double* rinv, int k) {
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int j = 0; j < k; ++j) {
-        const double piv = R[j * k + j];
-        const double ri = piv > kPivotFloor ? 1.0 / sqrt(piv) : 0.0;
-        if (tid == 0) rinv[j] = ri;
+        if (tid == 0) {
+            const double piv = R[j * k + j];
+            rinv[j] = piv > kPivotFloor ? 1.0 / sqrt(piv) : 0.0;
+        }
+        __syncthreads();
+        const double ri = rinv[j];
         const double r2 = ri * ri;
         const int m = k - j - 1;
         for (int e = tid; e < m * m; e += nt) {
@@ -73,57 +77,80 @@ __device__ void block_cholesky(double* R, double* rinv, int k) {
     }
 }
 
+// Scratch of one Jacobi round, one entry per column pair.
+struct RoundScratch {
+    double* c;   // cosine (FP64 phase) / unused
+    double* s;   // sine
+    int* act;    // 1 if the pair rotates
+};
+
 // One sweep of one-sided Jacobi rotations over all column pairs (circle-method rounds) of the
-// kp x kp column-major A, accumulating into the columns of V.  Pairs with
+// kp x kp column-major matrix A (leading dimension ld), accumulating into V (same layout).  Per
+// round: thread q < kp/2 forms pair q's three dot products and its rotation (one pair per
+// thread, so the FP64 square roots and divisions are not repeated across a warp), then every
+// thread applies the rotations, one (pair, row) element at a time.  Pairs with
 // |a_i . a_j| <= tol |a_i| |a_j| are left alone.  Returns (to every thread) the largest
 // |a_i . a_j| / (|a_i| |a_j|) seen.
 template <typename F>
-__device__ float jacobi_sweep(F* A, F* V, int kp, F tol, float* s_max) {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+__device__ float jacobi_sweep(F* A, F* V, int kp, int ld, F tol, RoundScratch rs, float* s_max) {
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
+    const int np = kp / 2;
     if (tid == 0) *s_max = 0.0f;
-    __syncthreads();
     float wmax = 0.0f;
     for (int round = 0; round < kp - 1; ++round) {
-        for (int q = warp; q < kp / 2; q += nw) {
+        for (int q = tid; q < np; q += nt) {
             const int p0 = q, p1 = kp - 1 - q;
             const int i = p0 == 0 ? 0 : 1 + (p0 - 1 + round) % (kp - 1);
             const int j = 1 + (p1 - 1 + round) % (kp - 1);
-            F* ai = A + (long long)i * kp;
-            F* aj = A + (long long)j * kp;
+            const F* ai = A + (long long)i * ld;
+            const F* aj = A + (long long)j * ld;
             F al = 0, be = 0, ga = 0;
-            for (int r = lane; r < kp; r += 32) {
+            for (int r = 0; r < kp; ++r) {
                 const F x = ai[r], y = aj[r];
                 al = fma(x, x, al);
                 be = fma(y, y, be);
                 ga = fma(x, y, ga);
             }
-            al = warp_allsum(al);
-            be = warp_allsum(be);
-            ga = warp_allsum(ga);
+            int act = 0;
+            F c = 1, sn = 0;
             if (al > F(0) && be > F(0)) {
-                const F nrm = sqrt(al) * sqrt(be);
-                const F rel = fabs(ga) / nrm;
+                const F rel = fabs(ga) / (sqrt(al) * sqrt(be));
                 wmax = fmaxf(wmax, (float)rel);
                 if (rel > tol) {
                     const F zeta = (be - al) / (F(2) * ga);
                     const F t = (zeta >= F(0) ? F(1) : F(-1)) / (fabs(zeta) + sqrt(F(1) + zeta * zeta));
-                    const F c = F(1) / sqrt(F(1) + t * t), s = c * t;
-                    F* vi = V + (long long)i * kp;
-                    F* vj = V + (long long)j * kp;
-                    for (int r = lane; r < kp; r += 32) {
-                        const F x = ai[r], y = aj[r];
-                        ai[r] = c * x - s * y;
-                        aj[r] = s * x + c * y;
-                        const F u = vi[r], w = vj[r];
-                        vi[r] = c * u - s * w;
-                        vj[r] = s * u + c * w;
-                    }
+                    c = F(1) / sqrt(F(1) + t * t);
+                    sn = c * t;
+                    act = 1;
                 }
             }
+            rs.c[q] = (double)c;
+            rs.s[q] = (double)sn;
+            rs.act[q] = act;
+        }
+        __syncthreads();
+        for (int e = tid; e < np * kp; e += nt) {
+            const int q = e / kp, r = e % kp;
+            if (!rs.act[q]) continue;
+            const int p0 = q, p1 = kp - 1 - q;
+            const int i = p0 == 0 ? 0 : 1 + (p0 - 1 + round) % (kp - 1);
+            const int j = 1 + (p1 - 1 + round) % (kp - 1);
+            const F c = (F)rs.c[q], sn = (F)rs.s[q];
+            F* ai = A + (long long)i * ld;
+            F* aj = A + (long long)j * ld;
+            F* vi = V + (long long)i * ld;
+            F* vj = V + (long long)j * ld;
+            const F x = ai[r], y = aj[r];
+            ai[r] = c * x - sn * y;
+            aj[r] = sn * x + c * y;
+            const F u = vi[r], w = vj[r];
+            vi[r] = c * u - sn * w;
+            vj[r] = sn * u + c * w;
         }
         __syncthreads();
     }
     // relative values are non-negative, so their float bits order as integers
+    for (int o = 16; o > 0; o >>= 1) wmax = fmaxf(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
     if (lane == 0) atomicMax((int*)s_max, __float_as_int(wmax));
     __syncthreads();
     const float r = *s_max;
@@ -157,9 +184,9 @@ __global__ void __launch_bounds__(kPsvdThreads)
     }
     __syncthreads();
     block_cholesky(R, rinv, k);
-    // X = F^-1 by back substitution, one column per thread (F[r][l] = R[r][l] rinv[r]):
-    // x_r = (delta_rc - sum_l F[r][l] x_l) / F[r][r] = rinv[r] (delta_rc - rinv[r] sum_l R[r][l] x_l) / (R[r][r] rinv[r]^2)
-    // simplified with F[r][r] = 1 / rinv[r]:  x_r = rinv[r] * (delta_rc - rinv[r] * sum_l R[r][l] x_l)
+    for (int i = tid; i < k; i += nt) d[i] = d[i] > 0.0 ? 1.0 / d[i] : 0.0;  // now 1 / norm
+    // X = F^-1 by back substitution, one column per thread.  With F[r][l] = R[r][l] rinv[r] and
+    // F[r][r] = 1 / rinv[r]:  x_r = rinv[r] (delta_rc - rinv[r] sum_{l > r} R[r][l] x_l)
     for (int c = tid; c < k; c += nt) {
         for (int r = k - 1; r >= 0; --r) {
             double x = 0.0;
@@ -175,34 +202,40 @@ __global__ void __launch_bounds__(kPsvdThreads)
     __syncthreads();
     for (int e = tid; e < k * k; e += nt) {  // T = D^-1 F^-1, column-major
         const int i = e % k, j = e / k;
-        T[e] = (d[i] > 0.0 && j >= i) ? X[i * k + j] / d[i] : 0.0;
+        T[e] = j >= i ? X[i * k + j] * d[i] : 0.0;
     }
 }
 
 // SVD of B (k x k, column-major): B W = A with orthogonal columns, B = U S W^T, U = A S^-1.
 // Writes S (k, decreasing), U and W (k x k, column-major, columns in the order of S).
-// info: 0, or 1 if a sweep limit was reached.  Shared memory: 2 kp^2 + kp doubles + kp ints,
-// kp = k rounded up to even (an odd k gets a zero column that is never rotated).
+// info: 0, or 1 if the FP64 sweep limit was reached.  kp = k rounded up to even (an odd k gets a
+// zero column that is never rotated); columns are stored with the odd leading dimension
+// ld = kp + 1 so that the threads of the dot-product phase, which read different columns, hit
+// different shared-memory banks.  Shared memory: jacobi_svd_smem(k).
 __global__ void __launch_bounds__(kPsvdThreads)
     jacobi_svd_kernel(const double* __restrict__ B, int k, double* __restrict__ S,
                       double* __restrict__ U, double* __restrict__ W, int* info) {
     extern __shared__ double sm[];
-    const int kp = k + (k & 1);
-    double* A = sm;                // FP64 phase: column j at A + j kp
-    double* V = sm + kp * kp;      // W, column j at V + j kp
+    const int kp = k + (k & 1), ld = kp + 1, np = kp / 2;
+    double* A = sm;                // FP64 phase: column j at A + j ld
+    double* V = sm + kp * ld;      // W, column j at V + j ld
     float* A32 = (float*)A;        // FP32 phase: both FP32 matrices inside A's space
-    float* V32 = A32 + kp * kp;
-    double* sig = sm + 2 * kp * kp;
-    int* rank = (int*)(sig + kp);
+    float* V32 = A32 + kp * ld;
+    double* sig = sm + 2 * kp * ld;
+    RoundScratch rs;
+    rs.c = sig + kp;
+    rs.s = rs.c + np;
+    int* rank = (int*)(rs.s + np);
+    rs.act = rank + kp;
     __shared__ float s_max;
+    __shared__ int s_exp;
+    __shared__ double s_wmax[kPsvdThreads / 32];
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5,
               nw = nt >> 5;
-    __shared__ int s_exp;
     int bad = 0;
 
     // 0. scale: B 2^-ex has entries below 1 in magnitude (exact; FP32 squares stay in range)
     {
-        __shared__ double s_wmax[kPsvdThreads / 32];
         double m = 0.0;
         for (int e = tid; e < k * k; e += nt) m = fmax(m, fabs(B[e]));
         for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -218,27 +251,27 @@ __global__ void __launch_bounds__(kPsvdThreads)
         __syncthreads();
     }
     const int ex = s_exp;
-    // 1. FP32 sweeps on B 2^-ex
+    // 1. FP32 sweeps on B 2^-ex, until no pair is above the FP32 rounding level of a kp-term dot
+    //    product
     for (int e = tid; e < kp * kp; e += nt) {
         const int r = e % kp, c = e / kp;
-        A32[e] = (r < k && c < k) ? (float)ldexp(B[r + (long long)c * k], -ex) : 0.0f;
-        V32[e] = (r == c) ? 1.0f : 0.0f;
+        A32[c * ld + r] = (r < k && c < k) ? (float)ldexp(B[r + (long long)c * k], -ex) : 0.0f;
+        V32[c * ld + r] = (r == c) ? 1.0f : 0.0f;
     }
     __syncthreads();
-    // stop once no pair is above the FP32 rounding level of a kp-term dot product
     const float tol32 = 4.0f * (float)kp * 5.9604645e-8f;
-    {
-        int sw = 0;
-        for (; sw < kJacobiMaxSweeps32; ++sw)
-            if (jacobi_sweep<float>(A32, V32, kp, tol32, &s_max) <= tol32) break;
+    for (int sw = 0; sw < kJacobiMaxSweeps32; ++sw)
+        if (jacobi_sweep<float>(A32, V32, kp, ld, tol32, rs, &s_max) <= tol32) break;
+    // 2. W = V32 in FP64, re-orthonormalised: W <- W F^-1 with F^T F = W^T W
+    for (int e = tid; e < kp * kp; e += nt) {
+        const int r = e % kp, c = e / kp;
+        V[c * ld + r] = (double)V32[c * ld + r];
     }
-    // 2. W = V32 in FP64, re-orthonormalised: W <- W R^-1 with R^T R = W^T W
-    for (int e = tid; e < kp * kp; e += nt) V[e] = (double)V32[e];
     __syncthreads();
-    for (int e = tid; e < kp * kp; e += nt) {  // A (row-major) = W^T W; A32/V32 are dead now
+    for (int e = tid; e < kp * kp; e += nt) {  // A (row-major, stride kp) = W^T W
         const int i = e / kp, j = e % kp;
         double v = 0.0;
-        for (int l = 0; l < kp; ++l) v = fma(V[i * kp + l], V[j * kp + l], v);
+        for (int l = 0; l < kp; ++l) v = fma(V[i * ld + l], V[j * ld + l], v);
         A[e] = v;
     }
     __syncthreads();
@@ -247,19 +280,19 @@ __global__ void __launch_bounds__(kPsvdThreads)
     // row r of W: x F = w_r in place (forward substitution), F[i][j] = A[i][j] rinv[i]
     for (int r = tid; r < kp; r += nt) {
         for (int j = 0; j < kp; ++j) {
-            double acc = V[j * kp + r];
-            for (int i = 0; i < j; ++i) acc -= V[i * kp + r] * (A[i * kp + j] * rinv[i]);
-            V[j * kp + r] = acc * rinv[j];
+            double acc = V[j * ld + r];
+            for (int i = 0; i < j; ++i) acc -= V[i * ld + r] * (A[i * kp + j] * rinv[i]);
+            V[j * ld + r] = acc * rinv[j];
         }
     }
     __syncthreads();
-    // 3. A = B W in FP64
+    // 3. A = B W 2^-ex in FP64
     for (int e = tid; e < kp * kp; e += nt) {
         const int r = e % kp, c = e / kp;
         double v = 0.0;
         if (r < k)
-            for (int l = 0; l < k; ++l) v = fma(B[r + (long long)l * k], V[c * kp + l], v);
-        A[e] = ldexp(v, -ex);
+            for (int l = 0; l < k; ++l) v = fma(B[r + (long long)l * k], V[c * ld + l], v);
+        A[c * ld + r] = ldexp(v, -ex);
     }
     __syncthreads();
     // 4. FP64 sweeps; tol64 = kp eps is the rounding level of a kp-term dot product.  Jacobi
@@ -269,7 +302,7 @@ __global__ void __launch_bounds__(kPsvdThreads)
     {
         int sw = 0;
         for (; sw < kJacobiMaxSweeps64; ++sw) {
-            const float mx = jacobi_sweep<double>(A, V, kp, tol64, &s_max);
+            const float mx = jacobi_sweep<double>(A, V, kp, ld, tol64, rs, &s_max);
             if (mx <= tol64 || mx < 1e-7f) break;
         }
         if (sw >= kJacobiMaxSweeps64) bad = 1;
@@ -277,7 +310,7 @@ __global__ void __launch_bounds__(kPsvdThreads)
     // 5. singular values = column norms, ranks by decreasing value (ties: lower index first)
     for (int c = warp; c < k; c += nw) {
         double v = 0.0;
-        for (int r = lane; r < kp; r += 32) v = fma(A[c * kp + r], A[c * kp + r], v);
+        for (int r = lane; r < kp; r += 32) v = fma(A[c * ld + r], A[c * ld + r], v);
         v = warp_allsum(v);
         if (lane == 0) sig[c] = sqrt(v);  // of B 2^-ex
     }
@@ -293,8 +326,8 @@ __global__ void __launch_bounds__(kPsvdThreads)
         const int r = e % k, c = e / k;
         const int dst = r + rank[c] * k;
         const double sc = sig[c];
-        U[dst] = sc > 0.0 ? A[c * kp + r] / sc : 0.0;
-        W[dst] = V[c * kp + r];
+        U[dst] = sc > 0.0 ? A[c * ld + r] / sc : 0.0;
+        W[dst] = V[c * ld + r];
     }
     for (int c = tid; c < k; c += nt) S[rank[c]] = ldexp(sig[c], ex);
     if (tid == 0 && info) *info = bad;
@@ -334,8 +367,8 @@ void launch_refill(double* V, int n, int k, const double* S, unsigned long long 
 
 size_t chol_orth_smem(int k) { return (size_t)(2 * k * k + 2 * k) * sizeof(double); }
 size_t jacobi_svd_smem(int k) {
-    const int kp = k + (k & 1);
-    return (size_t)(2 * kp * kp + kp) * sizeof(double) + (size_t)kp * sizeof(int);
+    const int kp = k + (k & 1), ld = kp + 1, np = kp / 2;
+    return (size_t)(2 * kp * ld + kp + 2 * np) * sizeof(double) + (size_t)(kp + np) * sizeof(int);
 }
 
 void launch_chol_orth(const double* G, int k, double shift, double* T, cudaStream_t s) {
