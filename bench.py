@@ -27,6 +27,11 @@ METRIC = "split-CTMRG f+∇f evals/s at D=4 χ=64, mixed vs FP64 at |Δf|≤1e-8
 WORKLOAD = dict(D=4, chi=64, T=4.5, seed=2)   # the configuration the metric is quoted on
 NOMINAL_FP64_TFLOPS = 1.25                     # GB300 FP64 (vector and tensor), nominal
 NOMINAL_BF16_TFLOPS = 2250.0
+PRECISIONS = {'fp64': 0, 'tf32': 1, 'tf32x3': 2, 'bf16': 3, 'bf16x3': 4}
+SVD_MODES = {'qr': 0, 'polar': 1, 'partial': 2}
+SVD_NAMES = {'qr': 'cuSOLVER gesvd', 'polar': 'cuSOLVER gesvdp',
+             'partial': 'partial SVD: gesvd cold solve, then warm-started subspace iteration + '
+                        'one-CTA Jacobi'}
 
 
 def parse():
@@ -41,8 +46,12 @@ def parse():
     ap.add_argument('--batch', type=int, default=0,
                     help='batched sweep: B contexts (T uniform in [4.40, 4.62], seeds 100..) '
                          'iterated concurrently; 0 = the single-instance workload')
-    ap.add_argument('--svd', default='qr', choices=['qr', 'polar'],
-                    help='FP64 SVD of the projectors: cuSOLVER gesvd (qr) or gesvdp (polar)')
+    ap.add_argument('--svd', default='partial', choices=['partial', 'qr', 'polar'],
+                    help='FP64 SVD of the projectors: the partial SVD (warm-started subspace '
+                         'iteration after a cuSOLVER gesvd cold solve), cuSOLVER gesvd (qr) or '
+                         'gesvdp (polar)')
+    ap.add_argument('--precision', default='fp64', choices=list(PRECISIONS),
+                    help='arithmetic of the move contractions (mixed forms polish in FP64)')
     return ap.parse_args()
 
 
@@ -207,7 +216,8 @@ def run_ours(args):
     st, o = sctm.sctm_default_opts()
     o.T, o.D, o.p, o.d = w['T'], w['D'], 2, 2
     o.cuda_stream = stream.cuda_stream
-    o.svd_mode = sctm.SCTM_SVD_POLAR if args.svd == 'polar' else sctm.SCTM_SVD_QR
+    o.svd_mode = SVD_MODES[args.svd]
+    o.precision = PRECISIONS[args.precision]
     A_dev = torch.from_numpy(A_host).to(dev)
     st, ctx = sctm.sctm_create(A_dev, np.ascontiguousarray(O), w['chi'], o)
     if st != sctm.SCTM_OK:
@@ -321,11 +331,13 @@ def run_ours(args):
     line = {
         'metric': METRIC, 'value': value, 'unit': 'evals/s', 'n_gpus': world,
         'steps': args.steps, 'warmup': args.warmup, 'ms_per_step': ms / args.steps,
-        'higher_is_better': True, 'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f64',
+        'higher_is_better': True, 'scaling': 'weak', 'vs_baseline': None,
+        'dtype': 'f64' if args.precision == 'fp64' else args.precision + '+f64',
         'data': 'synthetic',
         'config': {'workload': workload_name(args.iters), 'D': w['D'], 'chi': w['chi'],
                    'T': w['T'], 'seed': w['seed'], 'iterations_per_eval': args.iters,
-                   'precision': 'FP64 contractions, FP64 SVD (%s)' % ('cuSOLVER gesvdp' if args.svd == 'polar' else 'cuSOLVER gesvd'),
+                   'precision': '%s move contractions, FP64 SVD (%s)' % (
+                       args.precision.upper(), SVD_NAMES[args.svd]),
                    'parallelism': 'replicas',
                    'l2': 'flushed before every step (256 MiB write, outside the step events)'},
         'iterations_per_s': total_its * world / (ms * 1e-3),
@@ -368,7 +380,8 @@ def run_batch(args):
         st, o = sctm.sctm_default_opts()
         o.T, o.D, o.p, o.d = float(T), w['D'], 2, 2
         o.cuda_stream = streams[i].cuda_stream
-        o.svd_mode = sctm.SCTM_SVD_POLAR if args.svd == 'polar' else sctm.SCTM_SVD_QR
+        o.svd_mode = SVD_MODES[args.svd]
+        o.precision = PRECISIONS[args.precision]
         st, ctx = sctm.sctm_create(A, np.ascontiguousarray(O), w['chi'], o)
         if st != sctm.SCTM_OK:
             raise RuntimeError('sctm_create failed for batch member %d: %s' % (i, sctm.STATUS_NAMES[st]))
@@ -409,8 +422,9 @@ def run_batch(args):
         'data': 'synthetic',
         'config': {'workload': 'batched sweep: %d contexts, T uniform in [4.40, 4.62], PEPS D=%d '
                                'N(0,1) seeds 100..%d, chi=%d, %d iterations per evaluation, '
-                               'FP64, iterated concurrently (one host thread and stream set '
-                               'per context)' % (B, w['D'], 99 + B, w['chi'], args.iters),
+                               '%s, SVD %s, iterated concurrently (one host thread and stream '
+                               'set per context)' % (B, w['D'], 99 + B, w['chi'], args.iters,
+                                                     args.precision.upper(), args.svd),
                    'batch': B, 'iterations_per_eval': args.iters, 'device_bytes': mem,
                    'timing': 'host wall clock around each step with device synchronisation'},
         'clocks': clk,
