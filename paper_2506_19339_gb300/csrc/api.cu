@@ -249,13 +249,14 @@ sctm_status sctm_iterate(sctm_ctx* ctx, int max_it, double tol, int* it_done, do
                 for (int m = 0; m < 4; ++m) e.run(net.move[m]);
                 e.run(net.spectrum);
                 check_cuda("iteration");
-                int err = 0;
+                int err[2] = {0, 0};
                 cuda_ok(cudaMemcpyAsync(&dS, net.dS, sizeof(double), cudaMemcpyDeviceToHost, s0),
                         "dS copy");
-                cuda_ok(cudaMemcpyAsync(&err, e.dev_err, sizeof(int), cudaMemcpyDeviceToHost, s0),
+                cuda_ok(cudaMemcpyAsync(err, e.dev_err, 2 * sizeof(int), cudaMemcpyDeviceToHost, s0),
                         "error flag copy");
                 cuda_ok(cudaStreamSynchronize(s0), "iteration sync");
-                if (err) throw Error(SCTM_ETIMEOUT, "tensor-core contraction wait timed out");
+                if (err[0]) throw Error(SCTM_ETIMEOUT, "tensor-core contraction wait timed out");
+                if (err[1]) throw Error(SCTM_ENUMERIC, "non-finite projector matrix");
                 if (!std::isfinite(dS)) throw Error(SCTM_ENUMERIC, "non-finite spectrum change");
                 if (net.precision != SCTM_PREC_FP64) {
                     if (dS < 0.5 * best) {
@@ -587,6 +588,13 @@ sctm_status sctm_gemm(const double* X, const double* Y, double* O, int M, int N,
     a.on = dev_copy(on);
     a.err = dev_copy({0});
     if (!a.xm || !a.xk || !a.yk || !a.yn || !a.om || !a.on || !a.err) st = SCTM_ENOMEM;
+    if (st == SCTM_OK && precision != SCTM_PREC_FP64) {
+        void* p = nullptr;
+        if (cudaMalloc(&p, 2 * kScaleBlocks * sizeof(double)) != cudaSuccess)
+            st = SCTM_ENOMEM;
+        else
+            bufs.push_back(p), a.scale_ws = (double*)p;
+    }
     if (st == SCTM_OK && splits > 1) {
         void* p = nullptr;
         if (cudaMalloc(&p, (size_t)splits * M * N * sizeof(double)) != cudaSuccess)

@@ -25,7 +25,7 @@ namespace {
 
 constexpr int TBM = 128, TBN = 64, TBK = 32, TNT = 128;
 constexpr int kTmemCols = 64;                 // FP32 accumulator columns (= TBN)
-constexpr long long kSpinLimit = 1LL << 26;   // bounded mbarrier wait
+constexpr long long kSpinLimit = 1LL << 20;   // bounded mbarrier wait (about a second)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -133,6 +133,45 @@ __device__ __forceinline__ void mma<true>(uint32_t tmem, uint64_t da, uint64_t d
 
 }  // namespace
 
+// Per-block maxima of |X| (blocks 0 .. kScaleBlocks-1) and |Y| (the next kScaleBlocks) over the
+// elements the contraction reads, through its gather tables.  FP32 and its TF32 / BF16 subsets
+// cover about 1e-38 .. 3e38, while the FP64 tensors of a large network can sit far below that
+// (projector matrices of ~1e-35 at D=4, chi=64 with a normalised PEPS), so the tensor-core
+// kernel scales each operand by a power of two taken from these maxima.
+__global__ void __launch_bounds__(256) ctr_maxabs_kernel(const CtrLaunch a) {
+    const bool isY = blockIdx.x >= kScaleBlocks;
+    const int blk = isY ? blockIdx.x - kScaleBlocks : blockIdx.x;
+    const long long R = isY ? a.N : a.M;
+    const long long per = R * a.K;
+    const long long total = per * a.nb;
+    double m = 0.0;
+    for (long long e = blk * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)kScaleBlocks * blockDim.x) {
+        const int b = (int)(e / per);
+        const long long rem = e - b * per;
+        const int r = (int)(rem / a.K), k = (int)(rem - (long long)r * a.K);
+        const double v = isY ? a.Y[(a.yb ? a.yb[b] : 0) + a.yk[k] + a.yn[r]]
+                             : a.X[(a.xb ? a.xb[b] : 0) + a.xm[r] + a.xk[k]];
+        m = fmax(m, fabs(v));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    __shared__ double wm[8];
+    if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double mm = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mm = fmax(mm, wm[w]);
+        a.scale_ws[blockIdx.x] = mm;
+    }
+}
+
+// power-of-two exponent e with max < 2^e (0 for a zero or non-finite maximum)
+__device__ __forceinline__ int scale_exponent(double mx) {
+    int e = 0;
+    if (mx > 0.0 && isfinite(mx)) frexp(mx, &e);
+    return e;
+}
+
 template <bool BF16, bool X3>
 __global__ void __launch_bounds__(TNT) ctr_tc_kernel(const CtrLaunch a) {
     using O = Op<BF16>;
@@ -149,6 +188,7 @@ __global__ void __launch_bounds__(TNT) ctr_tc_kernel(const CtrLaunch a) {
     __shared__ __align__(8) unsigned long long mbar;
     __shared__ uint32_t tmem_base;
     __shared__ int s_fail;
+    __shared__ double s_mx[2][TNT / 32];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.y * TBM, n0 = blockIdx.x * TBN;
@@ -175,6 +215,32 @@ __global__ void __launch_bounds__(TNT) ctr_tc_kernel(const CtrLaunch a) {
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_base;
     const uint32_t bar = smem_u32(&mbar);
+    // operand scales 2^-ex, 2^-ey (exact) so that both operands have max |.| < 1; the product
+    // is scaled back by 2^(ex + ey) in FP64 before it is stored
+    {
+        double mx = 0.0, my = 0.0;
+        for (int i = tid; i < kScaleBlocks; i += TNT) {
+            mx = fmax(mx, a.scale_ws[i]);
+            my = fmax(my, a.scale_ws[kScaleBlocks + i]);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            my = fmax(my, __shfl_xor_sync(0xffffffffu, my, o));
+        }
+        if (lane == 0) {
+            s_mx[0][warp] = mx;
+            s_mx[1][warp] = my;
+        }
+        __syncthreads();
+    }
+    double mxa = 0.0, mya = 0.0;
+#pragma unroll
+    for (int w = 0; w < TNT / 32; ++w) {
+        mxa = fmax(mxa, s_mx[0][w]);
+        mya = fmax(mya, s_mx[1][w]);
+    }
+    const int ex = scale_exponent(mxa), ey = scale_exponent(mya);
+    const double sx = ldexp(1.0, -ex), sy = ldexp(1.0, -ey), sxy = ldexp(1.0, ex + ey);
 
     const int kbeg = sp * a.kchunk;
     const int kend = min(a.K, kbeg + a.kchunk);
@@ -194,7 +260,7 @@ __global__ void __launch_bounds__(TNT) ctr_tc_kernel(const CtrLaunch a) {
             tile_pos<E>(e, mm, kk);
             const int k = k0 + kk;
             const int om_ = sxm[mm];
-            const double v = (om_ >= 0 && k < kend) ? a.X[xbo + om_ + a.xk[k]] : 0.0;
+            const double v = (om_ >= 0 && k < kend) ? a.X[xbo + om_ + a.xk[k]] * sx : 0.0;
             T hi, lo;
             O::split(v, hi, lo);
             *reinterpret_cast<T*>(a_hi + e * E) = hi;
@@ -205,7 +271,7 @@ __global__ void __launch_bounds__(TNT) ctr_tc_kernel(const CtrLaunch a) {
             tile_pos<E>(e, nn, kk);
             const int k = k0 + kk;
             const int on_ = syn[nn];
-            const double v = (on_ >= 0 && k < kend) ? a.Y[ybo + a.yk[k] + on_] : 0.0;
+            const double v = (on_ >= 0 && k < kend) ? a.Y[ybo + a.yk[k] + on_] * sy : 0.0;
             T hi, lo;
             O::split(v, hi, lo);
             *reinterpret_cast<T*>(b_hi + e * E) = hi;
@@ -272,7 +338,7 @@ __global__ void __launch_bounds__(TNT) ctr_tc_kernel(const CtrLaunch a) {
                 for (int j = 0; j < 16; ++j) {
                     const int n = n0 + c0 + j;
                     if (n >= a.N) continue;
-                    const double v = (double)__uint_as_float(r[j]);
+                    const double v = (double)__uint_as_float(r[j]) * sxy;
                     if (a.splits > 1) {
                         a.partial[((long long)z * a.M + m) * a.N + n] = v;
                     } else {
@@ -326,6 +392,7 @@ static void launch_tc(const CtrLaunch& a, cudaStream_t s) {
 }
 
 void launch_ctr_tc(const CtrLaunch& a, cudaStream_t s) {
+    ctr_maxabs_kernel<<<2 * kScaleBlocks, 256, 0, s>>>(a);
     switch (a.precision) {
         case SCTM_PREC_TF32: launch_tc<false, false>(a, s); break;
         case SCTM_PREC_TF32X3: launch_tc<false, true>(a, s); break;

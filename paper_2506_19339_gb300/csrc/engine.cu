@@ -67,8 +67,9 @@ struct CtrStep : Step {
     void run(Engine& e) override {
         const int e0 = e.profile ? e.record(sid) : -1;
         launch_ctr(a, e.lane().streams[sid]);
-        const int splits = a.precision == SCTM_PREC_FP64 ? a.splits : a.tc_splits;
-        e.kernel_launches += splits > 1 ? 2 : 1;
+        const bool tc = a.precision != SCTM_PREC_FP64;
+        const int splits = tc ? a.tc_splits : a.splits;
+        e.kernel_launches += (splits > 1 ? 2 : 1) + (tc ? 1 : 0);
         if (e.profile) e.record_done(sid, KIND_CTR, flops, e0);
     }
 };
@@ -171,7 +172,7 @@ thread_local int Engine::cur_lane = 0;
 Engine::Engine(cudaStream_t s, int prec, double cut) : stream(s), precision(prec), cutoff(cut) {
     const char* dr = getenv("SCTM_DRYRUN");
     dry = dr && dr[0] == '1';
-    dev_err = ialloc({0});
+    dev_err = ialloc({0, 0});
     if (dry) return;
     for (int l = 0; l < kLanes; ++l) {
         Lane& L = lanes[l];
@@ -495,6 +496,11 @@ Engine::PPair Engine::projector(Network& net, Plan& P, const Ten& U, const Ten& 
         net.svd_steps.push_back(sv.get());
         return sv;
     };
+    // non-finite entries would send the QR iteration of gesvd into its iteration limit: zero
+    // them and flag the iteration as failed (SCTM_ENUMERIC)
+    int* nonfinite = dev_err + 1;
+    const long long nn = (long long)n * n;
+    push(P, std::make_unique<FnStep>([=](cudaStream_t s) { launch_sanitize(M.p, nn, nonfinite, s); }));
     if (svd_mode != SCTM_SVD_PARTIAL) {
         push(P, make_svd(Vs));
     } else {
@@ -947,6 +953,7 @@ void Engine::cold_svd(Network& net) {
 void Engine::init_env(Network& net, unsigned long long seed) {
     cold_svd(net);
     if (dry) return;
+    CUDA_OK(cudaMemsetAsync(dev_err, 0, 2 * sizeof(int), stream));
     unsigned long long q = 0;
     for (int i = 0; i < 4; ++i) launch_splitmix_fill(net.C[i].p, net.C[i].numel(), seed, q++, stream);
     for (int i = 0; i < 4; ++i)
@@ -979,10 +986,15 @@ void Engine::build_network(Network& net) {
 
 double Engine::cutoff_floor(int prec) {
     switch (prec) {
+        // Singular values of rho_B rho_T below the form's relative error of that product are
+        // noise, and S^-1/2 would amplify their vectors: measured on D=2, chi=16 (Ising,
+        // T=4.6), a cutoff of 1e-6 for the hi/lo forms let such directions through and moved
+        // ln kappa by 1e-2 against FP64 at the same cutoff, while 1e-3 (TF32) and 1e-2 (BF16)
+        // kept the plain forms within 3e-4.
         case SCTM_PREC_TF32: return 1e-3;    // 11-bit significand
         case SCTM_PREC_BF16: return 1e-2;    // 8-bit significand
-        case SCTM_PREC_TF32X3:
-        case SCTM_PREC_BF16X3: return 1e-6;  // hi/lo: about FP32 (FP32 accumulation)
+        case SCTM_PREC_TF32X3: return 1e-4;  // hi/lo, FP32 accumulation
+        case SCTM_PREC_BF16X3: return 1e-3;
         default: return 0.0;
     }
 }
@@ -998,6 +1010,11 @@ void Engine::finalize(Network& net) {
         if (net.splitk_need[k] > 0) net.splitk_ws[k] = dalloc((long long)net.splitk_need[k]);
     for (CtrStep* s : net.ctr_steps)
         if (s->partial_need > 0) s->a.partial = net.splitk_ws[s->sid];
+    for (CtrStep* s : net.ctr_steps) {
+        if (!s->mixed_ok) continue;
+        if (!net.scale_ws[s->sid]) net.scale_ws[s->sid] = dalloc(2 * kScaleBlocks);
+        s->a.scale_ws = net.scale_ws[s->sid];
+    }
     void* p = nullptr;
     if (!dry) {
         CUDA_OK(cudaMalloc(&p, std::max(net.n_svd, 1) * sizeof(int)));

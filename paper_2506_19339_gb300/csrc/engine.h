@@ -69,6 +69,7 @@ struct Network {
     int n_svd = 0;
     // per-network, per-stream work buffers, sized after the plans are built
     double* splitk_ws[kStreams] = {nullptr};
+    double* scale_ws[kStreams] = {nullptr};   // operand max-abs pass of the tensor-core form
     size_t splitk_need[kStreams] = {0};
     void* svd_dwork[kStreams] = {nullptr};
     size_t svd_dbytes = 0;
@@ -108,7 +109,9 @@ public:
     cusolverDnParams_t solver_params = nullptr;
     int precision;      // SCTM_PREC_* currently set on the move plans' contractions
     double cutoff;
-    int* dev_err = nullptr;  // device flag: a tensor-core contraction's bounded wait ran out
+    // device flags: [0] a tensor-core contraction's bounded wait ran out, [1] a projector matrix
+    // had non-finite entries (zeroed before the SVD)
+    int* dev_err = nullptr;
     bool mixed_build = false;  // contractions built now may run in a mixed-precision form
     // Arithmetic of the move plans' mixed-eligible contractions (absorption, half patches,
     // rho_B rho_T, renormalisation); projector formation, the spectrum and the local

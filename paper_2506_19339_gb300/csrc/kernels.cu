@@ -323,6 +323,23 @@ void launch_check_finite(const double* p, long long n, int* flag, cudaStream_t s
     check_finite_kernel<<<1, 256, 0, s>>>(p, n, flag);
 }
 
+__global__ void sanitize_kernel(double* p, long long n, int* flag) {
+    int bad = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (!isfinite(p[i])) {
+            p[i] = 0.0;
+            bad = 1;
+        }
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(flag, 1);
+}
+
+void launch_sanitize(double* p, long long n, int* flag, cudaStream_t s) {
+    const int blocks = (int)std::min<long long>((n + 255) / 256, 1024);
+    sanitize_kernel<<<std::max(blocks, 1), 256, 0, s>>>(p, n, flag);
+}
+
 // Convergence (Sec. III.D): S = singular values of rho_eff / Tr(rho_eff); dS = ||S - S_old||_2;
 // S_old <- S.  rho is chi x chi column-major (only its diagonal is read here, for the trace).
 __global__ void spectrum_update_kernel(const double* Sraw, const double* rho, int chi,

@@ -41,7 +41,9 @@ struct CtrLaunch {
     int tile = 64;                     // CTA output tile: 64 x 64 or 32 x 32 (FP64 kernel)
     int* err = nullptr;                // set to 1 by the tensor-core kernel on a wait timeout
     int tc_splits = 1, tc_kchunk = 1;  // split-K of the tensor-core kernel (128 x 64 tiles)
+    double* scale_ws = nullptr;        // 2 * kScaleBlocks doubles: per-block max |X|, max |Y|
 };
+constexpr int kScaleBlocks = 152;       // blocks of the operand max-abs pass (one per SM)
 
 void launch_ctr(const CtrLaunch& a, cudaStream_t s);
 // tensor-core variant (a.precision = SCTM_PREC_TF32 / TF32X3 / BF16 / BF16X3), 128 x 64 tiles
@@ -75,6 +77,8 @@ void launch_vt_columns(const double* VT, double* Vout, int n, int k, cudaStream_
 void launch_zero(double* p, long long n, cudaStream_t s);
 // flag[0] = 1 if any of p[0..n) is NaN or infinite, else 0
 void launch_check_finite(const double* p, long long n, int* flag, cudaStream_t s);
+// p[i] <- 0 where p[i] is not finite, and *flag <- 1 if any was (flag is never cleared here)
+void launch_sanitize(double* p, long long n, int* flag, cudaStream_t s);
 void launch_spectrum_update(const double* Sraw, const double* rho, int chi, double* S_old,
                             double* dS_out, cudaStream_t s);
 // lnk[0] = ln(Z11 Z00 / (Z10 Z01)) (NaN if the ratio is <= 0 or not finite), lnk[1] = Z11
