@@ -50,13 +50,16 @@ def parse():
                     help='FP64 SVD of the projectors: the partial SVD (warm-started subspace '
                          'iteration after a cuSOLVER gesvd cold solve), cuSOLVER gesvd (qr) or '
                          'gesvdp (polar)')
+    ap.add_argument('--D', type=int, default=None,
+                    help='override the PEPS bond dimension (small cases for profiler captures)')
+    ap.add_argument('--chi', type=int, default=None, help='override chi (profiler captures)')
     ap.add_argument('--precision', default='fp64', choices=list(PRECISIONS),
                     help='arithmetic of the move contractions (mixed forms polish in FP64)')
     return ap.parse_args()
 
 
-def workload_name(it):
-    w = WORKLOAD
+def workload_name(it, w=None):
+    w = w or WORKLOAD
     return ('split-CTMRG f+grad, 3D Ising PEPO, PEPS D=%d N(0,1) seed %d, chi=%d, T=%g, '
             '%d iterations (num + norm networks) per evaluation, tol %g' %
             (w['D'], w['seed'], w['chi'], w['T'], it, 1e-10))
@@ -189,7 +192,11 @@ def run_reference(args):
 def run_ours(args):
     import torch
     from paper_2506_19339_gb300 import build, inputs, sctm
-    w = WORKLOAD
+    w = dict(WORKLOAD)
+    if args.D:
+        w['D'] = args.D
+    if args.chi:
+        w['chi'] = args.chi
     world = int(os.environ.get('WORLD_SIZE', '1'))
     rank = int(os.environ.get('RANK', '0'))
     local = int(os.environ.get('LOCAL_RANK', '0'))
@@ -334,7 +341,7 @@ def run_ours(args):
         'higher_is_better': True, 'scaling': 'weak', 'vs_baseline': None,
         'dtype': 'f64' if args.precision == 'fp64' else args.precision + '+f64',
         'data': 'synthetic',
-        'config': {'workload': workload_name(args.iters), 'D': w['D'], 'chi': w['chi'],
+        'config': {'workload': workload_name(args.iters, w), 'D': w['D'], 'chi': w['chi'],
                    'T': w['T'], 'seed': w['seed'], 'iterations_per_eval': args.iters,
                    'precision': '%s move contractions, FP64 SVD (%s)' % (
                        args.precision.upper(), SVD_NAMES[args.svd]),
