@@ -594,6 +594,16 @@ sctm_status sctm_gemm(const double* X, const double* Y, double* O, int M, int N,
             st = SCTM_ENOMEM;
         else
             bufs.push_back(p), a.scale_ws = (double*)p;
+        void* q = nullptr;
+        if (st == SCTM_OK && cudaMalloc(&q, tc_pack_bytes_x(a)) != cudaSuccess)
+            st = SCTM_ENOMEM;
+        else if (st == SCTM_OK)
+            bufs.push_back(q), a.pack_x = q;
+        q = nullptr;
+        if (st == SCTM_OK && cudaMalloc(&q, tc_pack_bytes_y(a)) != cudaSuccess)
+            st = SCTM_ENOMEM;
+        else if (st == SCTM_OK)
+            bufs.push_back(q), a.pack_y = q;
     }
     if (st == SCTM_OK && splits > 1) {
         void* p = nullptr;

@@ -2,13 +2,17 @@
 // TF32 or BF16 operands with FP32 accumulation in tensor memory, optionally with hi/lo split
 // products (x = hi + lo; hi*hi + hi*lo + lo*hi) that recover most of the FP32 input precision.
 //
+// Each launch first finds max |X| and max |Y| (ctr_maxabs_kernel), then converts both operands
+// once (ctr_pack_kernel): gathered through the offset tables (the leg permutation is folded into
+// this pass, as in the FP64 kernel), scaled by a power of two into the format's range, split into
+// hi/lo and written as tiles whose bytes are already in the shared-memory image order: K-major,
+// no-swizzle canonical layout (8-row x 16-byte core matrices: K-adjacent core matrices 128 B
+// apart, M/N-adjacent ones (32 * elem / 16) * 128 B apart).  FP64 arithmetic is scarce on this
+// GPU, so it is spent once per operand element rather than once per tile that reads it.
 // One CTA = 128 threads = 4 warps computes a 128 x 64 output tile (one tcgen05.mma of M=128,
-// N=64 per K-step).  Per K chunk of 32: every thread gathers FP64 operand elements through the
-// offset tables (the leg permutation is folded into the load, as in the FP64 kernel), splits them
-// into hi/lo, and stores them to shared memory in the K-major, no-swizzle canonical layout
-// (8-row x 16-byte core matrices: K-adjacent core matrices 128 B apart, M/N-adjacent ones
-// (32 * elem / 16) * 128 B apart); one thread issues the MMAs and commits them to an mbarrier that
-// every thread waits on before the shared tiles are reused.  The epilogue reads the accumulator
+// N=64 per K-step).  Per K chunk of 32 the threads copy the packed tiles to shared memory with
+// 16-byte moves; one thread issues the MMAs and commits them to an mbarrier that every thread
+// waits on before the shared tiles are reused.  The epilogue reads the accumulator
 // with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31 = tile rows) and scatters FP64 results
 // through the output tables.  Every wait is bounded: on timeout the kernel records an error,
 // drains, frees its tensor memory and returns.
@@ -172,6 +176,79 @@ __device__ __forceinline__ int scale_exponent(double mx) {
     return e;
 }
 
+// Elements per packed tile and tile counts: X in 128-row tiles, Y in 64-row tiles, K in chunks of
+// 32, zero-padded; tile (b, r, c) of an operand with R row tiles and C chunks starts at element
+// ((b R + r) C + c) * rows * 32, and inside it element e sits where the shared-memory image puts
+// it (tile_pos).  The lo tiles follow all hi tiles.
+__host__ __device__ inline long long tc_tiles_x(const CtrLaunch& a) {
+    return (long long)a.nb * ((a.M + TBM - 1) / TBM) * ((a.K + TBK - 1) / TBK);
+}
+__host__ __device__ inline long long tc_tiles_y(const CtrLaunch& a) {
+    return (long long)a.nb * ((a.N + TBN - 1) / TBN) * ((a.K + TBK - 1) / TBK);
+}
+
+// Convert both operands once: gather through the tables, scale by the power of two from the
+// max-abs pass, split into hi (and lo) in the tensor-core format, and write the tiles in
+// shared-memory image order, so that the contraction kernel only copies bytes.
+template <bool BF16, bool X3>
+__global__ void __launch_bounds__(256) ctr_pack_kernel(const CtrLaunch a) {
+    using O = Op<BF16>;
+    using T = typename O::T;
+    constexpr int E = O::kElem;
+    __shared__ double wm[2][8];
+    double mx = 0.0, my = 0.0;
+    for (int i = threadIdx.x; i < kScaleBlocks; i += blockDim.x) {
+        mx = fmax(mx, a.scale_ws[i]);
+        my = fmax(my, a.scale_ws[kScaleBlocks + i]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        my = fmax(my, __shfl_xor_sync(0xffffffffu, my, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        wm[0][threadIdx.x >> 5] = mx;
+        wm[1][threadIdx.x >> 5] = my;
+    }
+    __syncthreads();
+    mx = my = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        mx = fmax(mx, wm[0][w]);
+        my = fmax(my, wm[1][w]);
+    }
+    const double sx = ldexp(1.0, -scale_exponent(mx)), sy = ldexp(1.0, -scale_exponent(my));
+    const int nkc = (a.K + TBK - 1) / TBK;
+    const long long nx = tc_tiles_x(a) * (TBM * TBK), ny = tc_tiles_y(a) * (TBN * TBK);
+    T* xh = (T*)a.pack_x;
+    T* yh = (T*)a.pack_y;
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < nx + ny;
+         g += (long long)gridDim.x * blockDim.x) {
+        const bool isY = g >= nx;
+        const long long q = isY ? g - nx : g;
+        const int rows = isY ? TBN : TBM;
+        const int e = (int)(q % (rows * TBK));
+        const long long tile = q / (rows * TBK);
+        const int c = (int)(tile % nkc);
+        const long long br = tile / nkc;
+        const int nrt = isY ? (a.N + TBN - 1) / TBN : (a.M + TBM - 1) / TBM;
+        const int r = (int)(br % nrt), b = (int)(br / nrt);
+        int rr, kk;
+        tile_pos<E>(e, rr, kk);
+        const int row = r * rows + rr, k = c * TBK + kk;
+        double v = 0.0;
+        if (isY) {
+            if (row < a.N && k < a.K) v = a.Y[(a.yb ? a.yb[b] : 0) + a.yk[k] + a.yn[row]] * sy;
+        } else {
+            if (row < a.M && k < a.K) v = a.X[(a.xb ? a.xb[b] : 0) + a.xm[row] + a.xk[k]] * sx;
+        }
+        T hi, lo;
+        O::split(v, hi, lo);
+        T* dst = isY ? yh : xh;
+        const long long total = isY ? ny : nx;
+        dst[q] = hi;
+        if (X3) dst[total + q] = lo;
+    }
+}
+
 template <bool BF16, bool X3>
 __global__ void __launch_bounds__(TNT) ctr_tc_kernel(const CtrLaunch a) {
     using O = Op<BF16>;
@@ -183,8 +260,6 @@ __global__ void __launch_bounds__(TNT) ctr_tc_kernel(const CtrLaunch a) {
     unsigned char* a_lo = smem + A_BYTES;
     unsigned char* b_hi = smem + 2 * A_BYTES;
     unsigned char* b_lo = smem + 2 * A_BYTES + B_BYTES;
-    __shared__ int sxm[TBM];
-    __shared__ int syn[TBN];
     __shared__ __align__(8) unsigned long long mbar;
     __shared__ uint32_t tmem_base;
     __shared__ int s_fail;
@@ -194,11 +269,7 @@ __global__ void __launch_bounds__(TNT) ctr_tc_kernel(const CtrLaunch a) {
     const int m0 = blockIdx.y * TBM, n0 = blockIdx.x * TBN;
     const int z = blockIdx.z;
     const int b = z / a.splits, sp = z % a.splits;
-    const long long xbo = a.xb ? a.xb[b] : 0;
-    const long long ybo = a.yb ? a.yb[b] : 0;
 
-    if (tid < TBM) sxm[tid] = (m0 + tid < a.M) ? a.xm[m0 + tid] : -1;
-    if (tid < TBN) syn[tid] = (n0 + tid < a.N) ? a.yn[n0 + tid] : -1;
     if (tid == 0) {
         s_fail = 0;
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
@@ -215,8 +286,8 @@ __global__ void __launch_bounds__(TNT) ctr_tc_kernel(const CtrLaunch a) {
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_base;
     const uint32_t bar = smem_u32(&mbar);
-    // operand scales 2^-ex, 2^-ey (exact) so that both operands have max |.| < 1; the product
-    // is scaled back by 2^(ex + ey) in FP64 before it is stored
+    // the packed operands were scaled by 2^-ex, 2^-ey (exact, max |.| < 1); the product is scaled
+    // back by 2^(ex + ey) in FP64 before it is stored
     {
         double mx = 0.0, my = 0.0;
         for (int i = tid; i < kScaleBlocks; i += TNT) {
@@ -240,7 +311,7 @@ __global__ void __launch_bounds__(TNT) ctr_tc_kernel(const CtrLaunch a) {
         mya = fmax(mya, s_mx[1][w]);
     }
     const int ex = scale_exponent(mxa), ey = scale_exponent(mya);
-    const double sx = ldexp(1.0, -ex), sy = ldexp(1.0, -ey), sxy = ldexp(1.0, ex + ey);
+    const double sxy = ldexp(1.0, ex + ey);
 
     const int kbeg = sp * a.kchunk;
     const int kend = min(a.K, kbeg + a.kchunk);
@@ -249,33 +320,38 @@ __global__ void __launch_bounds__(TNT) ctr_tc_kernel(const CtrLaunch a) {
     uint32_t phase = 0, fail_phase = 0;
     bool first = true;
     bool ok = true;
+    const int nkc = (a.K + TBK - 1) / TBK;
+    const long long xtiles = tc_tiles_x(a), ytiles = tc_tiles_y(a);
 
     for (int k0 = kbeg; k0 < kend && ok; k0 += TBK) {
-        // gather, split, stage.  Element e of a tile goes to byte e * E of its shared-memory
-        // image: e runs over the 16-byte core-matrix rows first (T elements along K), then the 8
-        // rows of a core matrix, then the core matrices along K, then the 8-row groups, so a warp
-        // writes contiguous bytes and reads T consecutive k of 32 / T rows.
-        for (int e = tid; e < TBM * TBK; e += TNT) {
-            int mm, kk;
-            tile_pos<E>(e, mm, kk);
-            const int k = k0 + kk;
-            const int om_ = sxm[mm];
-            const double v = (om_ >= 0 && k < kend) ? a.X[xbo + om_ + a.xk[k]] * sx : 0.0;
-            T hi, lo;
-            O::split(v, hi, lo);
-            *reinterpret_cast<T*>(a_hi + e * E) = hi;
-            if (X3) *reinterpret_cast<T*>(a_lo + e * E) = lo;
-        }
-        for (int e = tid; e < TBN * TBK; e += TNT) {
-            int nn, kk;
-            tile_pos<E>(e, nn, kk);
-            const int k = k0 + kk;
-            const int on_ = syn[nn];
-            const double v = (on_ >= 0 && k < kend) ? a.Y[ybo + a.yk[k] + on_] * sy : 0.0;
-            T hi, lo;
-            O::split(v, hi, lo);
-            *reinterpret_cast<T*>(b_hi + e * E) = hi;
-            if (X3) *reinterpret_cast<T*>(b_lo + e * E) = lo;
+        // copy the packed tiles (already in shared-memory image order) with 16-byte moves
+        {
+            const int kc = k0 / TBK;
+            const long long xt = ((long long)b * gridDim.y + blockIdx.y) * nkc + kc;
+            const long long yt = ((long long)b * gridDim.x + blockIdx.x) * nkc + kc;
+            const uint4* gx = reinterpret_cast<const uint4*>(
+                reinterpret_cast<const unsigned char*>(a.pack_x) + xt * A_BYTES);
+            const uint4* gy = reinterpret_cast<const uint4*>(
+                reinterpret_cast<const unsigned char*>(a.pack_y) + yt * B_BYTES);
+            uint4* sa = reinterpret_cast<uint4*>(a_hi);
+            uint4* sb = reinterpret_cast<uint4*>(b_hi);
+            constexpr int NA = A_BYTES / 16, NB = B_BYTES / 16;
+#pragma unroll
+            for (int i = tid; i < NA; i += TNT) sa[i] = gx[i];
+#pragma unroll
+            for (int i = tid; i < NB; i += TNT) sb[i] = gy[i];
+            if (X3) {
+                const uint4* gxl = reinterpret_cast<const uint4*>(
+                    reinterpret_cast<const unsigned char*>(a.pack_x) + (xtiles + xt) * A_BYTES);
+                const uint4* gyl = reinterpret_cast<const uint4*>(
+                    reinterpret_cast<const unsigned char*>(a.pack_y) + (ytiles + yt) * B_BYTES);
+                uint4* sal = reinterpret_cast<uint4*>(a_lo);
+                uint4* sbl = reinterpret_cast<uint4*>(b_lo);
+#pragma unroll
+                for (int i = tid; i < NA; i += TNT) sal[i] = gxl[i];
+#pragma unroll
+                for (int i = tid; i < NB; i += TNT) sbl[i] = gyl[i];
+            }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
@@ -376,8 +452,16 @@ __global__ void __launch_bounds__(TNT) ctr_tc_kernel(const CtrLaunch a) {
     }
 }
 
+size_t tc_pack_bytes_x(const CtrLaunch& a) { return (size_t)tc_tiles_x(a) * TBM * TBK * 4 * 2; }
+size_t tc_pack_bytes_y(const CtrLaunch& a) { return (size_t)tc_tiles_y(a) * TBN * TBK * 4 * 2; }
+
 template <bool BF16, bool X3>
 static void launch_tc(const CtrLaunch& a, cudaStream_t s) {
+    {
+        const long long n = tc_tiles_x(a) * (TBM * TBK) + tc_tiles_y(a) * (TBN * TBK);
+        const int blocks = (int)std::min<long long>((n + 255) / 256, 4096);
+        ctr_pack_kernel<BF16, X3><<<std::max(blocks, 1), 256, 0, s>>>(a);
+    }
     constexpr int E = BF16 ? 2 : 4;
     // hi and lo tiles of A and B; at least 32 KB so that at most 7 CTAs share an SM and their
     // 64-column tensor-memory allocations (7 x 64 <= 512) never wait on one another

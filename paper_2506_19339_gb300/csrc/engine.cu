@@ -69,7 +69,7 @@ struct CtrStep : Step {
         launch_ctr(a, e.lane().streams[sid]);
         const bool tc = a.precision != SCTM_PREC_FP64;
         const int splits = tc ? a.tc_splits : a.splits;
-        e.kernel_launches += (splits > 1 ? 2 : 1) + (tc ? 1 : 0);
+        e.kernel_launches += (splits > 1 ? 2 : 1) + (tc ? 2 : 0);
         if (e.profile) e.record_done(sid, KIND_CTR, flops, e0);
     }
 };
@@ -1010,10 +1010,22 @@ void Engine::finalize(Network& net) {
         if (net.splitk_need[k] > 0) net.splitk_ws[k] = dalloc((long long)net.splitk_need[k]);
     for (CtrStep* s : net.ctr_steps)
         if (s->partial_need > 0) s->a.partial = net.splitk_ws[s->sid];
+    size_t px[kStreams] = {0}, py[kStreams] = {0};
+    for (CtrStep* s : net.ctr_steps) {
+        if (!s->mixed_ok) continue;
+        px[s->sid] = std::max(px[s->sid], tc_pack_bytes_x(s->a));
+        py[s->sid] = std::max(py[s->sid], tc_pack_bytes_y(s->a));
+    }
+    for (int k = 0; k < kStreams; ++k) {
+        if (px[k] > 0) net.pack_x[k] = dalloc((long long)((px[k] + 7) / 8));
+        if (py[k] > 0) net.pack_y[k] = dalloc((long long)((py[k] + 7) / 8));
+    }
     for (CtrStep* s : net.ctr_steps) {
         if (!s->mixed_ok) continue;
         if (!net.scale_ws[s->sid]) net.scale_ws[s->sid] = dalloc(2 * kScaleBlocks);
         s->a.scale_ws = net.scale_ws[s->sid];
+        s->a.pack_x = net.pack_x[s->sid];
+        s->a.pack_y = net.pack_y[s->sid];
     }
     void* p = nullptr;
     if (!dry) {

@@ -70,6 +70,8 @@ struct Network {
     // per-network, per-stream work buffers, sized after the plans are built
     double* splitk_ws[kStreams] = {nullptr};
     double* scale_ws[kStreams] = {nullptr};   // operand max-abs pass of the tensor-core form
+    void* pack_x[kStreams] = {nullptr};       // packed tensor-core operands (per stream)
+    void* pack_y[kStreams] = {nullptr};
     size_t splitk_need[kStreams] = {0};
     void* svd_dwork[kStreams] = {nullptr};
     size_t svd_dbytes = 0;

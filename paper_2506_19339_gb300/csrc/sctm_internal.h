@@ -42,7 +42,12 @@ struct CtrLaunch {
     int* err = nullptr;                // set to 1 by the tensor-core kernel on a wait timeout
     int tc_splits = 1, tc_kchunk = 1;  // split-K of the tensor-core kernel (128 x 64 tiles)
     double* scale_ws = nullptr;        // 2 * kScaleBlocks doubles: per-block max |X|, max |Y|
+    void* pack_x = nullptr;            // tensor-core operands, converted once per launch into
+    void* pack_y = nullptr;            //   hi (then lo) tiles in shared-memory image order
 };
+// bytes of the packed tensor-core operands (hi and lo, TF32: the largest form)
+size_t tc_pack_bytes_x(const CtrLaunch& a);
+size_t tc_pack_bytes_y(const CtrLaunch& a);
 constexpr int kScaleBlocks = 152;       // blocks of the operand max-abs pass (one per SM)
 
 void launch_ctr(const CtrLaunch& a, cudaStream_t s);
