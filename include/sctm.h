@@ -114,7 +114,14 @@ sctm_status sctm_set_peps(sctm_ctx* ctx, const double* peps, int reset_env);
  * of rho_eff = C1 C2 C3 C4 / Tr).  Each network stops on its own.  tol <= 0 runs exactly
  * max_it iterations.  *it_done (may be NULL) = the larger iteration count of the two networks;
  * *last_dS (may be NULL) = the larger final ||dS||_2.  Returns SCTM_ENOCONV when tol > 0 and a
- * network did not converge within max_it (the environments are still updated). */
+ * network did not converge within max_it (the environments are still updated).
+ * Mixed forms (o->precision != SCTM_PREC_FP64): each call starts in the context's form and
+ * stays in it while ||dS|| falls, then polishes in FP64 once ||dS|| is below the form's level
+ * (TF32 1e-4, BF16 1e-3, TF32 hi/lo 1e-6, BF16 hi/lo 1e-5) or has not halved in three
+ * iterations; convergence is only declared on FP64 iterations.  The pseudo-inverse cutoff is
+ * raised to the form's floor (1e-3, 1e-2, 1e-4, 1e-3) while the form is in use.
+ * Errors: ENUMERIC (non-finite spectrum change or projector matrix), ETIMEOUT (a bounded wait
+ * of the tensor-core kernel ran out), ECUSOLVER, ECUDA. */
 sctm_status sctm_iterate(sctm_ctx* ctx, int max_it, double tol, int* it_done, double* last_dS);
 
 /* sctm_free_energy -- f per 3D site in FP64 from the current environments (Sec. II):

@@ -265,7 +265,7 @@ sctm_status sctm_iterate(sctm_ctx* ctx, int max_it, double tol, int* it_done, do
                     } else {
                         ++stall;
                     }
-                    if (dS < Engine::cutoff_floor(form) || stall >= 3)
+                    if (dS < Engine::switch_level(form) || stall >= 3)
                         e.set_precision(net, SCTM_PREC_FP64);
                     continue;
                 }

@@ -999,6 +999,17 @@ double Engine::cutoff_floor(int prec) {
     }
 }
 
+double Engine::switch_level(int prec) {
+    // spectrum change below which a mixed-form iteration has reached the form's rounding level
+    switch (prec) {
+        case SCTM_PREC_TF32: return 1e-4;
+        case SCTM_PREC_BF16: return 1e-3;
+        case SCTM_PREC_TF32X3: return 1e-6;
+        case SCTM_PREC_BF16X3: return 1e-5;
+        default: return 0.0;
+    }
+}
+
 void Engine::set_precision(Network& net, int prec) {
     for (CtrStep* s : net.ctr_steps) s->a.precision = s->mixed_ok ? prec : SCTM_PREC_FP64;
     net.precision = prec;

@@ -122,6 +122,8 @@ public:
     // Smallest useful pseudo-inverse cutoff s_k/s_1 for a contraction form: below it the
     // singular values of rho_B rho_T are rounding noise of that form.
     static double cutoff_floor(int prec);
+    // ||dS|| at which sctm_iterate leaves a mixed form for the FP64 polish
+    static double switch_level(int prec);
     int svd_mode = SCTM_SVD_QR;
     bool dry = false;  // SCTM_DRYRUN=1: build plans with placeholder pointers, no CUDA calls
     int cur_stream = 0;  // stream index given to steps while a plan is being built

@@ -168,23 +168,20 @@ __global__ void __launch_bounds__(kPsvdThreads)
     extern __shared__ double sm[];
     double* R = sm;              // row-major k x k: scaled Gram, then the unscaled factor rows
     double* X = sm + k * k;      // row-major k x k: F^-1
-    double* d = sm + 2 * k * k;  // column norms
+    double* d = sm + 2 * k * k;  // reciprocal column norms
     double* rinv = d + k;        // reciprocal pivots
     const int tid = threadIdx.x, nt = blockDim.x;
-    for (int i = tid; i < k; i += nt) {
+    for (int i = tid; i < k; i += nt) {  // d = 1 / column norm (0 for a zero column)
         const double g = G[i + (long long)i * k];
-        d[i] = g > 0.0 ? sqrt(g) : 0.0;
+        d[i] = g > 0.0 ? 1.0 / sqrt(g) : 0.0;
     }
     __syncthreads();
     for (int e = tid; e < k * k; e += nt) {
         const int i = e / k, j = e % k;
-        const double di = d[i], dj = d[j];
-        R[e] = (di > 0.0 && dj > 0.0) ? G[i + (long long)j * k] / (di * dj) + (i == j ? shift : 0.0)
-                                       : 0.0;
+        R[e] = G[i + (long long)j * k] * d[i] * d[j] + ((i == j && d[i] > 0.0) ? shift : 0.0);
     }
     __syncthreads();
     block_cholesky(R, rinv, k);
-    for (int i = tid; i < k; i += nt) d[i] = d[i] > 0.0 ? 1.0 / d[i] : 0.0;  // now 1 / norm
     // X = F^-1 by back substitution, one column per thread.  With F[r][l] = R[r][l] rinv[r] and
     // F[r][r] = 1 / rinv[r]:  x_r = rinv[r] (delta_rc - rinv[r] sum_{l > r} R[r][l] x_l)
     for (int c = tid; c < k; c += nt) {
