@@ -28,10 +28,12 @@ WORKLOAD = dict(D=4, chi=64, T=4.5, seed=2)   # the configuration the metric is 
 NOMINAL_FP64_TFLOPS = 1.25                     # GB300 FP64 (vector and tensor), nominal
 NOMINAL_BF16_TFLOPS = 2250.0
 PRECISIONS = {'fp64': 0, 'tf32': 1, 'tf32x3': 2, 'bf16': 3, 'bf16x3': 4}
-SVD_MODES = {'qr': 0, 'polar': 1, 'partial': 2}
+SVD_MODES = {'qr': 0, 'polar': 1, 'partial': 2, 'partial-random': 3}
 SVD_NAMES = {'qr': 'cuSOLVER gesvd', 'polar': 'cuSOLVER gesvdp',
              'partial': 'partial SVD: gesvd cold solve, then warm-started subspace iteration + '
-                        'one-CTA Jacobi'}
+                        'one-CTA Jacobi',
+             'partial-random': 'partial SVD: randomized cold solve (4 subspace steps), then '
+                               'warm-started subspace iteration + one-CTA Jacobi'}
 
 
 def parse():
@@ -46,7 +48,7 @@ def parse():
     ap.add_argument('--batch', type=int, default=0,
                     help='batched sweep: B contexts (T uniform in [4.40, 4.62], seeds 100..) '
                          'iterated concurrently; 0 = the single-instance workload')
-    ap.add_argument('--svd', default='partial', choices=['partial', 'qr', 'polar'],
+    ap.add_argument('--svd', default='partial', choices=list(SVD_MODES),
                     help='FP64 SVD of the projectors: the partial SVD (warm-started subspace '
                          'iteration after a cuSOLVER gesvd cold solve), cuSOLVER gesvd (qr) or '
                          'gesvdp (polar)')

@@ -141,8 +141,7 @@ sctm_status sctm_create(const double* peps, const double* pepo, int chi, const s
         opts.precision < SCTM_PREC_FP64 || opts.precision > SCTM_PREC_BF16X3 ||
         opts.grad_mode != SCTM_GRAD_ENV ||
         !(opts.svd_cutoff >= 0.0) || opts.D > 64 || opts.d > 64 || opts.p > 64 ||
-        (opts.svd_mode != SCTM_SVD_QR && opts.svd_mode != SCTM_SVD_POLAR &&
-         opts.svd_mode != SCTM_SVD_PARTIAL))
+        opts.svd_mode < SCTM_SVD_QR || opts.svd_mode > SCTM_SVD_PARTIAL_RANDOM)
         return SCTM_EINVAL;
     std::unique_ptr<sctm_ctx> c(new sctm_ctx());
     c->opts = opts;

@@ -108,13 +108,25 @@ struct SvdStep : Step {
 
 // The partial SVD of one projector matrix: a full SVD (cold) while no warm-start subspace
 // exists, the warm-started subspace iteration step otherwise (psvd.cu has the algorithm).
+// SCTM_SVD_PARTIAL_RANDOM replaces the cold full SVD by kRandomColdSteps warm steps from a
+// pseudo-random subspace.
+constexpr int kRandomColdSteps = 4;
 struct PartialSvdStep : Step {
     Plan cold, warm;
+    Plan seed;                // randomized cold start: a pseudo-random subspace
     bool is_warm = false;
-    bool can_warm = true;  // false when the subspace exceeds the one-CTA kernels' limit
+    bool can_warm = true;     // false when the subspace exceeds the one-CTA kernels' limit
+    int random_steps = 0;     // > 0: cold solve = seed + this many warm steps instead of gesvd
     void run(Engine& e) override {
         const int e0 = e.profile ? e.record(sid) : -1;
-        e.run_sub(is_warm ? warm : cold);
+        if (is_warm) {
+            e.run_sub(warm);
+        } else if (random_steps > 0 && can_warm) {
+            e.run_sub(seed);
+            for (int i = 0; i < random_steps; ++i) e.run_sub(warm);
+        } else {
+            e.run_sub(cold);
+        }
         is_warm = can_warm;
         if (e.profile) e.record_done(sid, KIND_SVD, 0, e0);
     }
@@ -501,7 +513,7 @@ Engine::PPair Engine::projector(Network& net, Plan& P, const Ten& U, const Ten& 
     int* nonfinite = dev_err + 1;
     const long long nn = (long long)n * n;
     push(P, std::make_unique<FnStep>([=](cudaStream_t s) { launch_sanitize(M.p, nn, nonfinite, s); }));
-    if (svd_mode != SCTM_SVD_PARTIAL) {
+    if (svd_mode != SCTM_SVD_PARTIAL && svd_mode != SCTM_SVD_PARTIAL_RANDOM) {
         push(P, make_svd(Vs));
     } else {
         // subspace of chi + oversampling columns (Sec. III's partial SVD); the cold solve is
@@ -575,6 +587,14 @@ Engine::PPair Engine::projector(Network& net, Plan& P, const Ten& U, const Ten& 
             const unsigned long long salt = 0x5EEDull * (unsigned long long)(info_idx + 1);
             push(W, std::make_unique<FnStep>(
                         [=](cudaStream_t s) { launch_refill(Vs, n, k, S, salt, s); }));
+            if (svd_mode == SCTM_SVD_PARTIAL_RANDOM) {
+                // randomized cold start: every subspace column pseudo-random, then warm steps
+                ps->random_steps = kRandomColdSteps;
+                const unsigned long long seed0 = 0xC01Dull * (unsigned long long)(info_idx + 1);
+                push(ps->seed, std::make_unique<FnStep>([=](cudaStream_t s) {
+                    launch_refill(Vs, n, k, nullptr, seed0, s);
+                }));
+            }
         }
         net.psvd_steps.push_back(ps.get());
         push(P, std::move(ps));

@@ -342,12 +342,12 @@ __global__ void vt_columns_kernel(const double* __restrict__ VT, double* __restr
     }
 }
 
-// Columns c with S[c] == 0 (a zero column of the subspace basis) get uniform [-1, 1) entries
-// from SplitMix64 (Steele, Lea, Flood 2014) at counter seed + c n + r.
+// Columns c with S[c] == 0 (a zero column of the subspace basis; every column when S is null)
+// get uniform [-1, 1) entries from SplitMix64 (Steele, Lea, Flood 2014) at counter c n + r.
 __global__ void refill_kernel(double* __restrict__ V, int n, int k, const double* __restrict__ S,
                               unsigned long long seed) {
     const int c = blockIdx.x;
-    if (c >= k || S[c] != 0.0) return;
+    if (c >= k || (S && S[c] != 0.0)) return;
     for (int r = threadIdx.x; r < n; r += blockDim.x) {
         unsigned long long z = seed + ((unsigned long long)c * n + r + 1ULL) * 0x9E3779B97F4A7C15ULL;
         z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
