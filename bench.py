@@ -48,10 +48,10 @@ def parse():
     ap.add_argument('--batch', type=int, default=0,
                     help='batched sweep: B contexts (T uniform in [4.40, 4.62], seeds 100..) '
                          'iterated concurrently; 0 = the single-instance workload')
-    ap.add_argument('--svd', default='partial', choices=list(SVD_MODES),
-                    help='FP64 SVD of the projectors: the partial SVD (warm-started subspace '
-                         'iteration after a cuSOLVER gesvd cold solve), cuSOLVER gesvd (qr) or '
-                         'gesvdp (polar)')
+    ap.add_argument('--svd', default='partial-random', choices=list(SVD_MODES),
+                    help='FP64 SVD of the projectors: the partial SVD with a randomized cold '
+                         'solve (partial-random) or a gesvd cold solve (partial), cuSOLVER gesvd '
+                         '(qr) or gesvdp (polar)')
     ap.add_argument('--D', type=int, default=None,
                     help='override the PEPS bond dimension (small cases for profiler captures)')
     ap.add_argument('--chi', type=int, default=None, help='override chi (profiler captures)')

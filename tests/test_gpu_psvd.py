@@ -1,12 +1,13 @@
 """GPU: the partial SVD (Sec. III's iterative solver for the largest chi singular triplets) against
 the FP64 oracle, whose projectors come from a full SVD.
 
-The first solve of every projector after a cold start is a full SVD; later solves are one
+The first solve of every projector after a cold start is a full SVD (SCTM_SVD_PARTIAL) or four
+subspace steps from a pseudo-random subspace (SCTM_SVD_PARTIAL_RANDOM); later solves are one
 warm-started subspace-iteration step, whose subspace error decays geometrically with the
 iterations.  At a fixed point the two methods have the same projectors, so converged values
 agree to the convergence level; after a fixed number of iterations from the cold start they agree
 to the decayed subspace error of the first warm solves (f to 1e-10, g to 1e-5 on the contractive
-inputs below, measured 3e-11 and 1e-6 at worst)."""
+inputs below, measured 3e-11 and 1e-6 at worst in both modes)."""
 import numpy as np
 import pytest
 
@@ -31,14 +32,18 @@ def _oracle(A, T, chi, iters, tol=None):
     return sc.evaluate(A, ising.ising_pepo(1.0 / T), ising.identity_pepo(), T, chi, iters, tol)
 
 
+MODES = [sctm.SCTM_SVD_PARTIAL, sctm.SCTM_SVD_PARTIAL_RANDOM]
+
+
+@pytest.mark.parametrize('mode', MODES)
 @pytest.mark.parametrize('D,chi,T,seed,eps,iters', [
     (2, 16, 4.6, 7, 0.3, 40),
     (3, 10, 4.4, 4, 0.1, 30),
     (2, 7, 4.4, 3, 0.3, 30),
 ])
-def test_partial_svd_parity_fixed_iterations(D, chi, T, seed, eps, iters):
+def test_partial_svd_parity_fixed_iterations(D, chi, T, seed, eps, iters, mode):
     A = inputs.perturbed_product_peps(D, seed, eps=eps)
-    r = _ctx(A, T, chi)
+    r = _ctx(A, T, chi, mode)
     try:
         r.iterate(iters, 0.0)
         f, g = r.free_energy(), r.grad()
@@ -49,14 +54,15 @@ def test_partial_svd_parity_fixed_iterations(D, chi, T, seed, eps, iters):
     assert np.linalg.norm(g - ref['g']) <= 1e-5 * np.linalg.norm(ref['g'])
 
 
-def test_partial_svd_converged_fixed_point():
+@pytest.mark.parametrize('mode', MODES)
+def test_partial_svd_converged_fixed_point(mode):
     """Converged f against the oracle's converged f (1e-9: the oracle's own f moves by 6.4e-11
     between stopping at 1e-11 and 1e-13 on this input), and the partial run's fixed point is a
     fixed point of the full-SVD iteration: ten full-SVD iterations from it move f by less than
     1e-10."""
     T, chi = 4.6, 16
     A = inputs.perturbed_product_peps(2, 7)
-    rp, rq = _ctx(A, T, chi), _ctx(A, T, chi, sctm.SCTM_SVD_QR)
+    rp, rq = _ctx(A, T, chi, mode), _ctx(A, T, chi, sctm.SCTM_SVD_QR)
     try:
         st, it, ds = rp.iterate(400, 1e-11)
         assert st == sctm.SCTM_OK, (st, it, ds)
@@ -74,11 +80,12 @@ def test_partial_svd_converged_fixed_point():
     assert abs(fq - f) <= 1e-10 * abs(f), (fq, f)
 
 
-def test_partial_svd_full_size_runs():
+@pytest.mark.parametrize('mode', MODES)
+def test_partial_svd_full_size_runs(mode):
     """D=4, chi=64 (subspace 80 of 512): a cold and three warm iterations complete without an
     error status, and the spectrum change is finite."""
     A = inputs.random_peps(4, 2)
-    r = _ctx(A, 4.5, 64)
+    r = _ctx(A, 4.5, 64, mode)
     try:
         st, it, ds = r.iterate(4, 0.0)
         assert st in (sctm.SCTM_OK, sctm.SCTM_ENOCONV) and it == 4 and np.isfinite(ds)
