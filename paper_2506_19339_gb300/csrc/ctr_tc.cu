@@ -145,26 +145,28 @@ __device__ __forceinline__ void mma<true>(uint32_t tmem, uint64_t da, uint64_t d
 __global__ void __launch_bounds__(256) ctr_maxabs_kernel(const CtrLaunch a) {
     const bool isY = blockIdx.x >= kScaleBlocks;
     const int blk = isY ? blockIdx.x - kScaleBlocks : blockIdx.x;
-    const long long R = isY ? a.N : a.M;
-    const long long per = R * a.K;
-    const long long total = per * a.nb;
+    const int R = isY ? a.N : a.M;
+    const long long rows = (long long)R * a.nb;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nwb = blockDim.x >> 5;
     double m = 0.0;
-    for (long long e = blk * (long long)blockDim.x + threadIdx.x; e < total;
-         e += (long long)kScaleBlocks * blockDim.x) {
-        const int b = (int)(e / per);
-        const long long rem = e - b * per;
-        const int r = (int)(rem / a.K), k = (int)(rem - (long long)r * a.K);
-        const double v = isY ? a.Y[(a.yb ? a.yb[b] : 0) + a.yk[k] + a.yn[r]]
-                             : a.X[(a.xb ? a.xb[b] : 0) + a.xm[r] + a.xk[k]];
-        m = fmax(m, fabs(v));
+    // warp per (batch, row), lanes along K: no division in the inner loop
+    for (long long w = (long long)blk * nwb + wib; w < rows; w += (long long)kScaleBlocks * nwb) {
+        const int b = (int)(w / R), r = (int)(w - (long long)b * R);
+        if (isY) {
+            const long long base = (a.yb ? a.yb[b] : 0) + a.yn[r];
+            for (int k = lane; k < a.K; k += 32) m = fmax(m, fabs(a.Y[base + a.yk[k]]));
+        } else {
+            const long long base = (a.xb ? a.xb[b] : 0) + a.xm[r];
+            for (int k = lane; k < a.K; k += 32) m = fmax(m, fabs(a.X[base + a.xk[k]]));
+        }
     }
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
     __shared__ double wm[8];
-    if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+    if (lane == 0) wm[wib] = m;
     __syncthreads();
     if (threadIdx.x == 0) {
         double mm = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mm = fmax(mm, wm[w]);
+        for (int w = 0; w < nwb; ++w) mm = fmax(mm, wm[w]);
         a.scale_ws[blockIdx.x] = mm;
     }
 }
@@ -217,35 +219,38 @@ __global__ void __launch_bounds__(256) ctr_pack_kernel(const CtrLaunch a) {
     }
     const double sx = ldexp(1.0, -scale_exponent(mx)), sy = ldexp(1.0, -scale_exponent(my));
     const int nkc = (a.K + TBK - 1) / TBK;
-    const long long nx = tc_tiles_x(a) * (TBM * TBK), ny = tc_tiles_y(a) * (TBN * TBK);
+    const long long tx = tc_tiles_x(a), ty = tc_tiles_y(a);
+    const long long nx = tx * (TBM * TBK), ny = ty * (TBN * TBK);
     T* xh = (T*)a.pack_x;
     T* yh = (T*)a.pack_y;
-    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < nx + ny;
-         g += (long long)gridDim.x * blockDim.x) {
-        const bool isY = g >= nx;
-        const long long q = isY ? g - nx : g;
+    // block per tile (X tiles, then Y tiles), threads over the tile's elements: the tile is
+    // decoded once per thread, the element position by tile_pos (compile-time divisors)
+    for (long long tile = blockIdx.x; tile < tx + ty; tile += gridDim.x) {
+        const bool isY = tile >= tx;
+        const long long t = isY ? tile - tx : tile;
         const int rows = isY ? TBN : TBM;
-        const int e = (int)(q % (rows * TBK));
-        const long long tile = q / (rows * TBK);
-        const int c = (int)(tile % nkc);
-        const long long br = tile / nkc;
+        const int c = (int)(t % nkc);
+        const long long br = t / nkc;
         const int nrt = isY ? (a.N + TBN - 1) / TBN : (a.M + TBM - 1) / TBM;
         const int r = (int)(br % nrt), b = (int)(br / nrt);
-        int rr, kk;
-        tile_pos<E>(e, rr, kk);
-        const int row = r * rows + rr, k = c * TBK + kk;
-        double v = 0.0;
-        if (isY) {
-            if (row < a.N && k < a.K) v = a.Y[(a.yb ? a.yb[b] : 0) + a.yk[k] + a.yn[row]] * sy;
-        } else {
-            if (row < a.M && k < a.K) v = a.X[(a.xb ? a.xb[b] : 0) + a.xm[row] + a.xk[k]] * sx;
+        const long long xbo = (!isY && a.xb) ? a.xb[b] : 0, ybo = (isY && a.yb) ? a.yb[b] : 0;
+        T* dst = (isY ? yh : xh) + t * (long long)(rows * TBK);
+        const long long lo_off = isY ? ny : nx;
+        for (int e = threadIdx.x; e < rows * TBK; e += blockDim.x) {
+            int rr, kk;
+            tile_pos<E>(e, rr, kk);
+            const int row = r * rows + rr, k = c * TBK + kk;
+            double v = 0.0;
+            if (isY) {
+                if (row < a.N && k < a.K) v = a.Y[ybo + a.yk[k] + a.yn[row]] * sy;
+            } else {
+                if (row < a.M && k < a.K) v = a.X[xbo + a.xm[row] + a.xk[k]] * sx;
+            }
+            T hi, lo;
+            O::split(v, hi, lo);
+            dst[e] = hi;
+            if (X3) dst[lo_off + e] = lo;
         }
-        T hi, lo;
-        O::split(v, hi, lo);
-        T* dst = isY ? yh : xh;
-        const long long total = isY ? ny : nx;
-        dst[q] = hi;
-        if (X3) dst[total + q] = lo;
     }
 }
 
@@ -458,8 +463,8 @@ size_t tc_pack_bytes_y(const CtrLaunch& a) { return (size_t)tc_tiles_y(a) * TBN 
 template <bool BF16, bool X3>
 static void launch_tc(const CtrLaunch& a, cudaStream_t s) {
     {
-        const long long n = tc_tiles_x(a) * (TBM * TBK) + tc_tiles_y(a) * (TBN * TBK);
-        const int blocks = (int)std::min<long long>((n + 255) / 256, 4096);
+        const long long tiles = tc_tiles_x(a) + tc_tiles_y(a);
+        const int blocks = (int)std::min<long long>(tiles, 8192);
         ctr_pack_kernel<BF16, X3><<<std::max(blocks, 1), 256, 0, s>>>(a);
     }
     constexpr int E = BF16 ? 2 : 4;

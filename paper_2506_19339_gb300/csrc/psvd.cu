@@ -68,10 +68,10 @@ __device__ void block_cholesky(double* R, double* rinv, int k) {
         __syncthreads();
         const double ri = rinv[j];
         const double r2 = ri * ri;
-        const int m = k - j - 1;
-        for (int e = tid; e < m * m; e += nt) {
-            const int a = j + 1 + e / m, b = j + 1 + e % m;
-            if (b >= a) R[a * k + b] -= R[j * k + a] * R[j * k + b] * r2;
+        const int lane = tid & 31, nw = nt >> 5;
+        for (int a = j + 1 + (tid >> 5); a < k; a += nw) {
+            const double fa = R[j * k + a] * r2;
+            for (int b = a + lane; b < k; b += 32) R[a * k + b] -= fa * R[j * k + b];
         }
         __syncthreads();
     }
@@ -79,9 +79,11 @@ __device__ void block_cholesky(double* R, double* rinv, int k) {
 
 // Scratch of one Jacobi round, one entry per column pair.
 struct RoundScratch {
-    double* c;   // cosine (FP64 phase) / unused
+    double* c;   // cosine of each pair's rotation
     double* s;   // sine
     int* act;    // 1 if the pair rotates
+    int* pi;     // the pair's columns i, j (this round)
+    int* pj;
 };
 
 // One sweep of one-sided Jacobi rotations over all column pairs (circle-method rounds) of the
@@ -127,25 +129,26 @@ __device__ float jacobi_sweep(F* A, F* V, int kp, int ld, F tol, RoundScratch rs
             rs.c[q] = (double)c;
             rs.s[q] = (double)sn;
             rs.act[q] = act;
+            rs.pi[q] = i;
+            rs.pj[q] = j;
         }
         __syncthreads();
-        for (int e = tid; e < np * kp; e += nt) {
-            const int q = e / kp, r = e % kp;
+        // rotations: warp per pair, lane per row (no integer division in the inner loop)
+        for (int q = tid >> 5; q < np; q += nt >> 5) {
             if (!rs.act[q]) continue;
-            const int p0 = q, p1 = kp - 1 - q;
-            const int i = p0 == 0 ? 0 : 1 + (p0 - 1 + round) % (kp - 1);
-            const int j = 1 + (p1 - 1 + round) % (kp - 1);
             const F c = (F)rs.c[q], sn = (F)rs.s[q];
-            F* ai = A + (long long)i * ld;
-            F* aj = A + (long long)j * ld;
-            F* vi = V + (long long)i * ld;
-            F* vj = V + (long long)j * ld;
-            const F x = ai[r], y = aj[r];
-            ai[r] = c * x - sn * y;
-            aj[r] = sn * x + c * y;
-            const F u = vi[r], w = vj[r];
-            vi[r] = c * u - sn * w;
-            vj[r] = sn * u + c * w;
+            F* ai = A + (long long)rs.pi[q] * ld;
+            F* aj = A + (long long)rs.pj[q] * ld;
+            F* vi = V + (long long)rs.pi[q] * ld;
+            F* vj = V + (long long)rs.pj[q] * ld;
+            for (int r = tid & 31; r < kp; r += 32) {
+                const F x = ai[r], y = aj[r];
+                ai[r] = c * x - sn * y;
+                aj[r] = sn * x + c * y;
+                const F u = vi[r], w = vj[r];
+                vi[r] = c * u - sn * w;
+                vj[r] = sn * u + c * w;
+            }
         }
         __syncthreads();
     }
@@ -224,6 +227,8 @@ __global__ void __launch_bounds__(kPsvdThreads)
     rs.s = rs.c + np;
     int* rank = (int*)(rs.s + np);
     rs.act = rank + kp;
+    rs.pi = rs.act + np;
+    rs.pj = rs.pi + np;
     __shared__ float s_max;
     __shared__ int s_exp;
     __shared__ double s_wmax[kPsvdThreads / 32];
@@ -365,7 +370,7 @@ void launch_refill(double* V, int n, int k, const double* S, unsigned long long 
 size_t chol_orth_smem(int k) { return (size_t)(2 * k * k + 2 * k) * sizeof(double); }
 size_t jacobi_svd_smem(int k) {
     const int kp = k + (k & 1), ld = kp + 1, np = kp / 2;
-    return (size_t)(2 * kp * ld + kp + 2 * np) * sizeof(double) + (size_t)(kp + np) * sizeof(int);
+    return (size_t)(2 * kp * ld + kp + 2 * np) * sizeof(double) + (size_t)(kp + 3 * np) * sizeof(int);
 }
 
 void launch_chol_orth(const double* G, int k, double shift, double* T, cudaStream_t s) {
