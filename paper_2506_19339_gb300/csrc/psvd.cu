@@ -47,11 +47,6 @@ __device__ __forceinline__ double warp_allsum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
-__device__ __forceinline__ float warp_allsum(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
 
 // In-place right-looking Cholesky of the symmetric k x k matrix in R (row-major, upper triangle
 // used).  Rows are left unscaled: on return the upper factor is F[j][c] = R[j][c] * rinv[j]
