@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <functional>
 #include <map>
@@ -237,6 +238,11 @@ void Engine::record_done(int sid, int kind, long long flops, int e0) {
 }
 
 void Engine::harvest() {
+    // SCTM_TIMELINE=<file>: also append "lane stream kind flops start_ms end_ms" per record,
+    // relative to the first record of lane 0, stream 0 (a diagnostic of stream overlap)
+    const char* tl = getenv("SCTM_TIMELINE");
+    FILE* tf = (tl && tl[0] && lanes[0].ev_recs[0].size() > 0) ? fopen(tl, "a") : nullptr;
+    cudaEvent_t ref = tf ? lanes[0].ev_pool[0][lanes[0].ev_recs[0][0].e0] : nullptr;
     for (int l = 0; l < kLanes; ++l) {
         Lane& L = lanes[l];
         for (int sid = 0; sid < kStreams; ++sid) {
@@ -244,6 +250,13 @@ void Engine::harvest() {
                 float ms = 0;
                 CUDA_OK(cudaEventSynchronize(L.ev_pool[sid][r.e1]));
                 CUDA_OK(cudaEventElapsedTime(&ms, L.ev_pool[sid][r.e0], L.ev_pool[sid][r.e1]));
+                if (tf) {
+                    float t0 = 0, t1 = 0;
+                    cudaEventSynchronize(ref);
+                    cudaEventElapsedTime(&t0, ref, L.ev_pool[sid][r.e0]);
+                    cudaEventElapsedTime(&t1, ref, L.ev_pool[sid][r.e1]);
+                    fprintf(tf, "%d %d %d %lld %.4f %.4f\n", l, sid, r.kind, r.flops, t0, t1);
+                }
                 if (r.kind == KIND_CTR) {
                     ctr_ms += ms;
                     ctr_launches += 1;
@@ -257,6 +270,7 @@ void Engine::harvest() {
             L.ev_used[sid] = 0;
         }
     }
+    if (tf) fclose(tf);
 }
 
 double* Engine::dalloc(long long n) {
@@ -739,17 +753,67 @@ static void build_left_move(Engine& e, Network& net, Plan& P, const Frame& f) {
 
     // stage 1: bra-related legs of this column (P1, P2, P3) and the mirror-image pairs of the
     // opposite boundary on the ket-related legs of the next column -- six independent SVD
-    // pipelines, each on its own stream
+    // pipelines, each on its own stream.  Three more streams meanwhile build the parts of the
+    // two-column (stage 2) patches that do not involve the stage-1 projectors, so that this
+    // contraction work overlaps the SVD pipelines instead of following them.
     Engine::PPair pr1[6];
+    Ten ULA, URA, ULAO, URAO, Q1pre, Q2pre;           // upper halves (stream 7)
+    Ten LLkpre, LRkpre, LLipre, LRipre;               // lower halves, kappa and iota (stream 8)
+    Ten Q4pre, Q3pre;                                 // lower halves, alpha (stream 9)
     {
         const Ten* U[6] = {&Ua, &Ua, &Uk, &Uk, &Ui, &Ui};
         const Ten* L[6] = {&La, &La, &Lk, &Lk, &Li, &Li};
         const char* lab[6] = {"xAOBy", "xAOBy", "xesoby", "xesoby", "xeftby", "xeftby"};
         const char* tl[6] = {"xB", "yA", "xsb", "yes", "xtb", "yet"};
-        std::vector<Plan> sub(6);
+        std::vector<Plan> sub(9);
         for (int i = 0; i < 6; ++i) {
             e.cur_stream = i + 1;
             pr1[i] = e.projector(net, sub[i], *U[i], *L[i], lab[i], tl[i]);
+        }
+        {
+            Plan& S = sub[6];
+            e.cur_stream = 7;
+            auto D = [&](const char* spec, const Ten& X1, const Ten& Y1) { return e.ctr(net, S, spec, X1, Y1); };
+            ULA = D("hpobxl,splEr->hobxsEr", D("hvpob,vxl->hpobxl", Ct1, T4k), A);
+            URA = D("hpobyr,splEr->hobysEl", D("hwpob,wyr->hpobyr", Ct2, T2k), A);
+            ULAO = D("hobsErXL,tsoLfR->hbErXtfR", D("hobxsEr,xXL->hobsErXL", ULA, T4i), O);
+            URAO = D("hobsElYR,tsoLfR->hbElYtfL", D("hobysEl,yYR->hobsElYR", URA, T2i), O);
+            Q1pre = D("hbErtfRZM,tbMgS->hErfRZgS", D("hbErXtfR,XZM->hbErtfRZM", ULAO, T4b), B);
+            Q2pre = D("hbElWtfLS,tbMgS->hElWfLMg", D("hbElYtfL,YWS->hbElWtfLS", URAO, T2b), B);
+        }
+        {
+            Plan& S = sub[7];
+            e.cur_stream = 8;
+            auto D = [&](const char* spec, const Ten& X1, const Ten& Y1) { return e.ctr(net, S, spec, X1, Y1); };
+            Ten Y1 = D("hvEfg,Xvm->hEfgXm", Ct4, T4b);
+            Y1 = D("hEfgXm,tbmgQ->hEfXtbQ", Y1, B);
+            Y1 = D("hEfXtbQ,xXl->hEftbQxl", Y1, T4i);
+            LLkpre = D("hEftbQxl,tsolfR->hEbQxsoR", Y1, O);
+            Y1 = D("hwEfG,Ywm->hEfGYm", Ct3, T2b);
+            Y1 = D("hEfGYm,tbMGm->hEfYtbM", Y1, B);
+            Y1 = D("hEfYtbM,yYl->hEftbMyl", Y1, T2i);
+            LRkpre = D("hEftbMyl,tsoLfl->hEbMysoL", Y1, O);
+            Y1 = D("hvEfg,xvm->hEfgxm", Ct4, T4b);
+            LLipre = D("hEfgxm,tbmgQ->hEfxtbQ", Y1, B);
+            Y1 = D("hwEfG,ywm->hEfGym", Ct3, T2b);
+            LRipre = D("hEfGym,tbMGm->hEfytbM", Y1, B);
+        }
+        {
+            Plan& S = sub[8];
+            e.cur_stream = 9;
+            auto D = [&](const char* spec, const Ten& X1, const Ten& Y1) { return e.ctr(net, S, spec, X1, Y1); };
+            Ten Y1 = D("hvEfg,YvM->hEfgYM", Ct4, T4b);
+            Y1 = D("hEfgYM,tbMgS->hEfYtbS", Y1, B);
+            Y1 = D("hEfYtbS,XYL->hEftbSXL", Y1, T4i);
+            Y1 = D("hEftbSXL,tsoLfR->hEbSXsoR", Y1, O);
+            Y1 = D("hEbSXsoR,xXl->hEbSsoRxl", Y1, T4k);
+            Q4pre = D("hEbSsoRxl,splEr->hbSoRxpr", Y1, A);
+            Y1 = D("hwEfg,WwS->hEfgWS", Ct3, T2b);
+            Y1 = D("hEfgWS,tbMgS->hEfWtbM", Y1, B);
+            Y1 = D("hEfWtbM,ZWR->hEftbMZR", Y1, T2i);
+            Y1 = D("hEftbMZR,tsoLfR->hEbMZsoL", Y1, O);
+            Y1 = D("hEbMZsoL,yZr->hEbMsoLyr", Y1, T2k);
+            Q3pre = D("hEbMsoLyr,splEr->hbMoLypl", Y1, A);
         }
         e.cur_stream = 0;
         e.parallel(P, std::move(sub));
@@ -758,72 +822,49 @@ static void build_left_move(Engine& e, Network& net, Plan& P, const Frame& f) {
     const Engine::PPair &Pk = pr1[2], &Qk = pr1[3];   // [xl, s, B.u | k], [xr, A.d, s | k]
     const Engine::PPair &Pi = pr1[4], &Qi = pr1[5];   // [xl, s', B.u | k], [xr, A.d, s' | k]
 
-    // stage 2: two-column patches
-    // kappa (1 x 2 cells): (k2, A.d, O.u | O.u', B.u', kR)
-    const Ten ULA = C("hpobxl,splEr->hobxsEr", C("hvpob,vxl->hpobxl", Ct1, T4k), A);
-    const Ten ULk = C("hobxsEr,kxsb->hkEor", ULA, Pk.PT);
-    X = C("hwpob,wyr->hpobyr", Ct2, T2k);
-    const Ten URA = C("hpobyr,splEr->hobysEl", X, A);        // shared by kappa and iota
-    const Ten URk = C("hobysEl,kyEs->hlobk", URA, Qk.PT);
-    const Ten U2k = C("hkEor,hrOBK->kEoOBK", ULk, URk);
-    X = C("hvEfg,Xvm->hEfgXm", Ct4, T4b);
-    X = C("hEfgXm,tbmgQ->hEfXtbQ", X, B);
-    X = C("hEfXtbQ,xXl->hEftbQxl", X, T4i);
-    X = C("hEftbQxl,tsolfR->hEbQxsoR", X, O);
-    const Ten LLk = C("hEbQxsoR,xsbk->hkEoRQ", X, Pk.PB);
-    X = C("hwEfG,Ywm->hEfGYm", Ct3, T2b);
-    X = C("hEfGYm,tbMGm->hEfYtbM", X, B);
-    X = C("hEfYtbM,yYl->hEftbMyl", X, T2i);
-    X = C("hEftbMyl,tsoLfl->hEbMysoL", X, O);
-    const Ten LRk = C("hEbMysoL,yEsk->hLMobk", X, Qk.PB);
-    const Ten L2k = C("hkEoRQ,hRQOBK->kEoOBK", LLk, LRk);
-
-    // iota (1 x 2 cells): (k3, A.d, O.d | O.d', B.u', kR)
-    const Ten ULAO = C("hobsErXL,tsoLfR->hbErXtfR", C("hobxsEr,xXL->hobsErXL", ULA, T4i), O);
-    const Ten ULi = C("hbErXtfR,kXtb->hkEfrR", ULAO, Pi.PT);
-    const Ten URAO = C("hobsElYR,tsoLfR->hbElYtfL", C("hobysEl,yYR->hobsElYR", URA, T2i), O);
-    const Ten URi = C("hbElYtfL,kYEt->hlLfbk", URAO, Qi.PT);
-    const Ten U2i = C("hkEfrR,hrRFBK->kEfFBK", ULi, URi);
-    X = C("hvEfg,xvm->hEfgxm", Ct4, T4b);
-    X = C("hEfgxm,tbmgQ->hEfxtbQ", X, B);
-    const Ten LLi = C("hEfxtbQ,xtbk->hkEfQ", X, Pi.PB);
-    X = C("hwEfG,ywm->hEfGym", Ct3, T2b);
-    X = C("hEfGym,tbMGm->hEfytbM", X, B);
-    const Ten LRi = C("hEfytbM,yEtk->hMfbk", X, Qi.PB);
-    const Ten L2i = C("hkEfQ,hQFBK->kEfFBK", LLi, LRi);
-
-    // alpha (2 x 2 cells): (k1, A_v, O_v | O_v', B_v', kR)
-    X = C("hbErXtfR,XZM->hbErtfRZM", ULAO, T4b);
-    X = C("hbErtfRZM,tbMgS->hErfRZgS", X, B);
-    const Ten Q1 = C("hErfRZgS,kZg->hkEfrRS", X, Pa.PT);
-    X = C("hbElYtfL,YWS->hbElWtfLS", URAO, T2b);
-    X = C("hbElWtfLS,tbMgS->hElWfLMg", X, B);
-    const Ten Q2 = C("hElWfLMg,kWE->hlLMfgk", X, Qa.PT);
-    const Ten U2a = C("hkEfrRS,hrRSFGK->kEfFGK", Q1, Q2);
-    X = C("hvEfg,YvM->hEfgYM", Ct4, T4b);
-    X = C("hEfgYM,tbMgS->hEfYtbS", X, B);
-    X = C("hEfYtbS,XYL->hEftbSXL", X, T4i);
-    X = C("hEftbSXL,tsoLfR->hEbSXsoR", X, O);
-    X = C("hEbSXsoR,xXl->hEbSsoRxl", X, T4k);
-    X = C("hEbSsoRxl,splEr->hbSoRxpr", X, A);
-    const Ten Q4 = C("hbSoRxpr,xbk->hkporRS", X, Pa.PB);
-    X = C("hwEfg,WwS->hEfgWS", Ct3, T2b);
-    X = C("hEfgWS,tbMgS->hEfWtbM", X, B);
-    X = C("hEfWtbM,ZWR->hEftbMZR", X, T2i);
-    X = C("hEftbMZR,tsoLfR->hEbMZsoL", X, O);
-    X = C("hEbMZsoL,yZr->hEbMsoLyr", X, T2k);
-    X = C("hEbMsoLyr,splEr->hbMoLypl", X, A);
-    const Ten Q3 = C("hbMoLypl,ypk->hlLMobk", X, Qa.PB);
-    const Ten L2a = C("hkporRS,hrRSOBK->kpoOBK", Q4, Q3);
-
+    // stage 2: the two-column patches of the three cuts (stage-1 projectors applied), each
+    // followed by its SVD pipeline, one stream per cut
     Engine::PPair pr2[3];
     {
-        const Ten* U[3] = {&U2a, &U2k, &U2i};
-        const Ten* L[3] = {&L2a, &L2k, &L2i};
         std::vector<Plan> sub(3);
-        for (int i = 0; i < 3; ++i) {
-            e.cur_stream = i + 1;
-            pr2[i] = e.projector(net, sub[i], *U[i], *L[i], "abcdef", "abc");
+        // alpha (2 x 2 cells): (k1, A_v, O_v | O_v', B_v', kR)
+        {
+            Plan& S = sub[0];
+            e.cur_stream = 1;
+            auto D = [&](const char* spec, const Ten& X1, const Ten& Y1) { return e.ctr(net, S, spec, X1, Y1); };
+            const Ten Q1 = D("hErfRZgS,kZg->hkEfrRS", Q1pre, Pa.PT);
+            const Ten Q2 = D("hElWfLMg,kWE->hlLMfgk", Q2pre, Qa.PT);
+            const Ten U2a = D("hkEfrRS,hrRSFGK->kEfFGK", Q1, Q2);
+            const Ten Q4 = D("hbSoRxpr,xbk->hkporRS", Q4pre, Pa.PB);
+            const Ten Q3 = D("hbMoLypl,ypk->hlLMobk", Q3pre, Qa.PB);
+            const Ten L2a = D("hkporRS,hrRSOBK->kpoOBK", Q4, Q3);
+            pr2[0] = e.projector(net, S, U2a, L2a, "abcdef", "abc");
+        }
+        // kappa (1 x 2 cells): (k2, A.d, O.u | O.u', B.u', kR)
+        {
+            Plan& S = sub[1];
+            e.cur_stream = 2;
+            auto D = [&](const char* spec, const Ten& X1, const Ten& Y1) { return e.ctr(net, S, spec, X1, Y1); };
+            const Ten ULk = D("hobxsEr,kxsb->hkEor", ULA, Pk.PT);
+            const Ten URk = D("hobysEl,kyEs->hlobk", URA, Qk.PT);
+            const Ten U2k = D("hkEor,hrOBK->kEoOBK", ULk, URk);
+            const Ten LLk = D("hEbQxsoR,xsbk->hkEoRQ", LLkpre, Pk.PB);
+            const Ten LRk = D("hEbMysoL,yEsk->hLMobk", LRkpre, Qk.PB);
+            const Ten L2k = D("hkEoRQ,hRQOBK->kEoOBK", LLk, LRk);
+            pr2[1] = e.projector(net, S, U2k, L2k, "abcdef", "abc");
+        }
+        // iota (1 x 2 cells): (k3, A.d, O.d | O.d', B.u', kR)
+        {
+            Plan& S = sub[2];
+            e.cur_stream = 3;
+            auto D = [&](const char* spec, const Ten& X1, const Ten& Y1) { return e.ctr(net, S, spec, X1, Y1); };
+            const Ten ULi = D("hbErXtfR,kXtb->hkEfrR", ULAO, Pi.PT);
+            const Ten URi = D("hbElYtfL,kYEt->hlLfbk", URAO, Qi.PT);
+            const Ten U2i = D("hkEfrR,hrRFBK->kEfFBK", ULi, URi);
+            const Ten LLi = D("hEfxtbQ,xtbk->hkEfQ", LLipre, Pi.PB);
+            const Ten LRi = D("hEfytbM,yEtk->hMfbk", LRipre, Qi.PB);
+            const Ten L2i = D("hkEfQ,hQFBK->kEfFBK", LLi, LRi);
+            pr2[2] = e.projector(net, S, U2i, L2i, "abcdef", "abc");
         }
         e.cur_stream = 0;
         e.parallel(P, std::move(sub));

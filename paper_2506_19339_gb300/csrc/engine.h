@@ -37,7 +37,7 @@ Ten permute(const Ten& t, const std::vector<int>& perm);           // out axis k
 
 class Engine;
 
-constexpr int kStreams = 7;  // stream 0 = the caller's stream; 1..6 run independent projectors
+constexpr int kStreams = 10;  // stream 0 = the caller's stream; 1..9 run independent sub-plans
 struct EvRec {
     int kind;
     long long flops;
