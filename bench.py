@@ -27,7 +27,7 @@ METRIC = "split-CTMRG f+∇f evals/s at D=4 χ=64, mixed vs FP64 at |Δf|≤1e-8
 WORKLOAD = dict(D=4, chi=64, T=4.5, seed=2)   # the configuration the metric is quoted on
 NOMINAL_FP64_TFLOPS = 1.25                     # GB300 FP64 (vector and tensor), nominal
 NOMINAL_BF16_TFLOPS = 2250.0
-PRECISIONS = {'fp64': 0, 'tf32': 1, 'tf32x3': 2, 'bf16': 3, 'bf16x3': 4}
+PRECISIONS = {'fp64': 0, 'tf32': 1, 'tf32x3': 2, 'bf16': 3, 'bf16x3': 4, 'f64emu': 5}
 SVD_MODES = {'qr': 0, 'polar': 1, 'partial': 2, 'partial-random': 3}
 SVD_NAMES = {'qr': 'cuSOLVER gesvd', 'polar': 'cuSOLVER gesvdp',
              'partial': 'partial SVD: gesvd cold solve, then warm-started subspace iteration + '

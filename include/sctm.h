@@ -50,7 +50,9 @@ enum {
     SCTM_PREC_TF32 = 1,    /* contractions on tensor cores, TF32 inputs, FP32 accumulation     */
     SCTM_PREC_TF32X3 = 2,  /* TF32 with hi/lo split products (hi*hi + hi*lo + lo*hi)            */
     SCTM_PREC_BF16 = 3,    /* contractions on tensor cores, BF16 inputs, FP32 accumulation     */
-    SCTM_PREC_BF16X3 = 4   /* BF16 with hi/lo split products                                   */
+    SCTM_PREC_BF16X3 = 4,  /* BF16 with hi/lo split products                                   */
+    SCTM_PREC_F64EMU = 5   /* FP64-accurate: eight 7-bit BF16 digits per operand element, exact */
+                           /* FP32 level sums on the tensor cores, FP64 recombination           */
 };
 
 enum { SCTM_GRAD_ENV = 0, SCTM_GRAD_ADJOINT = 1 };

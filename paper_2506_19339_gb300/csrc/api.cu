@@ -138,7 +138,7 @@ sctm_status sctm_create(const double* peps, const double* pepo, int chi, const s
     sctm_opts opts;
     if (o) opts = *o; else sctm_default_opts(&opts);
     if (chi < 1 || chi > 4096 || opts.D < 1 || opts.p < 1 || opts.d < 1 || opts.batch != 1 ||
-        opts.precision < SCTM_PREC_FP64 || opts.precision > SCTM_PREC_BF16X3 ||
+        opts.precision < SCTM_PREC_FP64 || opts.precision > SCTM_PREC_F64EMU ||
         opts.grad_mode != SCTM_GRAD_ENV ||
         !(opts.svd_cutoff >= 0.0) || opts.D > 64 || opts.d > 64 || opts.p > 64 ||
         opts.svd_mode < SCTM_SVD_QR || opts.svd_mode > SCTM_SVD_PARTIAL_RANDOM)
@@ -257,7 +257,7 @@ sctm_status sctm_iterate(sctm_ctx* ctx, int max_it, double tol, int* it_done, do
                 if (err[0]) throw Error(SCTM_ETIMEOUT, "tensor-core contraction wait timed out");
                 if (err[1]) throw Error(SCTM_ENUMERIC, "non-finite projector matrix");
                 if (!std::isfinite(dS)) throw Error(SCTM_ENUMERIC, "non-finite spectrum change");
-                if (net.precision != SCTM_PREC_FP64) {
+                if (net.precision != SCTM_PREC_FP64 && net.precision != SCTM_PREC_F64EMU) {
                     if (dS < 0.5 * best) {
                         best = dS;
                         stall = 0;
@@ -272,7 +272,8 @@ sctm_status sctm_iterate(sctm_ctx* ctx, int max_it, double tol, int* it_done, do
             }
             its[n] = std::min(it, max_it);
             // a spectrum change measured on a mixed-form iteration never counts as converged
-            dss[n] = net.precision == SCTM_PREC_FP64 ? dS : std::max(dS, tol > 0.0 ? 2.0 * tol : dS);
+            const bool fp64_like = net.precision == SCTM_PREC_FP64 || net.precision == SCTM_PREC_F64EMU;
+            dss[n] = fp64_like ? dS : std::max(dS, tol > 0.0 ? 2.0 * tol : dS);
         } catch (...) {
             errs[n] = std::current_exception();
         }
@@ -532,7 +533,7 @@ static bool on_device(const void* p) {
 sctm_status sctm_gemm(const double* X, const double* Y, double* O, int M, int N, int K,
                       int precision, void* cuda_stream) {
     if (!X || !Y || !O || M < 1 || N < 1 || K < 1) return SCTM_EINVAL;
-    if (precision < SCTM_PREC_FP64 || precision > SCTM_PREC_BF16X3) return SCTM_EINVAL;
+    if (precision < SCTM_PREC_FP64 || precision > SCTM_PREC_F64EMU) return SCTM_EINVAL;
     if ((long long)M * K >= (1LL << 31) || (long long)K * N >= (1LL << 31) ||
         (long long)M * N >= (1LL << 31))
         return SCTM_EINVAL;
@@ -594,15 +595,22 @@ sctm_status sctm_gemm(const double* X, const double* Y, double* O, int M, int N,
         else
             bufs.push_back(p), a.scale_ws = (double*)p;
         void* q = nullptr;
-        if (st == SCTM_OK && cudaMalloc(&q, tc_pack_bytes_x(a)) != cudaSuccess)
+        const size_t bx = std::max(tc_pack_bytes_x(a), emu_pack_bytes_x(a));
+        const size_t by = std::max(tc_pack_bytes_y(a), emu_pack_bytes_y(a));
+        if (st == SCTM_OK && cudaMalloc(&q, bx) != cudaSuccess)
             st = SCTM_ENOMEM;
         else if (st == SCTM_OK)
             bufs.push_back(q), a.pack_x = q;
         q = nullptr;
-        if (st == SCTM_OK && cudaMalloc(&q, tc_pack_bytes_y(a)) != cudaSuccess)
+        if (st == SCTM_OK && cudaMalloc(&q, by) != cudaSuccess)
             st = SCTM_ENOMEM;
         else if (st == SCTM_OK)
             bufs.push_back(q), a.pack_y = q;
+        q = nullptr;
+        if (st == SCTM_OK && cudaMalloc(&q, emu_exp_ints(a) * sizeof(int)) != cudaSuccess)
+            st = SCTM_ENOMEM;
+        else if (st == SCTM_OK)
+            bufs.push_back(q), a.rexp = (int*)q;
     }
     if (st == SCTM_OK && splits > 1) {
         void* p = nullptr;

@@ -481,6 +481,10 @@ static void launch_tc(const CtrLaunch& a, cudaStream_t s) {
 }
 
 void launch_ctr_tc(const CtrLaunch& a, cudaStream_t s) {
+    if (a.precision == SCTM_PREC_F64EMU) {
+        launch_ctr_emu(a, s);
+        return;
+    }
     ctr_maxabs_kernel<<<2 * kScaleBlocks, 256, 0, s>>>(a);
     switch (a.precision) {
         case SCTM_PREC_TF32: launch_tc<false, false>(a, s); break;

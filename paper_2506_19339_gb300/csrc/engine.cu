@@ -1056,7 +1056,7 @@ double Engine::cutoff_floor(int prec) {
         case SCTM_PREC_BF16: return 1e-2;    // 8-bit significand
         case SCTM_PREC_TF32X3: return 1e-4;  // hi/lo, FP32 accumulation
         case SCTM_PREC_BF16X3: return 1e-3;
-        default: return 0.0;
+        default: return 0.0;  // FP64 and its emulation
     }
 }
 
@@ -1082,15 +1082,17 @@ void Engine::finalize(Network& net) {
         if (net.splitk_need[k] > 0) net.splitk_ws[k] = dalloc((long long)net.splitk_need[k]);
     for (CtrStep* s : net.ctr_steps)
         if (s->partial_need > 0) s->a.partial = net.splitk_ws[s->sid];
-    size_t px[kStreams] = {0}, py[kStreams] = {0};
+    size_t px[kStreams] = {0}, py[kStreams] = {0}, pe[kStreams] = {0};
     for (CtrStep* s : net.ctr_steps) {
         if (!s->mixed_ok) continue;
-        px[s->sid] = std::max(px[s->sid], tc_pack_bytes_x(s->a));
-        py[s->sid] = std::max(py[s->sid], tc_pack_bytes_y(s->a));
+        px[s->sid] = std::max({px[s->sid], tc_pack_bytes_x(s->a), emu_pack_bytes_x(s->a)});
+        py[s->sid] = std::max({py[s->sid], tc_pack_bytes_y(s->a), emu_pack_bytes_y(s->a)});
+        pe[s->sid] = std::max(pe[s->sid], emu_exp_ints(s->a));
     }
     for (int k = 0; k < kStreams; ++k) {
         if (px[k] > 0) net.pack_x[k] = dalloc((long long)((px[k] + 7) / 8));
         if (py[k] > 0) net.pack_y[k] = dalloc((long long)((py[k] + 7) / 8));
+        if (pe[k] > 0) net.rexp[k] = (int*)dalloc((long long)((pe[k] + 1) / 2));
     }
     for (CtrStep* s : net.ctr_steps) {
         if (!s->mixed_ok) continue;
@@ -1098,6 +1100,7 @@ void Engine::finalize(Network& net) {
         s->a.scale_ws = net.scale_ws[s->sid];
         s->a.pack_x = net.pack_x[s->sid];
         s->a.pack_y = net.pack_y[s->sid];
+        s->a.rexp = net.rexp[s->sid];
     }
     void* p = nullptr;
     if (!dry) {

@@ -72,6 +72,7 @@ struct Network {
     double* scale_ws[kStreams] = {nullptr};   // operand max-abs pass of the tensor-core form
     void* pack_x[kStreams] = {nullptr};       // packed tensor-core operands (per stream)
     void* pack_y[kStreams] = {nullptr};
+    int* rexp[kStreams] = {nullptr};          // row / column exponents of the FP64 emulation
     size_t splitk_need[kStreams] = {0};
     void* svd_dwork[kStreams] = {nullptr};
     size_t svd_dbytes = 0;

@@ -44,10 +44,16 @@ struct CtrLaunch {
     double* scale_ws = nullptr;        // 2 * kScaleBlocks doubles: per-block max |X|, max |Y|
     void* pack_x = nullptr;            // tensor-core operands, converted once per launch into
     void* pack_y = nullptr;            //   hi (then lo) tiles in shared-memory image order
+    int* rexp = nullptr;               // nb * (M + N) row / column exponents (SCTM_PREC_F64EMU)
 };
 // bytes of the packed tensor-core operands (hi and lo, TF32: the largest form)
 size_t tc_pack_bytes_x(const CtrLaunch& a);
 size_t tc_pack_bytes_y(const CtrLaunch& a);
+// FP64 emulation on the tensor cores (ctr_emu.cu)
+void launch_ctr_emu(const CtrLaunch& a, cudaStream_t s);
+size_t emu_pack_bytes_x(const CtrLaunch& a);
+size_t emu_pack_bytes_y(const CtrLaunch& a);
+size_t emu_exp_ints(const CtrLaunch& a);
 constexpr int kScaleBlocks = 152;       // blocks of the operand max-abs pass (one per SM)
 
 void launch_ctr(const CtrLaunch& a, cudaStream_t s);

@@ -16,7 +16,7 @@ SCTM_OK, SCTM_EINVAL, SCTM_ECUDA, SCTM_ECUSOLVER, SCTM_ENOMEM, SCTM_ENOCONV, SCT
     SCTM_ETIMEOUT = range(8)
 STATUS_NAMES = ['SCTM_OK', 'SCTM_EINVAL', 'SCTM_ECUDA', 'SCTM_ECUSOLVER', 'SCTM_ENOMEM',
                 'SCTM_ENOCONV', 'SCTM_ENUMERIC', 'SCTM_ETIMEOUT']
-SCTM_PREC_FP64, SCTM_PREC_TF32, SCTM_PREC_TF32X3, SCTM_PREC_BF16, SCTM_PREC_BF16X3 = range(5)
+SCTM_PREC_FP64, SCTM_PREC_TF32, SCTM_PREC_TF32X3, SCTM_PREC_BF16, SCTM_PREC_BF16X3, SCTM_PREC_F64EMU = range(6)
 SCTM_GRAD_ENV, SCTM_GRAD_ADJOINT = 0, 1
 SCTM_SVD_QR, SCTM_SVD_POLAR, SCTM_SVD_PARTIAL, SCTM_SVD_PARTIAL_RANDOM = 0, 1, 2, 3
 SCTM_NET_NUM, SCTM_NET_DEN = 0, 1

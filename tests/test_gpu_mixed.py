@@ -21,6 +21,8 @@ FORMS = {
     sctm.SCTM_PREC_TF32X3: (2e-5, 2e-6),
     sctm.SCTM_PREC_BF16: (1.6e-2, 8e-3),
     sctm.SCTM_PREC_BF16X3: (1e-4, 3e-5),
+    # eight 7-bit digits per element: 56 bits against each row's (column's) maximum
+    sctm.SCTM_PREC_F64EMU: (1e-13, 1e-13),
 }
 
 
@@ -72,6 +74,7 @@ def test_split_products_are_used():
     assert err[sctm.SCTM_PREC_BF16X3] < err[sctm.SCTM_PREC_BF16] / 50
     assert err[sctm.SCTM_PREC_TF32] < err[sctm.SCTM_PREC_BF16]
     assert err[sctm.SCTM_PREC_FP64] < 1e-14
+    assert err[sctm.SCTM_PREC_F64EMU] < 1e-14
 
 
 def test_gemm_rejects_bad_arguments():
@@ -158,3 +161,22 @@ def test_mixed_full_size_moves():
             assert np.all(np.isfinite(out[:4]))
     finally:
         r.close()
+
+
+@pytest.mark.parametrize('D,chi,T,seed,eps,iters', [
+    (2, 16, 4.6, 7, 0.3, 40),
+    (3, 10, 4.4, 4, 0.1, 30),
+])
+def test_f64emu_parity_with_oracle(D, chi, T, seed, eps, iters):
+    """The FP64 emulation on the tensor cores in the move contractions: the same tolerances as the
+    FP64 path (f 1e-10, g 1e-8 against the oracle) on the contractive inputs."""
+    A = inputs.perturbed_product_peps(D, seed, eps=eps)
+    r = _ctx(A, T, chi, sctm.SCTM_PREC_F64EMU)
+    try:
+        r.iterate(iters, 0.0)
+        f, g = r.free_energy(), r.grad()
+    finally:
+        r.close()
+    ref = sc.evaluate(A, ising.ising_pepo(1 / T), ising.identity_pepo(), T, chi, iters)
+    assert abs(f - ref['f']) <= 1e-10 * abs(ref['f']), (f, ref['f'])
+    assert np.linalg.norm(g - ref['g']) <= 1e-8 * np.linalg.norm(ref['g'])
