@@ -69,9 +69,9 @@ struct CtrStep : Step {
         const int e0 = e.profile ? e.record(sid) : -1;
         launch_ctr(a, e.lane().streams[sid]);
         const bool tc = a.precision != SCTM_PREC_FP64;
-        const int splits = tc ? a.tc_splits : a.splits;
+        const int splits = tc ? a.tc_splits : (ctr_is_skinny(a) ? 1 : a.splits);
         e.kernel_launches += (splits > 1 ? 2 : 1) + (tc ? 2 : 0);
-        if (e.profile) e.record_done(sid, KIND_CTR, flops, e0);
+        if (e.profile) e.record_done(sid, KIND_CTR, flops, e0, &a);
     }
 };
 
@@ -232,9 +232,17 @@ int Engine::record(int sid) {
     return idx;
 }
 
-void Engine::record_done(int sid, int kind, long long flops, int e0) {
+void Engine::record_done(int sid, int kind, long long flops, int e0, const CtrLaunch* a) {
     const int e1 = record(sid);
-    lane().ev_recs[sid].push_back({kind, flops, e0, e1});
+    EvRec r{kind, flops, e0, e1};
+    if (a) {
+        r.m = a->M;
+        r.n = a->N;
+        r.k = a->K;
+        r.nb = a->nb;
+        r.prec = a->precision;
+    }
+    lane().ev_recs[sid].push_back(r);
 }
 
 void Engine::harvest() {
@@ -255,7 +263,8 @@ void Engine::harvest() {
                     cudaEventSynchronize(ref);
                     cudaEventElapsedTime(&t0, ref, L.ev_pool[sid][r.e0]);
                     cudaEventElapsedTime(&t1, ref, L.ev_pool[sid][r.e1]);
-                    fprintf(tf, "%d %d %d %lld %.4f %.4f\n", l, sid, r.kind, r.flops, t0, t1);
+                    fprintf(tf, "%d %d %d %lld %.4f %.4f %d %d %d %d %d\n", l, sid, r.kind, r.flops,
+                            t0, t1, r.m, r.n, r.k, r.nb, r.prec);
                 }
                 if (r.kind == KIND_CTR) {
                     ctr_ms += ms;
@@ -1071,8 +1080,17 @@ double Engine::switch_level(int prec) {
     }
 }
 
+// The FP64 emulation pays off for long contractions only: measured per shape at D=4, chi=64,
+// it took 0.3-0.6x the FP64 kernel's time for K >= 512 (M >= 128, N >= 64) and 1.2-2.5x for
+// K <= 64, where the digit split and the per-block read-back outweigh the tensor-core speed.
+static bool emu_worth(const CtrLaunch& a) { return a.K >= 512 && a.M >= 128 && a.N >= 64; }
+
 void Engine::set_precision(Network& net, int prec) {
-    for (CtrStep* s : net.ctr_steps) s->a.precision = s->mixed_ok ? prec : SCTM_PREC_FP64;
+    for (CtrStep* s : net.ctr_steps) {
+        int p = s->mixed_ok ? prec : SCTM_PREC_FP64;
+        if (p == SCTM_PREC_F64EMU && !emu_worth(s->a)) p = SCTM_PREC_FP64;
+        s->a.precision = p;
+    }
     net.precision = prec;
     net.cutoff_now = std::max(cutoff, cutoff_floor(prec));
 }

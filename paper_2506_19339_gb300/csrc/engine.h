@@ -42,6 +42,7 @@ struct EvRec {
     int kind;
     long long flops;
     int e0, e1;
+    int m = 0, n = 0, k = 0, nb = 0, prec = 0;  // contraction shape (timeline diagnostic)
 };
 
 struct Step {
@@ -137,7 +138,7 @@ public:
     long long ctr_launches = 0, ctr_flops = 0, svd_calls = 0;
     std::atomic<long long> kernel_launches{0};  // own kernels only (cuSOLVER's are not counted)
     int record(int sid);                                       // event index in pool sid
-    void record_done(int sid, int kind, long long flops, int e0);
+    void record_done(int sid, int kind, long long flops, int e0, const CtrLaunch* a = nullptr);
     void harvest();
 
     size_t bytes = 0;                              // device bytes allocated

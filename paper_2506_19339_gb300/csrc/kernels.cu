@@ -140,6 +140,50 @@ __global__ void ctr_splitk_reduce_kernel(const CtrLaunch a) {
     }
 }
 
+// Skinny contractions (N <= 32 outputs per row, K <= 64, one K range): one thread per output row
+// keeps its N accumulators in registers, Y[b] is staged once per block in shared memory.  The
+// 64 x 64 tiles of ctr_f64_kernel would spend most of their FMAs on padding for these shapes
+// (N = 2..32 against a 64-wide tile), which are memory-bound.  The K loop runs in increasing k
+// with one FMA per term, as in ctr_f64_kernel, so the result is bitwise the same.
+constexpr int kSkinnyN = 32, kSkinnyK = 64, kSkinnyRows = 256;
+__global__ void __launch_bounds__(kSkinnyRows) ctr_skinny_kernel(const CtrLaunch a) {
+    __shared__ double ys[kSkinnyK * kSkinnyN];
+    const int b = blockIdx.y;
+    const long long ybo = a.yb ? a.yb[b] : 0;
+    for (int e = threadIdx.x; e < a.K * a.N; e += blockDim.x) {
+        const int k = e / a.N, n = e - k * a.N;
+        ys[k * kSkinnyN + n] = a.Y[ybo + a.yk[k] + a.yn[n]];
+    }
+    __syncthreads();
+    const long long xbo = a.xb ? a.xb[b] : 0;
+    const long long obo = a.ob ? a.ob[b] : 0;
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < a.M; m += gridDim.x * blockDim.x) {
+        double acc[kSkinnyN];
+#pragma unroll
+        for (int n = 0; n < kSkinnyN; ++n) acc[n] = 0.0;
+        const long long xr = xbo + a.xm[m];
+        for (int k = 0; k < a.K; ++k) {
+            const double x = a.X[xr + a.xk[k]];
+#pragma unroll
+            for (int n = 0; n < kSkinnyN; ++n)
+                if (n < a.N) acc[n] = fma(x, ys[k * kSkinnyN + n], acc[n]);
+        }
+        const double rs = a.rowscale ? a.rowscale[m] : 1.0;
+        const long long om_ = obo + a.om[m];
+#pragma unroll
+        for (int n = 0; n < kSkinnyN; ++n) {
+            if (n >= a.N) continue;
+            double v = acc[n] * rs;
+            if (a.colscale) v *= a.colscale[n];
+            a.O[om_ + a.on[n]] = v;
+        }
+    }
+}
+
+bool ctr_is_skinny(const CtrLaunch& a) {
+    return a.N <= kSkinnyN && a.K <= kSkinnyK && a.nb <= 65535;
+}
+
 void launch_ctr(const CtrLaunch& a0, cudaStream_t s) {
     if (a0.precision != SCTM_PREC_FP64) {
         CtrLaunch a = a0;
@@ -154,6 +198,12 @@ void launch_ctr(const CtrLaunch& a0, cudaStream_t s) {
         return;
     }
     const CtrLaunch& a = a0;
+    if (ctr_is_skinny(a)) {
+        const int bx = (int)std::min<long long>((a.M + kSkinnyRows - 1) / kSkinnyRows, 65535);
+        dim3 grid(std::max(bx, 1), a.nb);
+        ctr_skinny_kernel<<<grid, kSkinnyRows, 0, s>>>(a);
+        return;
+    }
     const int bm = a.tile, bn = a.tile;
     dim3 grid((a.N + bn - 1) / bn, (a.M + bm - 1) / bm, a.nb * a.splits);
     if (a.tile == 32)

@@ -57,6 +57,8 @@ size_t emu_exp_ints(const CtrLaunch& a);
 constexpr int kScaleBlocks = 152;       // blocks of the operand max-abs pass (one per SM)
 
 void launch_ctr(const CtrLaunch& a, cudaStream_t s);
+// shapes that launch_ctr (FP64) runs on the one-row-per-thread kernel
+bool ctr_is_skinny(const CtrLaunch& a);
 // tensor-core variant (a.precision = SCTM_PREC_TF32 / TF32X3 / BF16 / BF16X3), 128 x 64 tiles
 void launch_ctr_tc(const CtrLaunch& a, cudaStream_t s);
 
