@@ -145,14 +145,14 @@ def test_mixed_moves_against_fp64(prec, tol):
         rf.close()
 
 
-def test_mixed_full_size_moves():
-    """D=4, chi=64 in TF32 hi/lo: the projector matrices (~1e-35 for this normalised N(0,1)
-    PEPS) are below the FP32 range without the operands' power-of-two scaling; two moves of
-    each network complete with finite local values."""
+@pytest.mark.parametrize('prec', [sctm.SCTM_PREC_TF32X3, sctm.SCTM_PREC_F64EMU])
+def test_mixed_full_size_moves(prec):
+    """D=4, chi=64: the projector matrices (~1e-35 for this normalised N(0,1) PEPS) are below
+    the FP32 range without the operands' power-of-two (row) scaling; two moves of each network
+    complete with finite local values."""
     A = inputs.random_peps(4, 2)
     st, O = sctm.sctm_ising_pepo(4.5)
-    r = sctm.SplitCTMRG(A, O, 64, 4.5, precision=sctm.SCTM_PREC_TF32X3,
-                        svd_mode=sctm.SCTM_SVD_PARTIAL)
+    r = sctm.SplitCTMRG(A, O, 64, 4.5, precision=prec, svd_mode=sctm.SCTM_SVD_PARTIAL)
     try:
         for net in (sctm.SCTM_NET_NUM, sctm.SCTM_NET_DEN):
             for d in (sctm.SCTM_MOVE_LEFT, sctm.SCTM_MOVE_RIGHT):
