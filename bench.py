@@ -278,6 +278,9 @@ def run_ours(args):
     wall = time.perf_counter() - t_wall
     clk = clocks.stop()
     sctm.sctm_set_profiling(ctx, False)
+    kern = {name: sctm.sctm_profile_kernel(ctx, k)[1] for name, k in
+            (('ctr_f64_kernel', sctm.SCTM_KERNEL_F64), ('ctr_skinny_kernel', sctm.SCTM_KERNEL_SKINNY),
+             ('ctr_tc_kernel', sctm.SCTM_KERNEL_TC), ('emu_ctr_kernel', sctm.SCTM_KERNEL_F64EMU))}
     st, prof = sctm.sctm_profile(ctx, reset=True)
     ms = float(np.sum(step_ms))
 
@@ -333,7 +336,20 @@ def run_ours(args):
     else:
         fp64_peak = 1700.0 * NOMINAL_FP64_TFLOPS / NOMINAL_BF16_TFLOPS
         peak_note = 'fallback bf16 sustained x nominal FP64/BF16 ratio'
-    achieved = (prof['ctr_flops'] / (prof['ctr_ms'] * 1e-3) / 1e12) if prof['ctr_ms'] > 0 else None
+    kf = kern['ctr_f64_kernel']
+    achieved = (kf['flops'] / (kf['ms'] * 1e-3) / 1e12) if kf['ms'] > 0 else None
+    hbm = peaks.get('hbm_gbs', 6800.0)
+    kernels = {}
+    for name, kv in kern.items():
+        if kv['launches'] == 0:
+            continue
+        sec = kv['ms'] * 1e-3
+        kernels[name] = {'launches_per_step': kv['launches'] / args.steps,
+                         'ms_per_step': kv['ms'] / args.steps,
+                         'tflops': kv['flops'] / sec / 1e12 if sec > 0 else None,
+                         'min_gbs': kv['bytes'] / sec / 1e9 if sec > 0 else None}
+    if 'ctr_skinny_kernel' in kernels and kernels['ctr_skinny_kernel']['min_gbs']:
+        kernels['ctr_skinny_kernel']['frac_of_hbm'] = kernels['ctr_skinny_kernel']['min_gbs'] / hbm
     n_steps = args.steps * world
     value = n_steps / (ms * 1e-3)
     total_its = int(np.sum(its))
@@ -355,6 +371,7 @@ def run_ours(args):
                      'peak': fp64_peak, 'unit': 'TFLOP/s',
                      'frac': (achieved / fp64_peak) if achieved else None, 'traffic': None,
                      'peak_note': peak_note, 'dgemm_torch_tflops': dgemm_tflops,
+                     'kernels': kernels,
                      'ctr_ms_per_step': prof['ctr_ms'] / args.steps,
                      'svd_ms_per_step': prof['svd_ms'] / args.steps,
                      'ctr_launches_per_step': prof['ctr_launches'] / args.steps,

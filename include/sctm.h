@@ -215,6 +215,22 @@ sctm_status sctm_profile(sctm_ctx* ctx, double* ctr_ms, long long* ctr_launches,
                          long long* ctr_flops, double* svd_ms, long long* svd_calls,
                          long long* kernel_launches, int reset);
 
+/* Contraction kernels, for sctm_profile_kernel. */
+enum {
+    SCTM_KERNEL_F64 = 0,     /* tiled FP64 kernel (64 x 64 or 32 x 32 tiles, split K)              */
+    SCTM_KERNEL_SKINNY = 1,  /* FP64, one output row per thread (N <= 32, K <= 64)                 */
+    SCTM_KERNEL_TC = 2,      /* tensor cores, TF32 / BF16 (hi/lo) forms                             */
+    SCTM_KERNEL_F64EMU = 3   /* tensor cores, FP64 emulation                                        */
+};
+
+/* sctm_profile_kernel -- the profiling counters of one contraction kernel (SCTM_KERNEL_*) since
+ * creation or the last reset of sctm_profile: summed CUDA-event time around its launches,
+ * launches, algorithmic FLOPs (2 M N K per contraction) and minimum bytes (8 (MK + KN + MN) per
+ * contraction: each operand read once, the output written once).  Any pointer may be NULL.
+ * Errors: EINVAL (NULL ctx, bad kernel). */
+sctm_status sctm_profile_kernel(sctm_ctx* ctx, int kernel, double* ms, long long* launches,
+                                long long* flops, long long* bytes);
+
 /* sctm_gemm -- O = X Y for row-major device matrices X (M x K), Y (K x N), O (M x N), run by the
  * library's contraction kernels in the arithmetic `precision` (SCTM_PREC_*): the FP64 kernel, or
  * the tensor-core kernel with TF32 / BF16 operands (optionally hi/lo split) and FP32

@@ -510,6 +510,10 @@ sctm_status sctm_profile(sctm_ctx* ctx, double* ctr_ms, long long* ctr_launches,
     if (reset) {
         e.ctr_ms = e.svd_ms = 0;
         e.ctr_launches = e.ctr_flops = e.svd_calls = 0;
+        for (int i = 0; i < 4; ++i) {
+            e.kern_ms[i] = 0;
+            e.kern_launches[i] = e.kern_flops[i] = e.kern_bytes[i] = 0;
+        }
         e.kernel_launches = 0;
     }
     return SCTM_OK;
@@ -521,6 +525,20 @@ sctm_status sctm_profile(sctm_ctx* ctx, double* ctr_ms, long long* ctr_launches,
 // ---------------------------------------------------------------------------------------------
 // sctm_gemm: one plain row-major contraction through the library's kernels, in any form
 // ---------------------------------------------------------------------------------------------
+sctm_status sctm_profile_kernel(sctm_ctx* ctx, int kernel, double* ms, long long* launches,
+                                long long* flops, long long* bytes) {
+    API_BEGIN(ctx)
+    if (kernel < SCTM_KERNEL_F64 || kernel > SCTM_KERNEL_F64EMU) throw Error(SCTM_EINVAL, "bad kernel");
+    Engine& e = *ctx->eng;
+    e.harvest();
+    if (ms) *ms = e.kern_ms[kernel];
+    if (launches) *launches = e.kern_launches[kernel];
+    if (flops) *flops = e.kern_flops[kernel];
+    if (bytes) *bytes = e.kern_bytes[kernel];
+    return SCTM_OK;
+    API_END(ctx)
+}
+
 static bool on_device(const void* p) {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {

@@ -241,6 +241,10 @@ void Engine::record_done(int sid, int kind, long long flops, int e0, const CtrLa
         r.k = a->K;
         r.nb = a->nb;
         r.prec = a->precision;
+        r.variant = a->precision == SCTM_PREC_F64EMU ? SCTM_KERNEL_F64EMU
+                    : a->precision != SCTM_PREC_FP64 ? SCTM_KERNEL_TC
+                    : ctr_is_skinny(*a)               ? SCTM_KERNEL_SKINNY
+                                                      : SCTM_KERNEL_F64;
     }
     lane().ev_recs[sid].push_back(r);
 }
@@ -270,6 +274,11 @@ void Engine::harvest() {
                     ctr_ms += ms;
                     ctr_launches += 1;
                     ctr_flops += r.flops;
+                    kern_ms[r.variant] += ms;
+                    kern_launches[r.variant] += 1;
+                    kern_flops[r.variant] += r.flops;
+                    kern_bytes[r.variant] +=
+                        8LL * r.nb * ((long long)r.m * r.k + (long long)r.k * r.n + (long long)r.m * r.n);
                 } else {
                     svd_ms += ms;
                     svd_calls += 1;

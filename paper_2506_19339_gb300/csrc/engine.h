@@ -43,6 +43,7 @@ struct EvRec {
     long long flops;
     int e0, e1;
     int m = 0, n = 0, k = 0, nb = 0, prec = 0;  // contraction shape (timeline diagnostic)
+    int variant = 0;                            // SCTM_KERNEL_* of the contraction
 };
 
 struct Step {
@@ -136,6 +137,11 @@ public:
 
     double ctr_ms = 0, svd_ms = 0;
     long long ctr_launches = 0, ctr_flops = 0, svd_calls = 0;
+    // per contraction kernel (SCTM_KERNEL_*): event time, launches, algorithmic FLOPs, and the
+    // bytes the contraction must move at least (operands read once, output written once)
+    double kern_ms[4] = {0, 0, 0, 0};
+    long long kern_launches[4] = {0, 0, 0, 0}, kern_flops[4] = {0, 0, 0, 0},
+              kern_bytes[4] = {0, 0, 0, 0};
     std::atomic<long long> kernel_launches{0};  // own kernels only (cuSOLVER's are not counted)
     int record(int sid);                                       // event index in pool sid
     void record_done(int sid, int kind, long long flops, int e0, const CtrLaunch* a = nullptr);

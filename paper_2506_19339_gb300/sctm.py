@@ -71,6 +71,7 @@ def load():
         'sctm_local_values': (I, [P, I, P]),
         'sctm_gemm_noalloc': (I, [P, P, P, I, I, I, P]),
         'sctm_gemm': (I, [P, P, P, I, I, I, I, P]),
+        'sctm_profile_kernel': (I, [P, I, P, P, P, P]),
         'sctm_iterate_batch': (I, [ctypes.POINTER(P), I, I, D, ctypes.POINTER(I),
                                    ctypes.POINTER(I), ctypes.POINTER(D)]),
         'sctm_device_bytes': (S, [P]),
@@ -217,6 +218,17 @@ def sctm_profile(ctx, reset=False):
                              ctypes.byref(svd_ms), ctypes.byref(sc_), ctypes.byref(kl), int(reset))
     return st, {'ctr_ms': ctr_ms.value, 'ctr_launches': cl.value, 'ctr_flops': cf.value,
                 'svd_ms': svd_ms.value, 'svd_calls': sc_.value, 'kernel_launches': kl.value}
+
+
+SCTM_KERNEL_F64, SCTM_KERNEL_SKINNY, SCTM_KERNEL_TC, SCTM_KERNEL_F64EMU = range(4)
+
+
+def sctm_profile_kernel(ctx, kernel):
+    ms = ctypes.c_double(0)
+    ln, fl, by = (ctypes.c_longlong(0) for _ in range(3))
+    st = load().sctm_profile_kernel(ctx, int(kernel), ctypes.byref(ms), ctypes.byref(ln),
+                                    ctypes.byref(fl), ctypes.byref(by))
+    return st, {'ms': ms.value, 'launches': ln.value, 'flops': fl.value, 'bytes': by.value}
 
 
 def unpack_env(buf, chi, D, d):
