@@ -191,6 +191,18 @@ def run_reference(args):
 # ------------------------------------------------------------------------------------------------
 # our arm
 # ------------------------------------------------------------------------------------------------
+def combine_ranks(ms, e2e_ms, dist, device):
+    """The timed totals of this rank (device-timed ms, end-to-end ms) -> the maximum over all
+    ranks (every rank gets it).  Replicas run independently; the slowest rank sets the time of
+    the whole job, and value = (evaluations of all ranks) / that time."""
+    if not dist:
+        return ms, e2e_ms
+    import torch
+    t = torch.tensor([ms, e2e_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t[0]), float(t[1])
+
+
 def run_ours(args):
     import torch
     from paper_2506_19339_gb300 import build, inputs, sctm
@@ -315,13 +327,9 @@ def run_ours(args):
     sctm.sctm_destroy(ctx)
 
     # max over ranks
+    ms, e2e_total = combine_ranks(ms, float(np.sum(e2e_ms)), dist, dev)
     if dist:
-        t = torch.tensor([ms, float(np.sum(e2e_ms))], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, e2e_total = float(t[0]), float(t[1])
         dist.destroy_process_group()
-    else:
-        e2e_total = float(np.sum(e2e_ms))
     if rank != 0:
         return
 
