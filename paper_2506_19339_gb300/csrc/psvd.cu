@@ -174,9 +174,11 @@ __global__ void __launch_bounds__(kPsvdThreads)
         d[i] = g > 0.0 ? 1.0 / sqrt(g) : 0.0;
     }
     __syncthreads();
+    // G is a Gram matrix, symmetric bit for bit (each entry sums the same products in the same
+    // order), so the row-major R can be read from G's column-major storage element for element
     for (int e = tid; e < k * k; e += nt) {
         const int i = e / k, j = e % k;
-        R[e] = G[i + (long long)j * k] * d[i] * d[j] + ((i == j && d[i] > 0.0) ? shift : 0.0);
+        R[e] = G[e] * d[i] * d[j] + ((i == j && d[i] > 0.0) ? shift : 0.0);
     }
     __syncthreads();
     block_cholesky(R, rinv, k);
