@@ -43,8 +43,12 @@ typedef enum {
     SCTM_ETIMEOUT = 7    /* a bounded device-side wait ran out (tensor-core kernels)             */
 } sctm_status;
 
-/* Arithmetic of the contraction kernels.  SVDs, normalisations and the free-energy ratio are
- * FP64 in every mode. */
+/* Arithmetic of the move contractions (corner and edge absorption, half patches, rho_B rho_T,
+ * renormalisation; Sec. III).  Projector formation, SVDs, normalisations, the spectrum, the local
+ * contractions and the free-energy ratio are FP64 in every mode.  The TF32 / BF16 forms iterate
+ * with a raised pseudo-inverse cutoff and finish in FP64 (sctm_iterate); SCTM_PREC_F64EMU is
+ * FP64-accurate and runs on the tensor cores only for contractions with K >= 512, M >= 128,
+ * N >= 64 (elsewhere the FP64 kernels, which are faster there). */
 enum {
     SCTM_PREC_FP64 = 0,    /* all contractions in FP64                                         */
     SCTM_PREC_TF32 = 1,    /* contractions on tensor cores, TF32 inputs, FP32 accumulation     */
