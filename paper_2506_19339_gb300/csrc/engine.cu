@@ -518,22 +518,8 @@ Engine::PPair Engine::projector(Network& net, Plan& P, const Ten& U, const Ten& 
             s *= rdims[i];
         }
     }
-    const bool partial = svd_mode == SCTM_SVD_PARTIAL || svd_mode == SCTM_SVD_PARTIAL_RANDOM;
+    ctr(net, P, Llab + "," + labels + "->" + rlL + rl, L, U, &M);
     const bool mixed = mixed_build;
-    // non-finite entries would send the QR iteration of gesvd into its iteration limit: zero
-    // them and flag the iteration as failed (SCTM_ENUMERIC)
-    int* nonfinite = dev_err + 1;
-    const long long nn = (long long)n * n;
-    // the explicit M (and its guard) for the full SVDs; the partial SVD's warm steps never form
-    // M (they apply rho_T and rho_B to the thin subspace), so there it is built in the cold plan
-    auto build_M = [&](Plan& Q) {
-        mixed_build = mixed;
-        ctr(net, Q, Llab + "," + labels + "->" + rlL + rl, L, U, &M);
-        mixed_build = false;
-        push(Q, std::make_unique<FnStep>(
-                    [=](cudaStream_t s) { launch_sanitize(M.p, nn, nonfinite, s); }));
-    };
-    if (!partial) build_M(P);
     mixed_build = false;  // the SVD and the projector formation stay FP64
     double* S = dalloc(n);
     double* Us = dalloc((long long)n * n);
@@ -554,6 +540,11 @@ Engine::PPair Engine::projector(Network& net, Plan& P, const Ten& U, const Ten& 
         net.svd_steps.push_back(sv.get());
         return sv;
     };
+    // non-finite entries would send the QR iteration of gesvd into its iteration limit: zero
+    // them and flag the iteration as failed (SCTM_ENUMERIC)
+    int* nonfinite = dev_err + 1;
+    const long long nn = (long long)n * n;
+    push(P, std::make_unique<FnStep>([=](cudaStream_t s) { launch_sanitize(M.p, nn, nonfinite, s); }));
     if (svd_mode != SCTM_SVD_PARTIAL && svd_mode != SCTM_SVD_PARTIAL_RANDOM) {
         push(P, make_svd(Vs));
     } else {
@@ -566,7 +557,6 @@ Engine::PPair Engine::projector(Network& net, Plan& P, const Ten& U, const Ten& 
         double* VT = dalloc((long long)n * n);
         {
             Plan& C = ps->cold;
-            build_M(C);
             push(C, make_svd(VT));
             const int kc = ps->can_warm ? k : chi;
             push(C, std::make_unique<FnStep>(
@@ -596,6 +586,7 @@ Engine::PPair Engine::projector(Network& net, Plan& P, const Ten& U, const Ten& 
             double* Wr = dalloc((long long)k * k);
             const int info_idx = net.n_svd++;
             const Network* np = &net;  // svd_info is allocated after the plans are built
+            const Ten Mv = mat(M.p, n, n);  // M[r', r] at r' + r n
             const Ten Vb = mat(Vs, n, k), Ut = mat(Us, n, k);
             const Ten Gt = mat(G, k, k), Tt = mat(Tm, k, k), Wt = mat(Wr, k, k), Urt = mat(Ur, k, k);
             // shifted Cholesky QR shift for the unit-diagonal scaled Gram matrix
@@ -613,35 +604,11 @@ Engine::PPair Engine::projector(Network& net, Plan& P, const Ten& U, const Ten& 
                     ctr(net, W, "ac,cd->ad", x, Tt, &y);
                 }
             };
-            const Ten Qyt = mat(Qy, n, k), Zbt = mat(Zb, n, k), Qzt = mat(Qz, n, k),
-                      Bt = mat(R1, k, k);
-            // an n x k column-major buffer seen with the remaining legs: [r..., c]
-            auto legs = [&](double* p) {
-                Ten t;
-                t.p = p;
-                t.nd = (int)rl.size() + 1;
-                long long st = 1;
-                for (int i = (int)rl.size() - 1; i >= 0; --i) {
-                    t.dim[i] = rdims[i];
-                    t.st[i] = st;
-                    st *= rdims[i];
-                }
-                t.dim[rl.size()] = k;
-                t.st[rl.size()] = n;
-                return t;
-            };
-            const Ten Vl = legs(Vs), Yl = legs(Yb), Qyl = legs(Qy), Zl = legs(Zb);
-            // Y = M V_prev = rho_B^T (rho_T V_prev) and Z = M^T Q_y = rho_T^T (rho_B Q_y):
-            // M = L^T U is never formed (the paper's partial SVD without explicit rho_B rho_T)
-            mixed_build = mixed;
-            const Ten W1 = ctr(net, W, labels + "," + rl + K + "->" + tl + K, U, Vl);
-            ctr(net, W, Llab + "," + tl + K + "->" + rlL + K, L, W1, &Yl);
-            mixed_build = false;
+            const Ten Ybt = mat(Yb, n, k), Qyt = mat(Qy, n, k), Zbt = mat(Zb, n, k),
+                      Qzt = mat(Qz, n, k), Bt = mat(R1, k, k);
+            ctr(net, W, "ab,bc->ac", Mv, Vb, &Ybt);   // Y = M V_prev
             cholqr3(Yb, Q1, Zb, Qy);                  // Q_y
-            mixed_build = mixed;
-            const Ten W2 = ctr(net, W, Llab + "," + rlL + K + "->" + tl + K, L, Qyl);
-            ctr(net, W, labels + "," + tl + K + "->" + rl + K, U, W2, &Zl);
-            mixed_build = false;
+            ctr(net, W, "ba,bc->ac", Mv, Qyt, &Zbt);  // Z = M^T Q_y
             cholqr3(Zb, Yb, Q1, Qz);                  // Q_z
             ctr(net, W, "ac,ad->cd", Zbt, Qzt, &Bt);  // B = Z^T Q_z = Q_y^T M Q_z
             push(W, std::make_unique<FnStep>([=](cudaStream_t s) {
