@@ -358,6 +358,9 @@ def run_ours(args):
                          'min_gbs': kv['bytes'] / sec / 1e9 if sec > 0 else None}
     if 'ctr_skinny_kernel' in kernels and kernels['ctr_skinny_kernel']['min_gbs']:
         kernels['ctr_skinny_kernel']['frac_of_hbm'] = kernels['ctr_skinny_kernel']['min_gbs'] / hbm
+    # the step is FP64-bound as a whole: FP64 contraction FLOPs of the step over its device time
+    f64_flops = sum(kern[k]['flops'] for k in ('ctr_f64_kernel', 'ctr_skinny_kernel'))
+    gpu_wide = f64_flops / (ms * 1e-3) / 1e12 if ms > 0 else None
     n_steps = args.steps * world
     value = n_steps / (ms * 1e-3)
     total_its = int(np.sum(its))
@@ -380,6 +383,8 @@ def run_ours(args):
                      'frac': (achieved / fp64_peak) if achieved else None, 'traffic': None,
                      'peak_note': peak_note, 'dgemm_torch_tflops': dgemm_tflops,
                      'kernels': kernels,
+                     'step_fp64_contraction_tflops': gpu_wide,
+                     'step_fp64_contraction_frac': (gpu_wide / fp64_peak) if gpu_wide else None,
                      'ctr_ms_per_step': prof['ctr_ms'] / args.steps,
                      'svd_ms_per_step': prof['svd_ms'] / args.steps,
                      'ctr_launches_per_step': prof['ctr_launches'] / args.steps,
