@@ -69,7 +69,8 @@ enum { SCTM_GRAD_ENV = 0, SCTM_GRAD_ADJOINT = 1 };
  *   SCTM_SVD_PARTIAL  the partial SVD of Sec. III (largest chi triplets by an iterative
  *                     solver): the first solve of each projector after a cold start is gesvd,
  *                     every later one a subspace-iteration step warm-started from the previous
- *                     iteration's right singular subspace (chi + max(8, chi/4) columns) with a
+ *                     iteration's right singular subspace (chi + p columns, p = chi/4, at
+ *                     least 8, reduced to keep chi + p <= 112 where chi <= 104) with a
  *                     Rayleigh-Ritz (Jacobi) extraction, about 25 kernel launches instead of
  *                     thousands.  Projectors whose subspace would exceed 112 columns stay on
  *                     gesvd.  The fixed point is the same as SCTM_SVD_QR's; a trajectory from a

@@ -550,7 +550,9 @@ Engine::PPair Engine::projector(Network& net, Plan& P, const Ten& U, const Ten& 
     } else {
         // subspace of chi + oversampling columns (Sec. III's partial SVD); the cold solve is
         // gesvd with its V^T turned into columns, the warm one the subspace iteration step
-        const int over = std::max(8, chi / 4);
+        // oversampling chi/4 (at least 8), reduced down to 8 where that keeps the subspace
+        // within the one-CTA kernels' limit (chi <= kPsvdMaxK - 8)
+        const int over = std::max(8, std::min(chi / 4, kPsvdMaxK - chi));
         const int k = std::min(n, chi + over);
         auto ps = std::make_unique<PartialSvdStep>();
         ps->can_warm = k <= kPsvdMaxK;
