@@ -551,7 +551,8 @@ Engine::PPair Engine::projector(Network& net, Plan& P, const Ten& U, const Ten& 
         // subspace of chi + oversampling columns (Sec. III's partial SVD); the cold solve is
         // gesvd with its V^T turned into columns, the warm one the subspace iteration step
         // oversampling chi/4 (at least 8), reduced down to 8 where that keeps the subspace
-        // within the one-CTA kernels' limit (chi <= kPsvdMaxK - 8)
+        // within the one-CTA kernels' limit (chi <= kPsvdMaxK - 8); above kPsvdSmemK columns
+        // one k x k matrix of the Cholesky-QR and Jacobi kernels lives in global scratch
         const int over = std::max(8, std::min(chi / 4, kPsvdMaxK - chi));
         const int k = std::min(n, chi + over);
         auto ps = std::make_unique<PartialSvdStep>();
@@ -586,6 +587,10 @@ Engine::PPair Engine::projector(Network& net, Plan& P, const Ten& U, const Ten& 
             double* R1 = dalloc((long long)k * k);
             double* Ur = dalloc((long long)k * k);
             double* Wr = dalloc((long long)k * k);
+            const bool big = k > kPsvdSmemK;
+            const int kp2 = k + (k & 1);
+            double* Xg = big ? dalloc((long long)k * k) : nullptr;
+            double* Vg = big ? dalloc((long long)kp2 * (kp2 + 1)) : nullptr;
             const int info_idx = net.n_svd++;
             const Network* np = &net;  // svd_info is allocated after the plans are built
             const Ten Mv = mat(M.p, n, n);  // M[r', r] at r' + r n
@@ -602,7 +607,7 @@ Engine::PPair Engine::projector(Network& net, Plan& P, const Ten& U, const Ten& 
                     ctr(net, W, "ac,ad->cd", x, x, &Gt);
                     const double sh = pass < 2 ? shift : 0.0;
                     push(W, std::make_unique<FnStep>(
-                                [=](cudaStream_t s) { launch_chol_orth(G, k, sh, Tm, s); }));
+                                [=](cudaStream_t s) { launch_chol_orth(G, k, sh, Tm, Xg, s); }));
                     ctr(net, W, "ac,cd->ad", x, Tt, &y);
                 }
             };
@@ -614,7 +619,7 @@ Engine::PPair Engine::projector(Network& net, Plan& P, const Ten& U, const Ten& 
             cholqr3(Zb, Yb, Q1, Qz);                  // Q_z
             ctr(net, W, "ac,ad->cd", Zbt, Qzt, &Bt);  // B = Z^T Q_z = Q_y^T M Q_z
             push(W, std::make_unique<FnStep>([=](cudaStream_t s) {
-                launch_jacobi_svd(R1, k, S, Ur, Wr, np->svd_info + info_idx, s);
+                launch_jacobi_svd(R1, k, S, Ur, Wr, np->svd_info + info_idx, Vg, s);
             }));
             ctr(net, W, "ac,cd->ad", Qyt, Urt, &Ut);  // U = Q_y U_B
             ctr(net, W, "ac,cd->ad", Qzt, Wt, &Vb);   // V = Q_z V_B

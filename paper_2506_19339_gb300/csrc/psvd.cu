@@ -162,11 +162,12 @@ __device__ float jacobi_sweep(F* A, F* V, int kp, int ld, F tol, RoundScratch rs
 // orthonormal (up to the shift) for the Y that gave G = Y^T Y.  Shared memory: 2 k^2 + 2 k
 // doubles.
 __global__ void __launch_bounds__(kPsvdThreads)
-    chol_orth_kernel(const double* __restrict__ G, int k, double shift, double* __restrict__ T) {
+    chol_orth_kernel(const double* __restrict__ G, int k, double shift, double* __restrict__ T,
+                     double* Xg) {
     extern __shared__ double sm[];
-    double* R = sm;              // row-major k x k: scaled Gram, then the unscaled factor rows
-    double* X = sm + k * k;      // row-major k x k: F^-1
-    double* d = sm + 2 * k * k;  // reciprocal column norms
+    double* R = sm;                        // row-major k x k: scaled Gram, then the factor rows
+    double* X = Xg ? Xg : sm + k * k;      // row-major k x k: F^-1 (global above kPsvdSmemK)
+    double* d = sm + (Xg ? 1 : 2) * k * k; // reciprocal column norms
     double* rinv = d + k;        // reciprocal pivots
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int i = tid; i < k; i += nt) {  // d = 1 / column norm (0 for a zero column)
@@ -211,14 +212,14 @@ __global__ void __launch_bounds__(kPsvdThreads)
 // different shared-memory banks.  Shared memory: jacobi_svd_smem(k).
 __global__ void __launch_bounds__(kPsvdThreads)
     jacobi_svd_kernel(const double* __restrict__ B, int k, double* __restrict__ S,
-                      double* __restrict__ U, double* __restrict__ W, int* info) {
+                      double* __restrict__ U, double* __restrict__ W, int* info, double* Vg) {
     extern __shared__ double sm[];
     const int kp = k + (k & 1), ld = kp + 1, np = kp / 2;
-    double* A = sm;                // FP64 phase: column j at A + j ld
-    double* V = sm + kp * ld;      // W, column j at V + j ld
-    float* A32 = (float*)A;        // FP32 phase: both FP32 matrices inside A's space
+    double* A = sm;                        // FP64 phase: column j at A + j ld
+    double* V = Vg ? Vg : sm + kp * ld;    // W, column j at V + j ld (global above kPsvdSmemK)
+    float* A32 = (float*)A;                // FP32 phase: both FP32 matrices inside A's space
     float* V32 = A32 + kp * ld;
-    double* sig = sm + 2 * kp * ld;
+    double* sig = sm + (Vg ? 1 : 2) * kp * ld;
     RoundScratch rs;
     rs.c = sig + kp;
     rs.s = rs.c + np;
@@ -364,31 +365,36 @@ void launch_refill(double* V, int n, int k, const double* S, unsigned long long 
     refill_kernel<<<k, 256, 0, s>>>(V, n, k, S, seed);
 }
 
-size_t chol_orth_smem(int k) { return (size_t)(2 * k * k + 2 * k) * sizeof(double); }
-size_t jacobi_svd_smem(int k) {
-    const int kp = k + (k & 1), ld = kp + 1, np = kp / 2;
-    return (size_t)(2 * kp * ld + kp + 2 * np) * sizeof(double) + (size_t)(kp + 3 * np) * sizeof(int);
+size_t chol_orth_smem(int k, bool global_x) {
+    return (size_t)((global_x ? 1 : 2) * k * k + 2 * k) * sizeof(double);
 }
+size_t jacobi_svd_smem(int k, bool global_v) {
+    const int kp = k + (k & 1), ld = kp + 1, np = kp / 2;
+    return (size_t)((global_v ? 1 : 2) * kp * ld + kp + 2 * np) * sizeof(double) +
+           (size_t)(kp + 3 * np) * sizeof(int);
+}
+constexpr int kMaxDynSmem = 227 * 1024;  // opt-in dynamic shared memory per block
 
-void launch_chol_orth(const double* G, int k, double shift, double* T, cudaStream_t s) {
-    const size_t smem = chol_orth_smem(k);
+void launch_chol_orth(const double* G, int k, double shift, double* T, double* Xg,
+                      cudaStream_t s) {
+    const size_t smem = chol_orth_smem(k, Xg != nullptr);
     static std::once_flag once;
     std::call_once(once, [] {
         cudaFuncSetAttribute(chol_orth_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)chol_orth_smem(kPsvdMaxK));
+                             kMaxDynSmem);
     });
-    chol_orth_kernel<<<1, kPsvdThreads, smem, s>>>(G, k, shift, T);
+    chol_orth_kernel<<<1, kPsvdThreads, smem, s>>>(G, k, shift, T, Xg);
 }
 
 void launch_jacobi_svd(const double* B, int k, double* S, double* U, double* W, int* info,
-                       cudaStream_t s) {
-    const size_t smem = jacobi_svd_smem(k);
+                       double* Vg, cudaStream_t s) {
+    const size_t smem = jacobi_svd_smem(k, Vg != nullptr);
     static std::once_flag once;
     std::call_once(once, [] {
         cudaFuncSetAttribute(jacobi_svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)jacobi_svd_smem(kPsvdMaxK));
+                             kMaxDynSmem);
     });
-    jacobi_svd_kernel<<<1, kPsvdThreads, smem, s>>>(B, k, S, U, W, info);
+    jacobi_svd_kernel<<<1, kPsvdThreads, smem, s>>>(B, k, S, U, W, info, Vg);
 }
 
 void launch_vt_columns(const double* VT, double* Vout, int n, int k, cudaStream_t s) {

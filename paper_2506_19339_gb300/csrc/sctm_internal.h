@@ -80,12 +80,15 @@ void launch_scalevec(const double* S, int k, double cutoff, double* out, cudaStr
 void launch_signfix(double* U, double* V, int n, int k, int vt, cudaStream_t s);
 void launch_copy(const double* src, double* dst, long long n, cudaStream_t s);
 // partial SVD (psvd.cu): column-scaled Cholesky QR pass, one-CTA Jacobi SVD, V^T -> columns
-constexpr int kPsvdMaxK = 112;  // largest subspace (chi + oversampling) the one-CTA kernels take
-void launch_chol_orth(const double* G, int k, double shift, double* T, cudaStream_t s);
+constexpr int kPsvdSmemK = 112;  // subspaces up to this size keep all k x k work in shared memory
+constexpr int kPsvdMaxK = 160;   // largest subspace: above kPsvdSmemK one k x k matrix of each
+                                 // one-CTA kernel lives in a global scratch buffer
+void launch_chol_orth(const double* G, int k, double shift, double* T, double* Xg,
+                      cudaStream_t s);
 void launch_refill(double* V, int n, int k, const double* S, unsigned long long seed,
                    cudaStream_t s);
 void launch_jacobi_svd(const double* B, int k, double* S, double* U, double* W, int* info,
-                       cudaStream_t s);
+                       double* Vg, cudaStream_t s);
 void launch_vt_columns(const double* VT, double* Vout, int n, int k, cudaStream_t s);
 void launch_zero(double* p, long long n, cudaStream_t s);
 // flag[0] = 1 if any of p[0..n) is NaN or infinite, else 0
