@@ -373,15 +373,15 @@ size_t jacobi_svd_smem(int k, bool global_v) {
     return (size_t)((global_v ? 1 : 2) * kp * ld + kp + 2 * np) * sizeof(double) +
            (size_t)(kp + 3 * np) * sizeof(int);
 }
-constexpr int kMaxDynSmem = 227 * 1024;  // opt-in dynamic shared memory per block
 
 void launch_chol_orth(const double* G, int k, double shift, double* T, double* Xg,
                       cudaStream_t s) {
     const size_t smem = chol_orth_smem(k, Xg != nullptr);
     static std::once_flag once;
     std::call_once(once, [] {
-        cudaFuncSetAttribute(chol_orth_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             kMaxDynSmem);
+        // the largest request: all in shared memory at kPsvdSmemK, or X in global at kPsvdMaxK
+        const size_t mx = std::max(chol_orth_smem(kPsvdSmemK, false), chol_orth_smem(kPsvdMaxK, true));
+        cudaFuncSetAttribute(chol_orth_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
     });
     chol_orth_kernel<<<1, kPsvdThreads, smem, s>>>(G, k, shift, T, Xg);
 }
@@ -391,8 +391,9 @@ void launch_jacobi_svd(const double* B, int k, double* S, double* U, double* W, 
     const size_t smem = jacobi_svd_smem(k, Vg != nullptr);
     static std::once_flag once;
     std::call_once(once, [] {
-        cudaFuncSetAttribute(jacobi_svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             kMaxDynSmem);
+        const size_t mx =
+            std::max(jacobi_svd_smem(kPsvdSmemK, false), jacobi_svd_smem(kPsvdMaxK, true));
+        cudaFuncSetAttribute(jacobi_svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
     });
     jacobi_svd_kernel<<<1, kPsvdThreads, smem, s>>>(B, k, S, U, W, info, Vg);
 }
