@@ -70,10 +70,10 @@ enum { SCTM_GRAD_ENV = 0, SCTM_GRAD_ADJOINT = 1 };
  *                     solver): the first solve of each projector after a cold start is gesvd,
  *                     every later one a subspace-iteration step warm-started from the previous
  *                     iteration's right singular subspace (chi + p columns, p = chi/4, at
- *                     least 8, reduced to keep chi + p <= 112 where chi <= 104) with a
+ *                     least 8, reduced to keep chi + p <= 160 where chi <= 152) with a
  *                     Rayleigh-Ritz (Jacobi) extraction, about 25 kernel launches instead of
- *                     thousands.  Projectors whose subspace would exceed 112 columns stay on
- *                     gesvd.  The fixed point is the same as SCTM_SVD_QR's; a trajectory from a
+ *                     thousands.  Projectors whose subspace would exceed 160 columns stay on
+ *                     gesvd; above 112 columns the k x k kernels use a global scratch buffer.  The fixed point is the same as SCTM_SVD_QR's; a trajectory from a
  *                     cold start differs at the level of the subspace error of the early
  *                     iterations.  sctm_env_import and a reset start cold again.
  *   SCTM_SVD_PARTIAL_RANDOM  as SCTM_SVD_PARTIAL, but the cold solve is four subspace steps
