@@ -94,14 +94,14 @@ def test_partial_svd_full_size_runs(mode):
 
 
 def test_partial_svd_large_subspace_stays_on_full_svd():
-    """chi = 113 at D = 1: every subspace (chi + chi/4 columns, at most the cut dimension 113 or
-    226) is above the one-CTA limit of 112 columns, so every projector keeps the full SVD and the
-    result equals the full-SVD mode's bit for bit."""
+    """chi = 161 at D = 1: every subspace (161 columns at the alpha cut, whose dimension is 161;
+    169 at the kappa and iota cuts) is above the 160-column limit of the one-CTA kernels, so every
+    projector keeps the full SVD and the result equals the full-SVD mode's bit for bit."""
     A = inputs.product_plus_peps(1)
     fs = []
     for mode in (sctm.SCTM_SVD_QR, sctm.SCTM_SVD_PARTIAL):
         st, O = sctm.sctm_ising_pepo(10.0)
-        r = sctm.SplitCTMRG(A, O, 113, 10.0, svd_mode=mode)
+        r = sctm.SplitCTMRG(A, O, 161, 10.0, svd_mode=mode)
         try:
             r.iterate(2, 0.0)
             fs.append(r.free_energy())
