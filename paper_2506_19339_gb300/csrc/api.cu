@@ -279,6 +279,8 @@ sctm_status sctm_iterate(sctm_ctx* ctx, int max_it, double tol, int* it_done, do
         }
         Engine::cur_lane = 0;
     };
+    // each call reports its own device-side failures (timeout, non-finite projector matrix)
+    cuda_ok(cudaMemsetAsync(e.dev_err, 0, 2 * sizeof(int), e.stream), "error flags");
     cuda_ok(cudaEventRecord(ctx->lane_fork, e.stream), "fork");
     cuda_ok(cudaStreamWaitEvent(e.lanes[1].streams[0], ctx->lane_fork, 0), "fork wait");
     std::thread t1(drive, 1);
