@@ -32,7 +32,7 @@ SVD_MODES = {'qr': 0, 'polar': 1, 'partial': 2, 'partial-random': 3}
 SVD_NAMES = {'qr': 'cuSOLVER gesvd', 'polar': 'cuSOLVER gesvdp',
              'partial': 'partial SVD: gesvd cold solve, then warm-started subspace iteration + '
                         'one-CTA Jacobi',
-             'partial-random': 'partial SVD: randomized cold solve (4 subspace steps), then '
+             'partial-random': 'partial SVD: randomized cold solve (2 subspace steps), then '
                                'warm-started subspace iteration + one-CTA Jacobi'}
 
 

@@ -76,7 +76,7 @@ enum { SCTM_GRAD_ENV = 0, SCTM_GRAD_ADJOINT = 1 };
  *                     gesvd; above 112 columns the k x k kernels use a global scratch buffer.  The fixed point is the same as SCTM_SVD_QR's; a trajectory from a
  *                     cold start differs at the level of the subspace error of the early
  *                     iterations.  sctm_env_import and a reset start cold again.
- *   SCTM_SVD_PARTIAL_RANDOM  as SCTM_SVD_PARTIAL, but the cold solve is four subspace steps
+ *   SCTM_SVD_PARTIAL_RANDOM  as SCTM_SVD_PARTIAL, but the cold solve is two subspace steps
  *                     from a pseudo-random (SplitMix64) subspace instead of gesvd: no cuSOLVER
  *                     call at all.  Same fixed point; from a cold start the first iterations'
  *                     projectors carry the random start's subspace error, which the later warm

@@ -1,7 +1,7 @@
 """GPU: the partial SVD (Sec. III's iterative solver for the largest chi singular triplets) against
 the FP64 oracle, whose projectors come from a full SVD.
 
-The first solve of every projector after a cold start is a full SVD (SCTM_SVD_PARTIAL) or four
+The first solve of every projector after a cold start is a full SVD (SCTM_SVD_PARTIAL) or two
 subspace steps from a pseudo-random subspace (SCTM_SVD_PARTIAL_RANDOM); later solves are one
 warm-started subspace-iteration step, whose subspace error decays geometrically with the
 iterations.  At a fixed point the two methods have the same projectors, so converged values
