@@ -110,8 +110,8 @@ struct SvdStep : Step {
 // The partial SVD of one projector matrix: a full SVD (cold) while no warm-start subspace
 // exists, the warm-started subspace iteration step otherwise (psvd.cu has the algorithm).
 // SCTM_SVD_PARTIAL_RANDOM replaces the cold full SVD by kRandomColdSteps warm steps from a
-// pseudo-random subspace (two keep the partial-SVD parity of the four first used, and cut the
-// cold iteration's cost).
+// pseudo-random subspace (two steps meet the same parity bounds as four, at half the cold
+// iteration's cost).
 constexpr int kRandomColdSteps = 2;
 struct PartialSvdStep : Step {
     Plan cold, warm;
