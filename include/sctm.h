@@ -78,11 +78,11 @@ enum { SCTM_GRAD_ENV = 0, SCTM_GRAD_ADJOINT = 1 };
  *                     start differs at the level of the subspace error of the early iterations.
  *                     sctm_env_import and a reset start cold again.
  *   SCTM_SVD_PARTIAL_RANDOM  as SCTM_SVD_PARTIAL, but the cold solve is two subspace steps
- *                     from a pseudo-random (SplitMix64) subspace instead of gesvd: no cuSOLVER
- *                     call in the projectors (only the chi x chi spectrum of the convergence
- *                     test, Sec. III.D, stays on gesvd).  Same fixed point; from a cold start
- *                     the first iterations' projectors carry the random start's subspace error,
- *                     which the later warm steps remove. */
+ *                     from a pseudo-random (SplitMix64) subspace instead of gesvd, and the
+ *                     chi x chi spectrum of the convergence test (Sec. III.D) uses the same
+ *                     Jacobi kernel: no cuSOLVER call at all for chi <= 160.  Same fixed
+ *                     point; from a cold start the first iterations' projectors carry the
+ *                     random start's subspace error, which the later warm steps remove. */
 enum { SCTM_SVD_QR = 0, SCTM_SVD_POLAR = 1, SCTM_SVD_PARTIAL = 2, SCTM_SVD_PARTIAL_RANDOM = 3 };
 enum { SCTM_NET_NUM = 0, SCTM_NET_DEN = 1 };          /* <psi|T|psi> and <psi|psi>            */
 enum { SCTM_MOVE_LEFT = 0, SCTM_MOVE_RIGHT = 1, SCTM_MOVE_UP = 2, SCTM_MOVE_DOWN = 3 };

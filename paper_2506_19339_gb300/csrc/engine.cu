@@ -952,9 +952,27 @@ static void build_spectrum(Engine& e, Network& net) {
     const Ten R1 = e.ctr(net, P, "ab,ac->bc", net.C[0], net.C[1]);
     const Ten R2 = e.ctr(net, P, "bc,dc->bd", R1, net.C[2]);
     const Ten rho = e.ctr(net, P, "bd,de->be", R2, net.C[3]);
-    double* work = e.dalloc((long long)chi * chi);
     double* Sraw = e.dalloc(chi);
     double* rho_p = rho.p;
+    double* S_old = net.S_old;
+    double* dS = net.dS;
+    if (e.svd_mode == SCTM_SVD_PARTIAL_RANDOM && chi <= kPsvdMaxK) {
+        // singular values by the partial SVD's Jacobi kernel (the same values for rho and its
+        // transpose), so that this mode makes no cuSOLVER call at all
+        double* Ub = e.dalloc((long long)chi * chi);
+        double* Wb = e.dalloc((long long)chi * chi);
+        const int kp = chi + (chi & 1);
+        double* Vg = chi > kPsvdSmemK ? e.dalloc((long long)kp * (kp + 1)) : nullptr;
+        const int info_idx = net.n_svd++;
+        const Network* np = &net;
+        e.push(P, std::make_unique<FnStep>([=](cudaStream_t s) {
+            launch_jacobi_svd(rho_p, chi, Sraw, Ub, Wb, np->svd_info + info_idx, Vg, s);
+        }));
+        e.push(P, std::make_unique<FnStep>(
+            [=](cudaStream_t s) { launch_spectrum_update(Sraw, rho_p, chi, S_old, dS, s); }));
+        return;
+    }
+    double* work = e.dalloc((long long)chi * chi);
     e.push(P, std::make_unique<FnStep>(
         [=](cudaStream_t s) { launch_copy(rho_p, work, (long long)chi * chi, s); }));
     auto sv = std::make_unique<SvdStep>();
@@ -969,8 +987,6 @@ static void build_spectrum(Engine& e, Network& net) {
     net.svd_nmax = std::max(net.svd_nmax, chi);
     net.svd_steps.push_back(sv.get());
     e.push(P, std::move(sv));
-    double* S_old = net.S_old;
-    double* dS = net.dS;
     e.push(P, std::make_unique<FnStep>(
         [=](cudaStream_t s) { launch_spectrum_update(Sraw, rho_p, chi, S_old, dS, s); }));
 }
