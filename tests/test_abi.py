@@ -88,3 +88,19 @@ def test_plans_build_without_gpu(lib, D, d, chi, svd):
                          text=True, timeout=300)
     assert out.returncode == 0, out.stderr
     assert out.stdout.strip() == '0', out.stdout + out.stderr
+
+
+def test_binding_constants_match_header():
+    """The ctypes binding's enum values are the header's (status codes, precisions, SVD modes,
+    networks, moves, profiled kernels)."""
+    import re
+    text = open(os.path.join(ROOT, 'include', 'sctm.h')).read()
+    values = {}
+    for name, val in re.findall(r'\b(SCTM_[A-Z0-9_]+)\s*=\s*(\d+)', text):
+        values[name] = int(val)
+    assert len(values) > 20
+    for name, val in values.items():
+        if hasattr(sctm, name):
+            assert getattr(sctm, name) == val, name
+    for name in ('SCTM_PREC_F64EMU', 'SCTM_SVD_PARTIAL_RANDOM', 'SCTM_KERNEL_F64EMU', 'SCTM_ETIMEOUT'):
+        assert getattr(sctm, name) == values[name], name
