@@ -68,7 +68,7 @@ def test_host_side_error_paths(lib):
 
 @pytest.mark.parametrize('D,d,chi,svd', [(1, 2, 1, 0), (2, 2, 5, 0), (3, 2, 10, 0), (4, 2, 64, 0),
                                          (2, 3, 7, 0), (2, 2, 5, 2), (4, 2, 64, 2), (3, 2, 100, 2),
-                                         (3, 2, 36, 3)])
+                                         (3, 2, 36, 3), (5, 2, 100, 3)])
 def test_plans_build_without_gpu(lib, D, d, chi, svd):
     """SCTM_DRYRUN=1 builds every plan (four moves, convergence, local contractions) of both
     networks with placeholder pointers: every contraction's labels, dimensions and ranks are
