@@ -89,13 +89,28 @@ __global__ void splitk_sum_kernel(const double* part, double* O, long long MN, i
 std::mutex g_setup_mutex;
 double* g_scratch_dev[kMaxDevices] = {nullptr};
 
-bool is_device_pointer(const void* p) {
+// True if p is device (or managed) memory that belongs to device `dev`.  Memory of another GPU
+// is rejected: the kernel runs on the current device, and reaching another GPU's memory without
+// peer access would fault instead of returning an error.
+bool is_device_pointer_on(const void* p, int dev) {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();  // clears only the error this query itself raised
+        return false;
+    }
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
+}
+
+// True if the stream is the legacy / per-thread default stream or was created on `dev`.
+bool stream_on(cudaStream_t s, int dev) {
+    if (s == nullptr || s == cudaStreamLegacy || s == cudaStreamPerThread) return true;
+    int sd = -1;
+    if (cudaStreamGetDevice(s, &sd) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    return sd == dev;
 }
 
 }  // namespace
@@ -104,9 +119,15 @@ extern "C" sctm_status sctm_gemm_noalloc(const double* X, const double* Y, doubl
                                          int K, void* cuda_stream) {
     if (!X || !Y || !O || M < 1 || N < 1 || K < 1) return SCTM_EINVAL;
     if ((long long)M * N > kScratchDoubles) return SCTM_EINVAL;  // M*N above 2^21 doubles
-    if (!is_device_pointer(X) || !is_device_pointer(Y) || !is_device_pointer(O)) return SCTM_EINVAL;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SCTM_ECUDA;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (!is_device_pointer_on(X, dev) || !is_device_pointer_on(Y, dev) ||
+        !is_device_pointer_on(O, dev) || !stream_on(s, dev))
+        return SCTM_EINVAL;
+    // An error left pending by earlier, unrelated work is not this call's: report it without
+    // launching and without clearing it.
+    if (cudaPeekAtLastError() != cudaSuccess) return SCTM_ECUDA;
     double* scratch = nullptr;
     {
         // Once per device, with that device current: the scratch array's device address.
@@ -138,12 +159,12 @@ extern "C" sctm_status sctm_gemm_noalloc(const double* X, const double* Y, doubl
             kchunk = K;
         }
     }
-    cudaStream_t s = (cudaStream_t)cuda_stream;
     dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, splits);
     gemm_rowmajor_kernel<<<grid, NT, 0, s>>>(X, Y, O, M, N, K, splits, kchunk, scratch);
     if (splits > 1) {
         const int blocks = (int)std::min<long long>((MN + 255) / 256, 4096);
         splitk_sum_kernel<<<blocks, 256, 0, s>>>(scratch, O, MN, splits);
     }
+    // no error was pending before the launches, so any error now is theirs
     return cudaGetLastError() == cudaSuccess ? SCTM_OK : SCTM_ECUDA;
 }

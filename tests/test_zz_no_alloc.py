@@ -70,3 +70,29 @@ def test_no_alloc_general_shapes_and_limits():
     assert sctm.sctm_gemm_noalloc(X, Y, O, M, N, 1) == sctm.SCTM_EINVAL
     host = np.zeros((2, 2))
     assert sctm.sctm_gemm_noalloc(host, host, host, 2, 2, 2) == sctm.SCTM_EINVAL
+
+
+def test_no_alloc_warm_calls_leave_free_memory_unchanged():
+    """After one warm call (which loads the module and looks up the scratch address), further
+    calls -- single-pass and split-K shapes -- must not change the device's free memory: the
+    entry point allocates nothing.  Every tensor is allocated before the first reading."""
+    import torch
+    build.build()
+    sctm.load()
+    rng = np.random.default_rng(5)
+    shapes = [(5, 7, 20000), (300, 200, 500), (64, 64, 4096)]
+    ops = []
+    for (M, N, K) in shapes:
+        X, Y = _dev(rng.standard_normal((M, K))), _dev(rng.standard_normal((K, N)))
+        O = torch.zeros((M, N), dtype=torch.float64, device='cuda')
+        ops.append((X, Y, O, M, N, K))
+    X, Y, O, M, N, K = ops[0]
+    assert sctm.sctm_gemm_noalloc(X, Y, O, M, N, K) == sctm.SCTM_OK
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        for (X, Y, O, M, N, K) in ops:
+            assert sctm.sctm_gemm_noalloc(X, Y, O, M, N, K) == sctm.SCTM_OK
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
