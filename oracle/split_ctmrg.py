@@ -176,6 +176,7 @@ def projector_pair(U, L, t_axes, chi, cutoff):
     Um = U.transpose(perm).reshape(nt, nr)
     Lm = L.transpose(perm).reshape(nt, nr)
     M = Lm.T @ Um
+    _count(float(nr) * nr * nt)
     Us, S, Vh = np.linalg.svd(M)
     if chi is None:
         chi = S.shape[0]
@@ -193,6 +194,7 @@ def projector_pair(U, L, t_axes, chi, cutoff):
     PT = np.zeros((chi, nt))
     PB[:, :k] = (Um @ Vt) * inv[None, :]
     PT[:k, :] = ((Lm @ Ut) * inv[None, :]).T
+    _count(2.0 * nt * nr * k)
     return PB.reshape(tdims + [chi]), PT.reshape([chi] + tdims), S
 
 
@@ -200,11 +202,28 @@ def projector_pair(U, L, t_axes, chi, cutoff):
 # insertion and absorption (Sec. III.B, Fig. 5(a),(b))
 # ----------------------------------------------------------------------------------------------
 
+# Algorithmic FLOP count of the contractions evaluated so far: 2 x the product of the dimensions
+# of every distinct label of a pairwise contraction (its multiply-adds), and 2 M N K for the
+# projector matrix products.  reset_flops() zeroes it; SVDs are not counted.
+FLOPS = {'contractions': 0}
+
+
+def reset_flops():
+    FLOPS['contractions'] = 0
+
+
+def _count(n_macs):
+    FLOPS['contractions'] += 2 * int(n_macs)
+
+
 def _c2(spec, X, Y):
     """Pairwise contraction written as an einsum spec and evaluated with a BLAS matrix product
     (numpy.tensordot): every label shared by X and Y and absent from the output is summed."""
     ins, out = spec.split('->')
     a, b = ins.split(',')
+    dims = dict(zip(a, X.shape))
+    dims.update(zip(b, Y.shape))
+    _count(np.prod([dims[c] for c in dims], dtype=np.float64))
     shared = [c for c in a if c in b and c not in out]
     for c in a + b:
         if c not in out and (c in a) == (c in b):
@@ -610,3 +629,17 @@ def evaluate(A, O_num, O_den, T, chi, max_iter, tol=None, cutoff=1e-12, env_num=
     res['f'] = f
     res['g'] = g
     return res
+
+
+def fd_directional_derivative(A, O_num, O_den, T, chi, v, h, tol, env_num, env_den, max_iter=400,
+                              cutoff=1e-12):
+    """Central finite difference of the converged free energy along v:
+        (f(A + h v) - f(A - h v)) / (2 h),
+    each f the split-CTMRG result iterated until ||S[i+1] - S[i]||_2 < tol (Sec. III.D) from the
+    given environments (the converged ones of A: a warm start; the fixed point is the same).  This
+    is the plain definition of the derivative of f_chi(A) that the fixed-point adjoint computes;
+    the paper's environment gradient (Eq. "gradient expression") differs from it by the
+    environment's dependence on A, which vanishes as chi grows."""
+    fp = evaluate(A + h * v, O_num, O_den, T, chi, max_iter, tol, cutoff, env_num, env_den)['f']
+    fm = evaluate(A - h * v, O_num, O_den, T, chi, max_iter, tol, cutoff, env_num, env_den)['f']
+    return (fp - fm) / (2.0 * h)

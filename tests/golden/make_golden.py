@@ -1,0 +1,99 @@
+"""Write the stored expected values of the GPU parity tests, computed by the FP64 oracle only.
+
+Each case is a contractive stand-in (a perturbed product PEPS, see paper_2506_19339_gb300/inputs.py)
+at the (D, chi, T) of one workload configuration: for these inputs the split-CTMRG iteration
+(Sec. III.B) converges and rounding differences decay, so two FP64 implementations of the same
+algorithm can be compared.  For each requested iteration count ("converged" = iterate until
+||S[i+1] - S[i]||_2 < tol, Sec. III.D) the file records f = -T (ln kappa_num - ln kappa_den) and
+the environment gradient g = -2T (E_num / Z11_num - E_den / Z11_den) (Sec. II, Eqs. "free energy
+expression" and "gradient expression"), both networks iterated from the SplitMix64 cold start.
+
+    python tests/golden/make_golden.py <case> [<case> ...]        (cases: see CASES)
+
+Output: tests/golden/<case>.json.  Only oracle/ and the seeded input generators are imported.
+"""
+import json
+import os
+import platform
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+sys.path.insert(0, ROOT)
+
+from oracle import ising, split_ctmrg as sc  # noqa: E402
+from paper_2506_19339_gb300 import inputs  # noqa: E402
+
+# name: (D, chi, T, seed, eps, records, tol, max_iter); records are iteration counts and/or
+# 'converged'
+CASES = {
+    'cfg2_D3_chi36': (3, 36, 4.5115, 1, 0.1, [2, 'converged'], 1e-12, 400),
+    'cfg3_D4_chi64': (4, 64, 4.5, 2, 0.1, [2, 'converged'], 1e-11, 300),
+    'cfg4_D5_chi100': (5, 100, 4.52, 3, 0.1, [2, 'converged'], 1e-11, 300),
+    'cfg5b_D6_chi144': (6, 144, 4.5115, 4, 0.1, [2], None, 2),
+}
+
+
+def run_case(name):
+    D, chi, T, seed, eps, records, tol, max_iter = CASES[name]
+    A = inputs.perturbed_product_peps(D, seed, eps=eps)
+    nets = {'num': ising.ising_pepo(1.0 / T), 'den': ising.identity_pepo()}
+    state = {}
+    for k, O in nets.items():
+        state[k] = {'env': sc.init_env(chi, D, O.shape[2]), 'S': None, 'it': 0, 'dS': np.inf,
+                    'done': False}
+    out = {'case': name, 'D': D, 'chi': chi, 'T': T, 'seed': seed, 'eps': eps,
+           'peps': 'inputs.perturbed_product_peps(%d, %d, eps=%g)' % (D, seed, eps),
+           'cutoff': 1e-12, 'tol': tol, 'records': {},
+           'written_by': 'tests/golden/make_golden.py (oracle/split_ctmrg.py, FP64 NumPy)',
+           'host': platform.machine()}
+    t0 = time.time()
+
+    def record(label):
+        res = {}
+        for k, O in nets.items():
+            loc = sc.local_contractions(state[k]['env'], A, O, A)
+            res[k] = {'lnk': sc.ln_kappa(loc), 'Z11': loc['Z11'],
+                      'E': sc.bra_environment(state[k]['env'], loc)}
+        f = -T * (res['num']['lnk'] - res['den']['lnk'])
+        g = -2.0 * T * (res['num']['E'] / res['num']['Z11'] - res['den']['E'] / res['den']['Z11'])
+        out['records'][str(label)] = {
+            'f': f, 'g': [float(x) for x in g.ravel()],
+            'iterations': {k: state[k]['it'] for k in nets},
+            'dS': {k: float(state[k]['dS']) for k in nets},
+            'lnk': {k: res[k]['lnk'] for k in nets}}
+        print('%s %s: f = %.15f  its %s  dS %s  (%.0f s)' % (
+            name, label, f, out['records'][str(label)]['iterations'],
+            out['records'][str(label)]['dS'], time.time() - t0), flush=True)
+
+    fixed = sorted(r for r in records if r != 'converged')
+    for n_it in fixed:
+        for k, O in nets.items():
+            s = state[k]
+            steps = n_it - s['it']
+            if steps > 0:
+                s['env'], it, s['dS'], s['S'] = sc.iterate(s['env'], A, O, A, chi, steps,
+                                                           None, 1e-12, s['S'])
+                s['it'] += it
+        record(n_it)
+    if 'converged' in records:
+        for k, O in nets.items():
+            s = state[k]
+            while s['it'] < max_iter and not (s['dS'] < tol):
+                s['env'], it, s['dS'], s['S'] = sc.iterate(s['env'], A, O, A, chi, 1, None, 1e-12,
+                                                           s['S'])
+                s['it'] += it
+                print('  %s %s iteration %d: dS = %.3e' % (name, k, s['it'], s['dS']), flush=True)
+        record('converged')
+    out['seconds'] = time.time() - t0
+    with open(os.path.join(HERE, name + '.json'), 'w') as fh:
+        json.dump(out, fh, indent=0)
+        fh.write('\n')
+
+
+if __name__ == '__main__':
+    for case in sys.argv[1:] or list(CASES):
+        run_case(case)

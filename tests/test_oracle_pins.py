@@ -219,8 +219,13 @@ def test_projector_pair_identities():
     u, s, vh = np.linalg.svd(M)
     best = (u[:, :chi] * s[:chi]) @ vh[:chi]
     assert np.allclose(approx, best, atol=1e-10 * s[0])
-    # sign gauge: largest-magnitude entry of each kept left vector is positive
     assert np.all(S[:-1] >= S[1:])
+    # sign gauge: P_B[:, k] = rho_T v_k s_k^-1/2 fixes the sign the oracle gave the pair
+    # (u_k, v_k); with that sign the largest-magnitude entry of u_k must be positive
+    for k in range(chi):
+        sign = np.sign(np.dot(PB.reshape(6, chi)[:, k], Um @ vh[k]))
+        uk = sign * u[:, k]
+        assert sign != 0 and uk[np.argmax(np.abs(uk))] > 0, k
 
 
 # ---------------------------------------------------------------- V5 / V6: closed forms
@@ -312,23 +317,127 @@ def test_split_converges_to_reduced_reference():
     assert gaps[2] < 1e-7
 
 
+def _lnk_fixed_env(env, A, O, B):
+    loc = sc.local_contractions(env, A, O, B)
+    return loc['Z11'] * loc['Z00'] / (loc['Z10'] * loc['Z01'])
+
+
+@pytest.mark.parametrize('D,chi,directions', [(2, 5, 'all'), (3, 4, 8), (4, 3, 8)])
+def test_env_gradient_is_the_bra_derivative(D, chi, directions):
+    """Eq. "gradient expression": g = -2T (E_num / Z11_num - E_den / Z11_den) is twice the
+    derivative of f = -T (ln kappa_num - ln kappa_den) with respect to the bra tensor with the
+    environments held fixed.  Central differences of f in the bra slot only (the environments
+    and the ket A are not touched, so the difference quotient is exact up to O(h^2)) over all
+    p D^4 = 32 components at D = 2 and random directions at D = 3, 4, on random environments."""
+    T = 4.5
+    rng = np.random.default_rng(40 + D)
+    A = rng.standard_normal((2,) + (D,) * 4)
+    O, Oid = ising.ising_pepo(1 / T), ising.identity_pepo()
+    envs = [_rand_env(rng, chi, D, 2), _rand_env(rng, chi, D, 1)]
+    for e in envs:  # positive environments keep every kappa positive
+        for k in ('C1', 'C2', 'C3', 'C4'):
+            e[k] = np.abs(e[k])
+        for t in ('T1', 'T2', 'T3', 'T4'):
+            e[t] = [np.abs(x) for x in e[t]]
+    A = np.abs(A)
+
+    def f_bra(B):
+        return -T * (np.log(_lnk_fixed_env(envs[0], A, O, B)) - np.log(_lnk_fixed_env(envs[1], A, Oid, B)))
+
+    Es = []
+    Zs = []
+    for e, Oo in zip(envs, (O, Oid)):
+        loc = sc.local_contractions(e, A, Oo, A)
+        Es.append(sc.bra_environment(e, loc))
+        Zs.append(loc['Z11'])
+    g = -2.0 * T * (Es[0] / Zs[0] - Es[1] / Zs[1])
+    if directions == 'all':
+        dirs = [np.eye(A.size)[i].reshape(A.shape) for i in range(A.size)]
+    else:
+        dirs = [rng.standard_normal(A.shape) for _ in range(directions)]
+    h = 1e-5
+    for v in dirs:
+        fd = (f_bra(A + h * v) - f_bra(A - h * v)) / (2 * h)
+        # g is twice the bra-slot derivative
+        assert abs(2 * fd - np.sum(g * v)) <= 1e-7 * np.linalg.norm(g) * np.linalg.norm(v)
+
+
 @pytest.mark.slow
-def test_gradient_against_finite_differences():
-    """Eq. "gradient expression": the environment gradient g = 2 d f / d A-bar agrees with central
-    finite differences of f along random directions up to the truncation gap."""
+def test_fd_reference_and_env_gradient_gap():
+    """The finite-difference reference of d f_chi / dA (oracle.split_ctmrg.fd_directional_derivative:
+    converged f at A +- h v) vanishes along A (f(cA) = f(A)), and the paper's environment gradient
+    approaches it as chi grows (the environment's dependence on A drops out at the exact fixed
+    point).  Measured on this input: a gap of ~1.4e-4 at chi = 6 and ~2.4e-6 at chi = 12 (relative
+    to |g|)."""
     T = 4.6
     O, Oid = ising.ising_pepo(1 / T), ising.identity_pepo()
     A = inputs.perturbed_product_peps(2, 7)
-    r = sc.evaluate(A, O, Oid, T, 12, 100, 1e-11)
     rng = np.random.default_rng(3)
-    h = 1e-5
-    for _ in range(2):
-        v = rng.standard_normal(A.shape)
-        v -= np.sum(v * A) * A / np.sum(A * A)
-        fp = sc.evaluate(A + h * v, O, Oid, T, 12, 100, 1e-11)['f']
-        fm = sc.evaluate(A - h * v, O, Oid, T, 12, 100, 1e-11)['f']
-        fd = (fp - fm) / (2 * h)
-        assert abs(fd - np.sum(r['g'] * v)) < 1e-4 * np.linalg.norm(r['g']) * np.linalg.norm(v)
+    v = rng.standard_normal(A.shape)
+    v -= np.sum(v * A) * A / np.sum(A * A)
+    v /= np.linalg.norm(v)
+    gaps = []
+    for chi in (6, 12):
+        r = sc.evaluate(A, O, Oid, T, chi, 400, 1e-11)
+        fd = sc.fd_directional_derivative(A, O, Oid, T, chi, v, 1e-5, 1e-11, r['num']['env'],
+                                          r['den']['env'])
+        gaps.append(abs(fd - np.sum(r['g'] * v)) / np.linalg.norm(r['g']))
+        if chi == 12:
+            along = sc.fd_directional_derivative(A, O, Oid, T, chi, A / np.linalg.norm(A), 1e-5,
+                                                 1e-11, r['num']['env'], r['den']['env'])
+            assert abs(along) <= 1e-8 * np.linalg.norm(r['g'])
+    assert gaps[1] < gaps[0] / 10
+    assert gaps[1] < 2e-5
+
+
+def test_ctm_spectrum_is_a_gauge_invariant_plaquette_product():
+    """Sec. III.D: the convergence measure is the spectrum of the product of the four corners
+    around the plaquette, normalised by its trace.  Each of the four bonds that join neighbouring
+    corners (top, right, bottom, and the left bond where the product is opened) carries an
+    arbitrary orthogonal gauge; the spectrum must not depend on any of them, which fixes which leg
+    of every corner meets which (a transposed corner or another product order breaks the
+    invariance for generic corners).  The same check applied to wrong products (planted mistakes,
+    on the CPU only) fails, so the pin has the power to detect them."""
+    rng = np.random.default_rng(17)
+    chi = 5
+    env = {c: rng.standard_normal((chi, chi)) + 3 * np.eye(chi) for c in ('C1', 'C2', 'C3', 'C4')}
+
+    def q():
+        return np.linalg.qr(rng.standard_normal((chi, chi)))[0]
+
+    def gauged(e, Gt, Gr, Gb, Gl):
+        # C1[h,v]: h top, v left; C2[h,v]: h top, v right; C3[h,v]: h bottom, v right;
+        # C4[h,v]: h bottom, v left
+        return {'C1': Gt.T @ e['C1'] @ Gl, 'C2': Gt.T @ e['C2'] @ Gr,
+                'C3': Gb.T @ e['C3'] @ Gr, 'C4': Gb.T @ e['C4'] @ Gl}
+
+    S0 = sc.ctm_spectrum(env)
+    assert np.all(S0[:-1] >= S0[1:]) and abs(np.sum(S0)) > 0
+    for _ in range(3):
+        S1 = sc.ctm_spectrum(gauged(env, q(), q(), q(), q()))
+        assert np.allclose(S1, S0, rtol=1e-12, atol=1e-14)
+    wrong = [lambda e: e['C1'] @ e['C2'] @ e['C3'].T @ e['C4'],        # C1 not transposed
+             lambda e: e['C1'].T @ e['C2'] @ e['C3'] @ e['C4'],        # C3 not transposed
+             lambda e: e['C1'].T @ e['C3'] @ e['C2'].T @ e['C4']]      # corners out of order
+    for bad in wrong:
+        def spec(e):
+            r = bad(e)
+            return np.linalg.svd(r / np.trace(r), compute_uv=False)
+        moved = max(np.abs(spec(gauged(env, q(), q(), q(), q())) - spec(env)).max() for _ in range(3))
+        assert moved > 1e-6
+
+
+def test_oracle_flop_counter():
+    """The oracle's algorithmic FLOP count: 2 x the product of every distinct label's dimension
+    for a pairwise contraction (2 M N K for a matrix product, batch labels included)."""
+    rng = np.random.default_rng(1)
+    X, Y = rng.standard_normal((3, 4, 5)), rng.standard_normal((5, 4, 6))
+    sc.reset_flops()
+    sc._c2('abk,kbn->abn', X, Y)      # batch b: 3*4*5*6 multiply-adds
+    assert sc.FLOPS['contractions'] == 2 * 3 * 4 * 5 * 6
+    sc.reset_flops()
+    sc._c2('ak,kn->an', rng.standard_normal((7, 8)), rng.standard_normal((8, 9)))
+    assert sc.FLOPS['contractions'] == 2 * 7 * 8 * 9
 
 
 # ---------------------------------------------------------------- counter-based initialisation
