@@ -47,8 +47,9 @@ typedef enum {
  * renormalisation; Sec. III).  Projector formation, SVDs, normalisations, the spectrum, the local
  * contractions and the free-energy ratio are FP64 in every mode.  The TF32 / BF16 forms iterate
  * with a raised pseudo-inverse cutoff and finish in FP64 (sctm_iterate); SCTM_PREC_F64EMU is
- * FP64-accurate and runs on the tensor cores only for contractions with K >= 512, M >= 128,
- * N >= 64 (elsewhere the FP64 kernels, which are faster there). */
+ * FP64-accurate and runs a contraction on the tensor cores where an autotuner, run when the
+ * context is created, measured the emulation faster than the FP64 kernels for that contraction
+ * shape (sctm_autotune_info); elsewhere the FP64 kernels. */
 enum {
     SCTM_PREC_FP64 = 0,    /* all contractions in FP64                                         */
     SCTM_PREC_TF32 = 1,    /* contractions on tensor cores, TF32 inputs, FP32 accumulation     */
@@ -59,6 +60,15 @@ enum {
                            /* FP32 level sums on the tensor cores, FP64 recombination           */
 };
 
+/* Gradient returned by sctm_grad:
+ *   SCTM_GRAD_ENV      the paper's gradient (Sec. II, Eq. "gradient expression"): twice the
+ *                      derivative of f with respect to the bra tensor with the environment held
+ *                      fixed, g = -2T (E_num/Z11_num - E_den/Z11_den)
+ *   SCTM_GRAD_ADJOINT  the derivative of the converged free energy itself, d f / d A (both the
+ *                      ket and the bra slot, and the environment's dependence on A), by implicit
+ *                      differentiation of the split-CTMRG fixed point.  The paper has no such
+ *                      gradient; the two agree as chi grows (the environment part vanishes at
+ *                      the exact fixed point). */
 enum { SCTM_GRAD_ENV = 0, SCTM_GRAD_ADJOINT = 1 };
 /* FP64 SVD of the projector matrices (Eq. "projector construction"):
  *   SCTM_SVD_QR       cuSOLVER gesvd (bidiagonalisation + QR iteration), the reference path: its
@@ -85,6 +95,17 @@ enum { SCTM_GRAD_ENV = 0, SCTM_GRAD_ADJOINT = 1 };
  *                     random start's subspace error, which the later warm steps remove. */
 enum { SCTM_SVD_QR = 0, SCTM_SVD_POLAR = 1, SCTM_SVD_PARTIAL = 2, SCTM_SVD_PARTIAL_RANDOM = 3 };
 enum { SCTM_NET_NUM = 0, SCTM_NET_DEN = 1 };          /* <psi|T|psi> and <psi|psi>            */
+/* Contraction method of the triple-layer network:
+ *   SCTM_METHOD_SPLIT    the paper's split-CTMRG (Sec. III): three edge layers per side, two-stage
+ *                        truncation with six projector pairs per move
+ *   SCTM_METHOD_REDUCED  the reduced method it is compared with (Sec. II, Fig. 3; Sec. IV.A): A,
+ *                        O and A-bar fused into one tensor of bond D d D, standard directional
+ *                        CTMRG with one projector pair per move from the two-by-two patch.  FP64
+ *                        only (precision must be SCTM_PREC_FP64), environment gradient only; its
+ *                        edge tensors are exported in the ket slots (leg m = D d D, grouped
+ *                        (A, O, A-bar)), the int and bra slots are empty; cold start
+ *                        C = e_0 e_0^T, T[0][0][:] = 1. */
+enum { SCTM_METHOD_SPLIT = 0, SCTM_METHOD_REDUCED = 1 };
 enum { SCTM_MOVE_LEFT = 0, SCTM_MOVE_RIGHT = 1, SCTM_MOVE_UP = 2, SCTM_MOVE_DOWN = 3 };
 
 typedef struct {
@@ -93,12 +114,13 @@ typedef struct {
     int p;                        /* physical dimension (2 for Ising), >= 1                 */
     int d;                        /* PEPO in-plane bond dimension (2 for Ising), >= 1       */
     int precision;                /* SCTM_PREC_*                                            */
-    int grad_mode;                /* SCTM_GRAD_ENV (the only mode implemented)              */
+    int grad_mode;                /* SCTM_GRAD_ENV or SCTM_GRAD_ADJOINT                     */
     double svd_cutoff;            /* pseudo-inverse cutoff s_k/s_1 (default 1e-12)          */
     unsigned long long init_seed; /* SplitMix64 seed of the cold-start environment (0)      */
     int batch;                    /* reserved, must be 1                                    */
     void* cuda_stream;            /* cudaStream_t for all work, NULL = legacy default       */
-    int svd_mode;                 /* SCTM_SVD_QR (default) or SCTM_SVD_POLAR                */
+    int svd_mode;                 /* SCTM_SVD_* (default SCTM_SVD_QR)                       */
+    int method;                   /* SCTM_METHOD_SPLIT (default) or SCTM_METHOD_REDUCED     */
 } sctm_opts;
 
 /* Fill *o with the defaults: T=1, D=2, p=2, d=2, FP64, env gradient, cutoff 1e-12, seed 0,
@@ -151,6 +173,35 @@ sctm_status sctm_free_energy(sctm_ctx* ctx, double* f);
  * Same status rules as sctm_free_energy. */
 sctm_status sctm_grad(sctm_ctx* ctx, double* g);
 
+/* sctm_set_grad_mode -- choose what sctm_grad returns (SCTM_GRAD_ENV or SCTM_GRAD_ADJOINT), and
+ * for the adjoint the relative residual tol (0 < tol < 1, default 1e-10), the largest number of
+ * matrix-vector products (>= 1, default 400) of its linear solve, and svd_grad_cutoff in [0, 1)
+ * (default 1e-6): kept singular values below svd_grad_cutoff s_0 are held fixed in the SVD
+ * backward.  Their projector columns are rounding-level directions whose exact sensitivities
+ * (through S^-1/2 and 1 / (s_j^2 - s_i^2)) are huge and cancel in f; carried through, they make
+ * the linear system numerically useless at large chi (measured at D=4, chi=64: no GMRES progress
+ * without the cutoff, a relative residual of 1e-10 with 1e-6).  0 differentiates every kept value.
+ * The adjoint gradient: with E* = F(E*, A) the converged environment of a network (F one
+ * iteration: left, right, up, down moves, Sec. III.B) and ln kappa its per-site value (Sec. II),
+ *     d ln kappa / dA = d ln kappa / dA |_E + lambda^T dF/dA,   (I - J^T) lambda = d ln kappa / dE,
+ * J = dF/dE at E*, and d f / dA = -T (d ln kappa_num / dA - d ln kappa_den / dA).  sctm_grad then
+ * (i) runs one more iteration of each network with full SVDs, keeping every intermediate and a
+ * copy of each move's input (checkpointed recompute), (ii) solves for lambda by restarted GMRES,
+ * each product with J^T one pass of the hand-written backward plans (contractions transposed on
+ * the same kernels, the truncated-SVD backward from the full singular basis with a Lorentzian
+ * broadening of 1e-12 s_0^2, the normalisation's backward), (iii) applies dF/dA^T.  Everything
+ * runs in FP64 on the GPU.  The first adjoint call builds the backward plans (about as much
+ * device memory again as the forward plans).  sctm_grad returns SCTM_ENOCONV (with g written)
+ * if the solve stopped above tol; the environment is left one iteration further.
+ * Errors: EINVAL (mode, tol, max_matvecs). */
+sctm_status sctm_set_grad_mode(sctm_ctx* ctx, int mode, double tol, int max_matvecs,
+                               double svd_grad_cutoff);
+
+/* sctm_adjoint_info -- statistics of the last adjoint gradient: matvecs[0..1] the products with
+ * J^T of the numerator and norm networks' solves, residual[0..1] their final relative residuals
+ * |w - (I - J^T) lambda| / |w|.  Either pointer may be NULL. */
+sctm_status sctm_adjoint_info(sctm_ctx* ctx, int* matvecs, double* residual);
+
 /* sctm_destroy -- release every resource of the context.  NULL-safe (returns SCTM_OK). */
 sctm_status sctm_destroy(sctm_ctx* ctx);
 
@@ -198,6 +249,13 @@ sctm_status sctm_spectrum(sctm_ctx* ctx, int network, double* S);
 sctm_status sctm_iterate_batch(sctm_ctx* const* ctxs, int count, int max_it, double tol,
                                int* status, int* it_done, double* last_dS);
 
+/* sctm_autotune_info -- for an SCTM_PREC_F64EMU context: how many of one network's
+ * FP64-accurate move contractions run on the emulation kernel (*emu) out of those that may
+ * (*eligible), as chosen at creation by timing both kernels once per contraction shape (shapes
+ * below 4 MFLOP stay on the FP64 kernels).  Both are 0 for other forms.  Either pointer may be
+ * NULL.  Errors: EINVAL (NULL ctx, bad network). */
+sctm_status sctm_autotune_info(sctm_ctx* ctx, int network, int* emu, int* eligible);
+
 /* sctm_device_bytes -- device memory held by the context (all of it is allocated at create). */
 size_t sctm_device_bytes(const sctm_ctx* ctx);
 
@@ -207,9 +265,14 @@ size_t sctm_device_bytes(const sctm_ctx* ctx);
  * on the normalisation of the environment tensors; kappa does not.  For inspection and tests. */
 sctm_status sctm_local_values(sctm_ctx* ctx, int network, double* out5);
 
-/* sctm_set_profiling -- on != 0 records CUDA events around every contraction kernel and every
- * SVD (no host synchronisation is added; the events are read after each iteration).  Off by
- * default, or on from creation when the environment variable SCTM_PROFILE=1 is set. */
+/* sctm_set_profiling -- mode 1 records CUDA events around every contraction kernel and every
+ * SVD (no host synchronisation is added; the events are read after each iteration); the
+ * concurrent streams share the GPU, so an event pair then also counts time the launch spent
+ * waiting behind other streams' work.  Mode 2 does the same with the execution serialised (every
+ * step on the caller's stream, the parallel sub-plans and the two networks one after the other),
+ * so each event pair measures that launch alone: per-kernel durations, at the cost of overlap.
+ * Mode 0 (the default, or 1 from creation when the environment variable SCTM_PROFILE=1 is set)
+ * turns both off.  Errors: EINVAL (other modes). */
 sctm_status sctm_set_profiling(sctm_ctx* ctx, int on);
 
 /* sctm_profile -- counters since creation or the last reset (reset != 0 zeroes them after
@@ -227,7 +290,9 @@ enum {
     SCTM_KERNEL_F64 = 0,     /* tiled FP64 kernel (64 x 64 or 32 x 32 tiles, split K)              */
     SCTM_KERNEL_SKINNY = 1,  /* FP64, one output row per thread (N <= 32, K <= 64)                 */
     SCTM_KERNEL_TC = 2,      /* tensor cores, TF32 / BF16 (hi/lo) forms                             */
-    SCTM_KERNEL_F64EMU = 3   /* tensor cores, FP64 emulation                                        */
+    SCTM_KERNEL_F64EMU = 3,  /* tensor cores, FP64 emulation                                        */
+    SCTM_KERNEL_JACOBI = 4,  /* partial SVD: one-CTA Jacobi SVD of the k x k Rayleigh-Ritz matrix   */
+    SCTM_KERNEL_CHOL = 5     /* partial SVD: one-CTA Cholesky-QR pass (flops and bytes not counted)  */
 };
 
 /* sctm_profile_kernel -- the profiling counters of one contraction kernel (SCTM_KERNEL_*) since
@@ -244,9 +309,11 @@ sctm_status sctm_profile_kernel(sctm_ctx* ctx, int kernel, double* ms, long long
  * accumulation, the forms the move contractions of Sec. III take in the mixed modes.  The
  * elementwise error is bounded by c (|X||Y|)_ij with c about 2^-11 (TF32), 2^-8 (BF16), 2^-21
  * (TF32X3), 2^-16 (BF16X3) and the FP64 rounding for SCTM_PREC_FP64.
- *   X, Y, O      device pointers (host pointers: SCTM_EINVAL); caller-owned
+ *   X, Y, O      device pointers of the current device (host pointers, and memory of another
+ *                GPU: SCTM_EINVAL); caller-owned
  *   M, N, K      >= 1, M*N*... each below 2^31 elements
- *   cuda_stream  cudaStream_t (NULL = legacy default); the call synchronises it before
+ *   cuda_stream  cudaStream_t of the current device (NULL = legacy default; a stream of another
+ *                device: SCTM_EINVAL); the call synchronises it before
  *                returning (it allocates and frees its index tables and split-K buffer)
  * Returns SCTM_OK, SCTM_EINVAL, SCTM_ENOMEM, SCTM_ECUDA, or SCTM_ETIMEOUT if a bounded wait of
  * the tensor-core kernel ran out (the result is then invalid). */
@@ -260,17 +327,22 @@ sctm_status sctm_gemm(const double* X, const double* Y, double* O, int M, int N,
  * trigger the device-wide synchronisation a cudaMalloc/cudaFree can imply, or code that runs where
  * the runtime's allocator is unavailable.  The context-based entry points allocate all their
  * buffers in sctm_create; this one uses no context.
- *   X, Y, O      device pointers (host pointers are rejected with SCTM_EINVAL); caller-owned
+ *   X, Y, O      device pointers of the current device (host pointers, and memory of another
+ *                GPU, are rejected with SCTM_EINVAL); caller-owned
  *   M, N, K      >= 1; M*N must not exceed 2^21 (SCTM_EINVAL otherwise)
- *   cuda_stream  cudaStream_t for the work (NULL = legacy default stream)
+ *   cuda_stream  cudaStream_t of the current device for the work (NULL = legacy default stream;
+ *                a stream of another device: SCTM_EINVAL)
  * The split-K partial sums live in one 16 MiB file-scope device array that every device loading
  * the library holds until exit.  All calls share it: calls whose work overlaps on a GPU (several
  * streams or host threads at once) race and must be serialised by the caller.  It keeps the last
  * call's contents, every value read is written earlier by the same call.  The first call on each
- * device looks up the array's device address (cudaGetSymbolAddress, with that device current);
- * make that first call before any stream capture on the device.  No cudaMalloc, cudaFree or
- * allocating library routine is called.  The result is deterministic (fixed summation order).
- * Returns SCTM_OK, SCTM_EINVAL or SCTM_ECUDA (launch or lookup failure). */
+ * device looks up the array's device address (cudaGetSymbolAddress, with that device current)
+ * and keeps it for the life of the process; make that first call before any stream capture on
+ * the device.  A cudaDeviceReset of the device invalidates the kept address: do not call this
+ * entry point on that device again in the same process.  No cudaMalloc, cudaFree or allocating
+ * library routine is called.  The result is deterministic (fixed summation order).
+ * Returns SCTM_OK, SCTM_EINVAL, or SCTM_ECUDA (launch or lookup failure, or a CUDA error left
+ * pending by earlier work, which is then reported without launching and left for its owner). */
 sctm_status sctm_gemm_noalloc(const double* X, const double* Y, double* O, int M, int N, int K,
                               void* cuda_stream);
 

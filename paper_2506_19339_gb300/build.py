@@ -15,7 +15,8 @@ CSRC = os.path.join(PKG, 'csrc')
 INCLUDE = os.path.join(ROOT, 'include')
 BUILD = os.path.join(PKG, '_build')
 LIB = os.path.join(PKG, 'libsctm.so')
-SOURCES = ['kernels.cu', 'ctr_tc.cu', 'ctr_emu.cu', 'psvd.cu', 'engine.cu', 'api.cu', 'noalloc.cu']
+SOURCES = ['kernels.cu', 'ctr_tc.cu', 'ctr_emu.cu', 'psvd.cu', 'engine.cu', 'adjoint.cu',
+           'reduced.cu', 'api.cu', 'noalloc.cu']
 ARCH = ['-gencode', 'arch=compute_103a,code=sm_103a']
 
 

@@ -29,6 +29,13 @@ struct sctm_ctx {
         if (lane_join) cudaEventDestroy(lane_join);
     }
     bool converged = true;
+    // gradient mode (SCTM_GRAD_*) and the adjoint solve's settings and last statistics
+    int grad_mode = SCTM_GRAD_ENV;
+    double adj_tol = 1e-10;
+    int adj_max_mv = 400;
+    int adj_mv[2] = {0, 0};
+    double adj_res[2] = {0.0, 0.0};
+    double* adj_d[2] = {nullptr, nullptr};  // d ln kappa / dA of each network (device)
 };
 
 namespace {
@@ -89,6 +96,17 @@ void check_svd_info(sctm_ctx* c) {
     }
 }
 
+// cold start of one network (and, for the reduced method, the fused site tensor from A)
+void init_network(sctm_ctx* c, int n) {
+    Network& net = c->net[n];
+    if (net.method == SCTM_METHOD_REDUCED) {
+        c->eng->run(net.site);
+        c->eng->init_reduced_env(net);
+    } else {
+        c->eng->init_env(net, c->opts.init_seed);
+    }
+}
+
 }  // namespace
 
 extern "C" {
@@ -139,13 +157,17 @@ sctm_status sctm_create(const double* peps, const double* pepo, int chi, const s
     if (o) opts = *o; else sctm_default_opts(&opts);
     if (chi < 1 || chi > 4096 || opts.D < 1 || opts.p < 1 || opts.d < 1 || opts.batch != 1 ||
         opts.precision < SCTM_PREC_FP64 || opts.precision > SCTM_PREC_F64EMU ||
-        opts.grad_mode != SCTM_GRAD_ENV ||
+        (opts.grad_mode != SCTM_GRAD_ENV && opts.grad_mode != SCTM_GRAD_ADJOINT) ||
         !(opts.svd_cutoff >= 0.0) || opts.D > 64 || opts.d > 64 || opts.p > 64 ||
-        opts.svd_mode < SCTM_SVD_QR || opts.svd_mode > SCTM_SVD_PARTIAL_RANDOM)
+        opts.svd_mode < SCTM_SVD_QR || opts.svd_mode > SCTM_SVD_PARTIAL_RANDOM ||
+        (opts.method != SCTM_METHOD_SPLIT && opts.method != SCTM_METHOD_REDUCED) ||
+        (opts.method == SCTM_METHOD_REDUCED &&
+         (opts.precision != SCTM_PREC_FP64 || opts.grad_mode != SCTM_GRAD_ENV)))
         return SCTM_EINVAL;
     std::unique_ptr<sctm_ctx> c(new sctm_ctx());
     c->opts = opts;
     c->chi = chi;
+    c->grad_mode = opts.grad_mode;
     try {
         cudaStream_t s = (cudaStream_t)opts.cuda_stream;
         c->eng.reset(new Engine(s, opts.precision, opts.svd_cutoff));
@@ -182,16 +204,23 @@ sctm_status sctm_create(const double* peps, const double* pepo, int chi, const s
             net.B = net.A;
             net.O = n == 0 ? view(c->O_dev, {opts.p, opts.p, opts.d, opts.d, opts.d, opts.d})
                            : view(c->Oid_dev, {opts.p, opts.p, 1, 1, 1, 1});
-            e.build_network(net);
+            net.method = opts.method;
+            if (opts.method == SCTM_METHOD_REDUCED)
+                e.build_reduced_network(net);
+            else
+                e.build_network(net);
         }
         if (e.dry) {  // plans only: report success without a usable context
+            const char* da = getenv("SCTM_DRYRUN_ADJOINT");
+            if (da && da[0] == '1')
+                for (int n = 0; n < 2; ++n) e.build_adjoint(c->net[n]);
             c.reset();
             return SCTM_OK;
         }
         cuda_ok(cudaEventCreateWithFlags(&c->lane_fork, cudaEventDisableTiming), "event");
         cuda_ok(cudaEventCreateWithFlags(&c->lane_join, cudaEventDisableTiming), "event");
         cuda_ok(cudaDeviceSynchronize(), "plan build");
-        for (int n = 0; n < 2; ++n) e.init_env(c->net[n], opts.init_seed);
+        for (int n = 0; n < 2; ++n) init_network(c.get(), n);
         cuda_ok(cudaStreamSynchronize(s), "cold start");
         check_cuda("create");
     } catch (const Error& e) {
@@ -215,8 +244,12 @@ sctm_status sctm_set_peps(sctm_ctx* ctx, const double* peps, int reset_env) {
         return SCTM_ENUMERIC;
     }
     launch_copy(ctx->A_stage, ctx->A_dev, na, ctx->eng->stream);
-    if (reset_env)
-        for (int n = 0; n < 2; ++n) ctx->eng->init_env(ctx->net[n], ctx->opts.init_seed);
+    for (int n = 0; n < 2; ++n) {
+        if (reset_env)
+            init_network(ctx, n);
+        else if (ctx->net[n].method == SCTM_METHOD_REDUCED)
+            ctx->eng->run(ctx->net[n].site);  // the fused site tensor follows A
+    }
     check_cuda("set_peps");
     return SCTM_OK;
     API_END(ctx)
@@ -233,7 +266,7 @@ sctm_status sctm_iterate(sctm_ctx* ctx, int max_it, double tol, int* it_done, do
     std::exception_ptr errs[2];
     auto drive = [&](int n) {
         try {
-            Engine::cur_lane = n;
+            Engine::cur_lane = e.serial ? 0 : n;
             Network& net = ctx->net[n];
             cudaStream_t s0 = e.lane().streams[0];
             double dS = INFINITY;
@@ -242,11 +275,28 @@ sctm_status sctm_iterate(sctm_ctx* ctx, int max_it, double tol, int* it_done, do
             // falls, then polish in FP64; convergence is only declared on FP64 iterations.
             const int form = ctx->opts.precision;
             e.set_precision(net, form);
+            // graphs bake in every launch: only for the fixed FP64-accurate forms, and only in the
+            // SVD mode whose warm iteration makes no cuSOLVER call (SCTM_NO_GRAPH=1 disables them)
+            const char* ng = getenv("SCTM_NO_GRAPH");
+            bool use_graph = ctx->opts.svd_mode == SCTM_SVD_PARTIAL_RANDOM &&
+                             (form == SCTM_PREC_FP64 || form == SCTM_PREC_F64EMU) &&
+                             !(ng && ng[0] == '1');
             double best = INFINITY;
             int stall = 0;
             for (it = 1; it <= max_it; ++it) {
-                for (int m = 0; m < 4; ++m) e.run(net.move[m]);
-                e.run(net.spectrum);
+                // warm iterations of a capturable plan replay one captured CUDA graph
+                bool replay = false;
+                if (use_graph && !e.profile && !e.serial && e.all_warm(net)) {
+                    if (!net.graph_exec && !e.capture_iteration(net)) use_graph = false;
+                    replay = net.graph_exec != nullptr && use_graph;
+                }
+                if (replay) {
+                    cuda_ok(cudaGraphLaunch(net.graph_exec, s0), "graph launch");
+                    e.kernel_launches += net.graph_launches;
+                } else {
+                    for (int m = 0; m < 4; ++m) e.run(net.move[m]);
+                    e.run(net.spectrum);
+                }
                 check_cuda("iteration");
                 int err[2] = {0, 0};
                 cuda_ok(cudaMemcpyAsync(&dS, net.dS, sizeof(double), cudaMemcpyDeviceToHost, s0),
@@ -281,13 +331,18 @@ sctm_status sctm_iterate(sctm_ctx* ctx, int max_it, double tol, int* it_done, do
     };
     // each call reports its own device-side failures (timeout, non-finite projector matrix)
     cuda_ok(cudaMemsetAsync(e.dev_err, 0, 2 * sizeof(int), e.stream), "error flags");
-    cuda_ok(cudaEventRecord(ctx->lane_fork, e.stream), "fork");
-    cuda_ok(cudaStreamWaitEvent(e.lanes[1].streams[0], ctx->lane_fork, 0), "fork wait");
-    std::thread t1(drive, 1);
-    drive(0);
-    t1.join();
-    cuda_ok(cudaEventRecord(ctx->lane_join, e.lanes[1].streams[0]), "join");
-    cuda_ok(cudaStreamWaitEvent(e.stream, ctx->lane_join, 0), "join wait");
+    if (e.serial) {  // serialised profiling: both networks on the caller's stream, in turn
+        drive(0);
+        drive(1);
+    } else {
+        cuda_ok(cudaEventRecord(ctx->lane_fork, e.stream), "fork");
+        cuda_ok(cudaStreamWaitEvent(e.lanes[1].streams[0], ctx->lane_fork, 0), "fork wait");
+        std::thread t1(drive, 1);
+        drive(0);
+        t1.join();
+        cuda_ok(cudaEventRecord(ctx->lane_join, e.lanes[1].streams[0]), "join");
+        cuda_ok(cudaStreamWaitEvent(e.stream, ctx->lane_join, 0), "join wait");
+    }
     for (auto& x : errs)
         if (x) std::rethrow_exception(x);
     if (e.profile) e.harvest();
@@ -342,10 +397,27 @@ sctm_status sctm_grad(sctm_ctx* ctx, double* g) {
     API_BEGIN(ctx)
     if (!g) throw Error(SCTM_EINVAL, "NULL g");
     Engine& e = *ctx->eng;
-    finish_local(ctx);
     const int n = (int)peps_size(ctx->opts);
-    launch_grad_combine(ctx->net[0].E.p, ctx->net[0].lnk, ctx->net[1].E.p, ctx->net[1].lnk,
-                        ctx->opts.T, n, ctx->g_dev, e.stream);
+    if (ctx->grad_mode == SCTM_GRAD_ADJOINT) {
+        // d f / d A by implicit differentiation of each network's fixed point; the recompute
+        // iteration runs in FP64 (or its emulation) whatever the context's form
+        cuda_ok(cudaStreamSynchronize(e.stream), "adjoint start");
+        for (int k = 0; k < 2; ++k) {
+            Network& net = ctx->net[k];
+            if (!ctx->adj_d[k]) ctx->adj_d[k] = e.dalloc(n);
+            const int prec = net.precision;
+            if (prec != SCTM_PREC_FP64 && prec != SCTM_PREC_F64EMU)
+                e.set_precision(net, SCTM_PREC_FP64);
+            e.adjoint_lnk_grad(net, ctx->adj_d[k], ctx->adj_tol, ctx->adj_max_mv, &ctx->adj_mv[k],
+                               &ctx->adj_res[k]);
+        }
+        finish_local(ctx);
+        launch_adj_combine(ctx->adj_d[0], ctx->adj_d[1], ctx->opts.T, n, ctx->g_dev, e.stream);
+    } else {
+        finish_local(ctx);
+        launch_grad_combine(ctx->net[0].E.p, ctx->net[0].lnk, ctx->net[1].E.p, ctx->net[1].lnk,
+                            ctx->opts.T, n, ctx->g_dev, e.stream);
+    }
     check_cuda("gradient");
     cuda_ok(cudaMemcpyAsync(g, ctx->g_dev, n * sizeof(double), cudaMemcpyDefault, e.stream),
             "g copy");
@@ -358,9 +430,48 @@ sctm_status sctm_grad(sctm_ctx* ctx, double* g) {
         ctx->err = "kappa <= 0 or not finite";
         return SCTM_ENUMERIC;
     }
+    if (ctx->grad_mode == SCTM_GRAD_ADJOINT &&
+        !(ctx->adj_res[0] <= ctx->adj_tol && ctx->adj_res[1] <= ctx->adj_tol)) {
+        ctx->err = "adjoint linear solve stopped above its tolerance";
+        return SCTM_ENOCONV;
+    }
     if (!ctx->converged) {
         ctx->err = "environment not converged";
         return SCTM_ENOCONV;
+    }
+    return SCTM_OK;
+    API_END(ctx)
+}
+
+sctm_status sctm_set_grad_mode(sctm_ctx* ctx, int mode, double tol, int max_matvecs,
+                               double svd_grad_cutoff) {
+    API_BEGIN(ctx)
+    if (mode != SCTM_GRAD_ENV && mode != SCTM_GRAD_ADJOINT) throw Error(SCTM_EINVAL, "bad mode");
+    if (mode == SCTM_GRAD_ADJOINT && !(svd_grad_cutoff >= 0.0 && svd_grad_cutoff < 1.0))
+        throw Error(SCTM_EINVAL, "svd_grad_cutoff must lie in [0, 1)");
+    if (mode == SCTM_GRAD_ADJOINT && ctx->opts.method != SCTM_METHOD_SPLIT)
+        throw Error(SCTM_EINVAL, "the adjoint gradient is built for the split method only");
+    if (mode == SCTM_GRAD_ADJOINT && !(tol > 0.0 && tol < 1.0 && max_matvecs >= 1))
+        throw Error(SCTM_EINVAL, "adjoint tolerance must lie in (0, 1), max_matvecs >= 1");
+    ctx->grad_mode = mode;
+    if (mode == SCTM_GRAD_ADJOINT) {
+        ctx->adj_tol = tol;
+        ctx->adj_max_mv = max_matvecs;
+        for (int n = 0; n < 2; ++n) ctx->net[n].adj_gcut = svd_grad_cutoff;
+    }
+    return SCTM_OK;
+    API_END(ctx)
+}
+
+sctm_status sctm_adjoint_info(sctm_ctx* ctx, int* matvecs, double* residual) {
+    API_BEGIN(ctx)
+    if (matvecs) {
+        matvecs[0] = ctx->adj_mv[0];
+        matvecs[1] = ctx->adj_mv[1];
+    }
+    if (residual) {
+        residual[0] = ctx->adj_res[0];
+        residual[1] = ctx->adj_res[1];
     }
     return SCTM_OK;
     API_END(ctx)
@@ -487,12 +598,24 @@ sctm_status sctm_iterate_batch(sctm_ctx* const* ctxs, int count, int max_it, dou
     return SCTM_OK;
 }
 
+sctm_status sctm_autotune_info(sctm_ctx* ctx, int network, int* emu, int* eligible) {
+    API_BEGIN(ctx)
+    if (network < 0 || network > 1) throw Error(SCTM_EINVAL, "bad network");
+    if (emu) *emu = ctx->net[network].tuned_emu;
+    if (eligible) *eligible = ctx->net[network].tuned_total;
+    return SCTM_OK;
+    API_END(ctx)
+}
+
 size_t sctm_device_bytes(const sctm_ctx* ctx) { return ctx && ctx->eng ? ctx->eng->bytes : 0; }
 
 sctm_status sctm_set_profiling(sctm_ctx* ctx, int on) {
     API_BEGIN(ctx)
+    if (on < 0 || on > 2) throw Error(SCTM_EINVAL, "profiling mode must be 0, 1 or 2");
+    cuda_ok(cudaStreamSynchronize(ctx->eng->stream), "profiling switch");
     ctx->eng->harvest();
     ctx->eng->profile = on != 0;
+    ctx->eng->serial = on == 2;
     return SCTM_OK;
     API_END(ctx)
 }
@@ -512,7 +635,7 @@ sctm_status sctm_profile(sctm_ctx* ctx, double* ctr_ms, long long* ctr_launches,
     if (reset) {
         e.ctr_ms = e.svd_ms = 0;
         e.ctr_launches = e.ctr_flops = e.svd_calls = 0;
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < Engine::kKernels; ++i) {
             e.kern_ms[i] = 0;
             e.kern_launches[i] = e.kern_flops[i] = e.kern_bytes[i] = 0;
         }
@@ -530,7 +653,7 @@ sctm_status sctm_profile(sctm_ctx* ctx, double* ctr_ms, long long* ctr_launches,
 sctm_status sctm_profile_kernel(sctm_ctx* ctx, int kernel, double* ms, long long* launches,
                                 long long* flops, long long* bytes) {
     API_BEGIN(ctx)
-    if (kernel < SCTM_KERNEL_F64 || kernel > SCTM_KERNEL_F64EMU) throw Error(SCTM_EINVAL, "bad kernel");
+    if (kernel < SCTM_KERNEL_F64 || kernel > SCTM_KERNEL_CHOL) throw Error(SCTM_EINVAL, "bad kernel");
     Engine& e = *ctx->eng;
     e.harvest();
     if (ms) *ms = e.kern_ms[kernel];
@@ -541,13 +664,26 @@ sctm_status sctm_profile_kernel(sctm_ctx* ctx, int kernel, double* ms, long long
     API_END(ctx)
 }
 
-static bool on_device(const void* p) {
+// Device (or managed) memory of device `dev`: memory of another GPU is rejected, since the
+// kernels run on the current device and could not reach it without peer access.
+static bool on_device(const void* p, int dev) {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
+}
+
+static bool stream_on(cudaStream_t s, int dev) {
+    if (s == nullptr || s == cudaStreamLegacy || s == cudaStreamPerThread) return true;
+    int sd = -1;
+    if (cudaStreamGetDevice(s, &sd) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return sd == dev;
 }
 
 sctm_status sctm_gemm(const double* X, const double* Y, double* O, int M, int N, int K,
@@ -557,8 +693,11 @@ sctm_status sctm_gemm(const double* X, const double* Y, double* O, int M, int N,
     if ((long long)M * K >= (1LL << 31) || (long long)K * N >= (1LL << 31) ||
         (long long)M * N >= (1LL << 31))
         return SCTM_EINVAL;
-    if (!on_device(X) || !on_device(Y) || !on_device(O)) return SCTM_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SCTM_ECUDA;
     cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (!on_device(X, dev) || !on_device(Y, dev) || !on_device(O, dev) || !stream_on(s, dev))
+        return SCTM_EINVAL;
     std::vector<int> xm(M), xk(K), yk(K), yn(N), om(M), on(N);
     for (int m = 0; m < M; ++m) xm[m] = m * K, om[m] = m * N;
     for (int k = 0; k < K; ++k) xk[k] = k, yk[k] = k * N;
@@ -589,6 +728,9 @@ sctm_status sctm_gemm(const double* X, const double* Y, double* O, int M, int N,
     a.tile = 64;
     a.splits = a.tc_splits = splits;
     a.kchunk = a.tc_kchunk = kchunk;
+    // test switch: the first bounded wait of each tensor-core CTA gives up at once
+    if (const char* tw = getenv("SCTM_TEST_FIRST_WAIT_ZERO"))
+        if (tw[0] == '1') a.first_wait_limit = 0;
     std::vector<void*> bufs;
     auto dev_copy = [&](const std::vector<int>& v) -> int* {
         void* p = nullptr;

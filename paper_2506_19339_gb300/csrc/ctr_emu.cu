@@ -8,9 +8,18 @@
 // tensor-memory accumulator (8 levels x 64 FP32 columns = the whole 512-column tensor memory):
 // a level sum over K blocks of 128 is an integer below 8 * 127^2 * 128 < 2^24, so FP32
 // accumulation in the tensor core is exact.  After each K block the eight level sums are read
-// back (tcgen05.ld) and added into FP64 registers with their weights 2^(-7L), and the block's
-// MMAs restart the accumulators.  FP64 arithmetic is spent once per operand element (the digit
-// split) and once per output element and level per 128 K, not per multiply-add.
+// back (tcgen05.ld), combined exactly in 64-bit integers (levels 0-3 and 4-7 into one integer
+// each, below 2^46) and added into FP64 registers with two FMAs, and the block's MMAs restart
+// the accumulators.  FP64 arithmetic is spent once per operand element (the digit split) and
+// twice per output element per 128 K, not per multiply-add.
+//
+// Data movement: the digit split writes, per (row tile, K chunk of 32), the eight digit tiles
+// contiguously in the shared-memory image order (K-major, no swizzle), so one K chunk of the A
+// operand is a single 64 KB bulk copy and of the B operand a single 32 KB one.  The contraction
+// kernel keeps two such chunks in flight (cp.async.bulk into a two-stage shared-memory ring,
+// completion counted on an mbarrier per stage), one thread issues the 72 MMAs of a chunk
+// (36 digit pairs x 2 K-steps of 16) as soon as its stage has landed, and refills the stage
+// once a tcgen05.commit reports those MMAs done, so loads overlap the tensor-core work.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -22,13 +31,17 @@ namespace sctm {
 
 namespace {
 
-constexpr int EBM = 128, EBN = 64, EBK = 32, ENT = 128;
+constexpr int EBM = 128, EBN = 64, EBK = 32, ENT = 256;
+constexpr int kColsPerThread = EBN / 2;  // warps w and w + 4 share TMEM lanes 32 (w % 4)..
 constexpr int kDigits = 8;                   // slices per operand element
 constexpr int kLevels = 8;                   // levels L = t + u - 2 = 0..7
 constexpr int kBlockChunks = 4;              // K block of 4 x 32 = 128 between read-backs
 constexpr int kEmuTmemCols = kLevels * EBN;  // 512
 constexpr long long kEmuSpinLimit = 1LL << 20;
 constexpr uint32_t kSliceA = EBM * EBK * 2, kSliceB = EBN * EBK * 2;  // bytes per BF16 slice tile
+constexpr uint32_t kChunkA = kDigits * kSliceA, kChunkB = kDigits * kSliceB;  // 64 KB, 32 KB
+constexpr uint32_t kStageBytes = kChunkA + kChunkB;
+constexpr int kStages = 2;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -44,8 +57,9 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
 // kind::f16 instruction descriptor: D = F32, A = B = BF16, K-major, N = 64, M = 128
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((EBN >> 3) << 17) | ((EBM >> 4) << 24);
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    for (long long i = 0; i < kEmuSpinLimit; ++i) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
+                                          long long limit = kEmuSpinLimit) {
+    for (long long i = 0; i < limit; ++i) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -57,6 +71,29 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
         if (done) return true;
     }
     return false;
+}
+
+// 2^e as a double for a frexp exponent of a finite double (e in [-1073, 1024]): built from its
+// bits in one or two normal factors, so that a product by it is the exact scaling ldexp would do
+// (up to the rounding of a subnormal result)
+__device__ __forceinline__ double pow2_lo(int e) {  // e in [-1022, 1023]
+    return __longlong_as_double((long long)(e + 1023) << 52);
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+// one bulk (non-tensor) copy global -> shared, completion counted on the mbarrier in bytes;
+// both addresses 16-byte aligned and the size a multiple of 16
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes,
+                                          uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
 }
 
 __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t da, uint64_t db, uint32_t acc) {
@@ -111,8 +148,9 @@ __global__ void __launch_bounds__(256) emu_rowexp_kernel(const CtrLaunch a, int*
     }
 }
 
-// Digit split of both operands into kDigits BF16 slices, tiles in shared-memory image order
-// (slice-major: all tiles of digit 1, then digit 2, ...).  A block per tile.
+// Digit split of both operands into kDigits BF16 slices, tiles in shared-memory image order;
+// tile t (over batch, row tile, K chunk) holds its kDigits digit tiles contiguously, digit d at
+// (t kDigits + d) x (tile bytes).  A block per tile.
 __global__ void __launch_bounds__(256) emu_pack_kernel(const CtrLaunch a, const int* ex,
                                                        const int* ey) {
     const int nkc = (a.K + EBK - 1) / EBK;
@@ -127,8 +165,8 @@ __global__ void __launch_bounds__(256) emu_pack_kernel(const CtrLaunch a, const 
         const long long br = t / nkc;
         const int nrt = isY ? (a.N + EBN - 1) / EBN : (a.M + EBM - 1) / EBM;
         const int r = (int)(br % nrt), b = (int)(br / nrt);
-        const long long slice = (isY ? ty : tx) * (long long)(rows * EBK);
-        unsigned short* dst = (isY ? yp : xp) + t * (long long)(rows * EBK);
+        const long long slice = rows * EBK;
+        unsigned short* dst = (isY ? yp : xp) + t * (long long)(kDigits * rows * EBK);
         for (int e = threadIdx.x; e < rows * EBK; e += blockDim.x) {
             int rr, kk;
             tile_pos_bf16(e, rr, kk);
@@ -160,12 +198,10 @@ __global__ void __launch_bounds__(256) emu_pack_kernel(const CtrLaunch a, const 
     }
 }
 
-__global__ void __launch_bounds__(ENT) emu_ctr_kernel(const CtrLaunch a, const int* ex,
-                                                      const int* ey) {
-    extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char* sa = smem;                       // kDigits A slices
-    unsigned char* sb = smem + kDigits * kSliceA;   // kDigits B slices
-    __shared__ __align__(8) unsigned long long mbar;
+__global__ void __launch_bounds__(ENT, 1) emu_ctr_kernel(const CtrLaunch a, const int* ex,
+                                                         const int* ey) {
+    extern __shared__ __align__(1024) unsigned char smem[];  // kStages x (A chunk, B chunk)
+    __shared__ __align__(8) unsigned long long full_bar[kStages], mma_bar[kStages], acc_bar, drain_bar;
     __shared__ uint32_t tmem_base;
     __shared__ int s_fail;
 
@@ -173,9 +209,19 @@ __global__ void __launch_bounds__(ENT) emu_ctr_kernel(const CtrLaunch a, const i
     const int m0 = blockIdx.y * EBM, n0 = blockIdx.x * EBN;
     const int z = blockIdx.z;
     const int b = z / a.splits, sp = z % a.splits;
+    const int kbeg = sp * a.kchunk;
+    const int kend = min(a.K, kbeg + a.kchunk);
+    const int nch = kend > kbeg ? (kend - kbeg + EBK - 1) / EBK : 0;  // K chunks of this CTA
+    const int cfirst = kbeg / EBK;                                    // kchunk is a multiple of EBK
+    const int nkc = (a.K + EBK - 1) / EBK;
     if (tid == 0) {
         s_fail = 0;
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+        for (int s = 0; s < kStages; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full_bar[s])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mma_bar[s])));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&acc_bar)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&drain_bar)));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -188,114 +234,143 @@ __global__ void __launch_bounds__(ENT) emu_ctr_kernel(const CtrLaunch a, const i
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_base;
-    const uint32_t bar = smem_u32(&mbar);
-
-    const int kbeg = sp * a.kchunk;
-    const int kend = min(a.K, kbeg + a.kchunk);
-    const int nkc = (a.K + EBK - 1) / EBK;
-    const long long xtiles = emu_tiles_x(a), ytiles = emu_tiles_y(a);
+    const long long xt0 = ((long long)b * gridDim.y + blockIdx.y) * nkc + cfirst;
+    const long long yt0 = ((long long)b * gridDim.x + blockIdx.x) * nkc + cfirst;
+    const unsigned char* gx = reinterpret_cast<const unsigned char*>(a.pack_x);
+    const unsigned char* gy = reinterpret_cast<const unsigned char*>(a.pack_y);
     constexpr uint32_t LBO = 128, SBO = (EBK * 2 / 16) * 128;
-    uint32_t phase = 0, fail_phase = 0;
-    bool ok = true;
-    double acc[EBN];
-#pragma unroll
-    for (int j = 0; j < EBN; ++j) acc[j] = 0.0;
 
-    for (int kb = kbeg; kb < kend && ok; kb += kBlockChunks * EBK) {
-        const int kbend = min(kend, kb + kBlockChunks * EBK);
-        bool fresh = true;  // the block's first MMA into each level starts that accumulator
-        for (int k0 = kb; k0 < kbend && ok; k0 += EBK) {
-            {
-                const int kc = k0 / EBK;
-                const long long xt = ((long long)b * gridDim.y + blockIdx.y) * nkc + kc;
-                const long long yt = ((long long)b * gridDim.x + blockIdx.x) * nkc + kc;
+    // producer state (thread 0): phases of the stage barriers and the loads still in flight
+    uint32_t fph[kStages] = {0, 0}, mph[kStages] = {0, 0}, aph = 0;
+    bool pending[kStages] = {false, false};
+    auto issue_load = [&](int c, int s) {
+        const uint32_t fb = smem_u32(&full_bar[s]);
+        const uint32_t dst = smem_u32(smem + (size_t)s * kStageBytes);
+        mbar_expect_tx(fb, kStageBytes);
+        bulk_load(dst, gx + (xt0 + c) * (long long)kChunkA, kChunkA, fb);
+        bulk_load(dst + kChunkA, gy + (yt0 + c) * (long long)kChunkB, kChunkB, fb);
+        pending[s] = true;
+    };
+    if (tid == 0)
+        for (int c = 0; c < nch && c < kStages; ++c) issue_load(c, c);
+
+    // warp w reads TMEM lanes 32 (w % 4) .. + 31 (tile rows) and columns (w / 4) x 32 .. + 31
+    const int quarter = warp & 3, colhalf = warp >> 2;
+    double acc[kColsPerThread];
 #pragma unroll
-                for (int d = 0; d < kDigits; ++d) {
-                    const uint4* gx = reinterpret_cast<const uint4*>(
-                        reinterpret_cast<const unsigned char*>(a.pack_x) +
-                        ((long long)d * xtiles + xt) * kSliceA);
-                    const uint4* gy = reinterpret_cast<const uint4*>(
-                        reinterpret_cast<const unsigned char*>(a.pack_y) +
-                        ((long long)d * ytiles + yt) * kSliceB);
-                    uint4* dx = reinterpret_cast<uint4*>(sa + d * kSliceA);
-                    uint4* dy = reinterpret_cast<uint4*>(sb + d * kSliceB);
-                    for (int i = tid; i < (int)(kSliceA / 16); i += ENT) dx[i] = gx[i];
-                    for (int i = tid; i < (int)(kSliceB / 16); i += ENT) dy[i] = gy[i];
-                }
-            }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncthreads();
-            if (tid == 0) {
+    for (int j = 0; j < kColsPerThread; ++j) acc[j] = 0.0;
+
+    for (int c = 0; c < nch; ++c) {
+        const int s = c % kStages;
+        const bool fresh = (c % kBlockChunks) == 0;  // first chunk of a K block
+        if (tid == 0 && !s_fail) {
+            const long long lim =
+                (c == 0 && a.first_wait_limit >= 0) ? a.first_wait_limit : kEmuSpinLimit;
+            if (!mbar_wait(smem_u32(&full_bar[s]), fph[s], lim)) {
+                s_fail = 1;
+            } else {
+                fph[s] ^= 1u;
+                pending[s] = false;
                 asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t sa = smem_u32(smem + (size_t)s * kStageBytes);
+                const uint32_t sb = sa + kChunkA;
                 for (int da = 0; da < kDigits; ++da) {
                     for (int db = 0; db + da < kLevels; ++db) {
-                        const int L = da + db;
-                        const uint32_t ta = tmem + (uint32_t)(L * EBN);
+                        const uint32_t ta = tmem + (uint32_t)((da + db) * EBN);
 #pragma unroll
-                        for (int s = 0; s < EBK / 16; ++s) {
-                            const uint32_t step = s * 256;  // 16 BF16 along K = 2 core matrices
-                            const uint64_t dA = smem_desc(smem_u32(sa + da * kSliceA) + step, LBO, SBO);
-                            const uint64_t dB = smem_desc(smem_u32(sb + db * kSliceB) + step, LBO, SBO);
-                            // first MMA into level L in this block: da == 0 holds every level's
-                            // first pair (db = L), issued before any other pair of that level
-                            mma_bf16(ta, dA, dB, (fresh && da == 0 && s == 0) ? 0u : 1u);
+                        for (int st = 0; st < EBK / 16; ++st) {
+                            const uint32_t step = st * 256;  // 16 BF16 along K = 2 core matrices
+                            const uint64_t dA = smem_desc(sa + da * kSliceA + step, LBO, SBO);
+                            const uint64_t dB = smem_desc(sb + db * kSliceB + step, LBO, SBO);
+                            // a level's first MMA of the K block (da == 0, st == 0) starts it
+                            mma_bf16(ta, dA, dB, (fresh && da == 0 && st == 0) ? 0u : 1u);
                         }
                     }
                 }
                 asm volatile(
                     "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                        bar)
+                        smem_u32(&mma_bar[s]))
+                    : "memory");
+                if (c + kStages < nch) {
+                    // the stage is free once these MMAs have read it
+                    if (!mbar_wait(smem_u32(&mma_bar[s]), mph[s])) {
+                        s_fail = 1;
+                    } else {
+                        mph[s] ^= 1u;
+                        issue_load(c + kStages, s);
+                    }
+                }
+            }
+        }
+        if ((c % kBlockChunks) == kBlockChunks - 1 || c == nch - 1) {
+            // end of a K block: the level sums are complete once every MMA issued so far is done
+            if (tid == 0 && !s_fail) {
+                asm volatile(
+                    "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                        smem_u32(&acc_bar))
                     : "memory");
             }
-            fresh = false;
-            if (!mbar_wait(bar, phase)) {
-                ok = false;
-                s_fail = 1;
-                fail_phase = phase;
-            }
-            phase ^= 1u;
             __syncthreads();
-            if (s_fail) ok = false;
-        }
-        if (!ok) break;
-        // read back the eight level sums of this K block into the FP64 accumulators
-        asm volatile("tcgen05.fence::after_thread_sync;");
-#pragma unroll 1
-        for (int L = 0; L < kLevels; ++L) {
-            const double w = ldexp(1.0, -7 * (L + 2));
+            if (s_fail) break;
+            if (!mbar_wait(smem_u32(&acc_bar), aph)) atomicExch(&s_fail, 1);
+            aph ^= 1u;
+            __syncthreads();
+            if (s_fail) break;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            // level sums are exact integers (|S| < 2^24): combine levels 0-3 and 4-7 exactly in
+            // 64-bit integers (S_0 2^21 + S_1 2^14 + S_2 2^7 + S_3, below 2^46), then two FP64
+            // FMAs with weights 2^-35 and 2^-63
 #pragma unroll
-            for (int c0 = 0; c0 < EBN; c0 += 16) {
-                uint32_t r[16];
-                const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(L * EBN + c0);
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, "
-                    "%9, %10, %11, %12, %13, %14, %15}, [%16];"
-                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
-                      "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
-                      "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-                    : "r"(taddr));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            for (int cb = 0; cb < kColsPerThread; cb += 8) {
 #pragma unroll
-                for (int j = 0; j < 16; ++j) acc[c0 + j] = fma((double)__uint_as_float(r[j]), w, acc[c0 + j]);
+                for (int half = 0; half < 2; ++half) {  // levels 0-3, then 4-7
+                    uint32_t r[4][8];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int L = 4 * half + q;
+                        const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) +
+                                               (uint32_t)(L * EBN + colhalf * kColsPerThread + cb);
+                        asm volatile(
+                            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, "
+                            "%7}, [%8];"
+                            : "=r"(r[q][0]), "=r"(r[q][1]), "=r"(r[q][2]), "=r"(r[q][3]),
+                              "=r"(r[q][4]), "=r"(r[q][5]), "=r"(r[q][6]), "=r"(r[q][7])
+                            : "r"(taddr));
+                    }
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    const double w = half ? 0x1p-63 : 0x1p-35;
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        long long v = 0;
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            v = v * 128 + (long long)__float2int_rn(__uint_as_float(r[q][j]));
+                        acc[cb + j] = fma((double)v, w, acc[cb + j]);
+                    }
+                }
             }
+            // the next block's MMAs overwrite the accumulators only after every warp has read them
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncthreads();
+            asm volatile("tcgen05.fence::after_thread_sync;");
         }
-        // the next block's MMAs overwrite the accumulators only after every warp has read them
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;");
     }
 
-    if (ok) {
-        const int m = m0 + warp * 32 + lane;
+    if (!s_fail) {
+        const int m = m0 + quarter * 32 + lane;
         if (m < a.M) {
+            // exponents of frexp on finite doubles lie in [-1073, 1024]: split each into two
+            // normal powers of two
             const int erow = ex[(long long)b * a.M + m];
+            const double er1 = pow2_lo(erow / 2), er2 = pow2_lo(erow - erow / 2);
             const double rs = a.rowscale ? a.rowscale[m] : 1.0;
             const long long obo = a.ob ? a.ob[b] : 0;
 #pragma unroll
-            for (int j = 0; j < EBN; ++j) {
-                const int n = n0 + j;
+            for (int j = 0; j < kColsPerThread; ++j) {
+                const int n = n0 + colhalf * kColsPerThread + j;
                 if (n >= a.N) continue;
-                const double v = ldexp(acc[j], erow + ey[(long long)b * a.N + n]);
+                const int ec = ey[(long long)b * a.N + n];
+                const double v = acc[j] * er1 * pow2_lo(ec / 2) * er2 * pow2_lo(ec - ec / 2);
                 if (a.splits > 1) {
                     a.partial[((long long)z * a.M + m) * a.N + n] = v;
                 } else {
@@ -305,9 +380,18 @@ __global__ void __launch_bounds__(ENT) emu_ctr_kernel(const CtrLaunch a, const i
                 }
             }
         }
-    } else {
-        mbar_wait(bar, fail_phase);  // drain (bounded) before the tensor memory is freed
-        if (tid == 0 && a.err) atomicExch(a.err, 1);
+    } else if (tid == 0) {
+        // drain (bounded) before the shared memory and the tensor memory are released: the bulk
+        // copies still in flight, then every MMA this thread issued (a commit to a barrier used
+        // for nothing else arrives once all of them have completed)
+        for (int s = 0; s < kStages; ++s)
+            if (pending[s]) mbar_wait(smem_u32(&full_bar[s]), fph[s]);
+        asm volatile(
+            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_u32(&drain_bar))
+            : "memory");
+        mbar_wait(smem_u32(&drain_bar), 0u);
+        if (a.err) atomicExch(a.err, 1);
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
@@ -335,8 +419,8 @@ void launch_ctr_emu(const CtrLaunch& a, cudaStream_t s) {
         emu_pack_kernel<<<(int)std::min<long long>(std::max<long long>(tiles, 1), 8192), 256, 0, s>>>(
             a, ex, ey);
     }
-    // > 114 KB of shared memory: one CTA per SM, which owns the whole tensor memory
-    const size_t smem = std::max<size_t>(kDigits * (kSliceA + kSliceB), 120 * 1024);
+    // two stages of 96 KB: one CTA per SM, which owns the whole tensor memory
+    const size_t smem = (size_t)kStages * kStageBytes;
     static std::once_flag once;
     std::call_once(once, [&] {
         cudaFuncSetAttribute(emu_ctr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

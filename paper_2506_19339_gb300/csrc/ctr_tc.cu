@@ -99,8 +99,9 @@ __device__ __forceinline__ void tile_pos(int e, int& r, int& k) {
     k = chunk * T + kin;
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    for (long long i = 0; i < kSpinLimit; ++i) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
+                                          long long limit = kSpinLimit) {
+    for (long long i = 0; i < limit; ++i) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -385,7 +386,8 @@ __global__ void __launch_bounds__(TNT) ctr_tc_kernel(const CtrLaunch a) {
         }
         first = false;
         // every thread waits for the MMAs before the tiles are overwritten
-        if (!mbar_wait(bar, phase)) {
+        if (!mbar_wait(bar, phase, (k0 == kbeg && a.first_wait_limit >= 0) ? a.first_wait_limit
+                                                                              : kSpinLimit)) {
             ok = false;
             s_fail = 1;
             fail_phase = phase;

@@ -12,6 +12,7 @@
 #include <cstring>
 #include <functional>
 #include <map>
+#include <tuple>
 
 namespace sctm {
 
@@ -58,16 +59,17 @@ Ten permute(const Ten& t, const std::vector<int>& perm) {
 // ---------------------------------------------------------------------------------------------
 // steps
 // ---------------------------------------------------------------------------------------------
-enum { KIND_CTR = 0, KIND_SVD = 1 };
+enum { KIND_CTR = 0, KIND_SVD = 1, KIND_FN = 2 };
 
 struct CtrStep : Step {
     CtrLaunch a;
     size_t partial_need = 0;
     long long flops = 0;
     bool mixed_ok = false;  // may run in a tensor-core form
+    bool emu_ok = false;    // SCTM_PREC_F64EMU runs it on the emulation kernel (autotune)
     void run(Engine& e) override {
         const int e0 = e.profile ? e.record(sid) : -1;
-        launch_ctr(a, e.lane().streams[sid]);
+        launch_ctr(a, e.strm(sid));
         const bool tc = a.precision != SCTM_PREC_FP64;
         const int splits = tc ? a.tc_splits : (ctr_is_skinny(a) ? 1 : a.splits);
         e.kernel_launches += (splits > 1 ? 2 : 1) + (tc ? 2 : 0);
@@ -89,7 +91,7 @@ struct SvdStep : Step {
         cusolverStatus_t st;
         if (e.svd_mode == SCTM_SVD_POLAR) {
             double herr = 0.0;
-            st = cusolverDnXgesvdp(e.lane().solver[sid], e.solver_params,
+            st = cusolverDnXgesvdp(e.solv(sid), e.solver_params,
                                    vectors ? CUSOLVER_EIG_MODE_VECTOR : CUSOLVER_EIG_MODE_NOVECTOR, 1,
                                    n, n, CUDA_R_64F, M, n, CUDA_R_64F, S, CUDA_R_64F, U, n,
                                    CUDA_R_64F, V, n, CUDA_R_64F, net->svd_dwork[sid],
@@ -97,7 +99,7 @@ struct SvdStep : Step {
                                    net->svd_info + info_idx, &herr);
         } else {  // gesvd writes V^T into V
             const signed char job = vectors ? 'S' : 'N';
-            st = cusolverDnDgesvd(e.lane().solver[sid], job, job, n, n, M, n, S, U, n, V, n,
+            st = cusolverDnDgesvd(e.solv(sid), job, job, n, n, M, n, S, U, n, V, n,
                                   (double*)net->svd_dwork[sid], net->svd_lwork, net->svd_rwork[sid],
                                   net->svd_info + info_idx);
         }
@@ -121,7 +123,9 @@ struct PartialSvdStep : Step {
     int random_steps = 0;     // > 0: cold solve = seed + this many warm steps instead of gesvd
     void run(Engine& e) override {
         const int e0 = e.profile ? e.record(sid) : -1;
-        if (is_warm) {
+        if (e.force_full_svd) {
+            e.run_sub(cold);  // full singular basis, for the adjoint's recompute
+        } else if (is_warm) {
             e.run_sub(warm);
         } else if (random_steps > 0 && can_warm) {
             e.run_sub(seed);
@@ -136,10 +140,16 @@ struct PartialSvdStep : Step {
 
 struct FnStep : Step {
     std::function<void(cudaStream_t)> f;
-    explicit FnStep(std::function<void(cudaStream_t)> g) : f(std::move(g)) {}
+    int prof = -1;  // SCTM_KERNEL_* whose profiling counters this launch feeds (-1: none)
+    explicit FnStep(std::function<void(cudaStream_t)> g, int p = -1) : f(std::move(g)), prof(p) {}
     void run(Engine& e) override {
-        f(e.lane().streams[sid]);
+        const int e0 = (e.profile && prof >= 0) ? e.record(sid) : -1;
+        f(e.strm(sid));
         e.kernel_launches += 1;
+        if (e0 >= 0) {
+            e.record_done(sid, KIND_FN, 0, e0);
+            e.lane().ev_recs[sid].back().variant = prof;
+        }
     }
 };
 
@@ -148,10 +158,22 @@ struct ParallelStep : Step {
     cudaEvent_t fork_ev = nullptr;
     std::vector<cudaEvent_t> join_ev;
     void run(Engine& e) override {
+        if (e.serial) {
+            for (auto& p : sub) e.run_sub(p);
+            return;
+        }
         Engine::Lane& L = e.lane();
         const int lane = Engine::cur_lane;
-        cudaEventRecord(fork_ev, L.streams[0]);
+        cudaEventRecord(fork_ev, e.strm(0));
         for (size_t i = 0; i < sub.size(); ++i) cudaStreamWaitEvent(L.streams[i + 1], fork_ev, 0);
+        if (Engine::capturing) {  // recording a graph: the sub-plans become parallel branches
+            for (auto& p : sub) e.run_sub(p);
+            for (size_t i = 0; i < sub.size(); ++i) {
+                cudaEventRecord(join_ev[i], L.streams[i + 1]);
+                cudaStreamWaitEvent(e.strm(0), join_ev[i], 0);
+            }
+            return;
+        }
         std::vector<std::exception_ptr> errs(sub.size());
         std::vector<std::thread> th;
         for (size_t i = 1; i < sub.size(); ++i)
@@ -171,7 +193,7 @@ struct ParallelStep : Step {
         for (auto& t : th) t.join();
         for (size_t i = 0; i < sub.size(); ++i) {
             cudaEventRecord(join_ev[i], L.streams[i + 1]);
-            cudaStreamWaitEvent(L.streams[0], join_ev[i], 0);
+            cudaStreamWaitEvent(e.strm(0), join_ev[i], 0);
         }
         for (auto& x : errs)
             if (x) std::rethrow_exception(x);
@@ -182,6 +204,7 @@ struct ParallelStep : Step {
 // engine
 // ---------------------------------------------------------------------------------------------
 thread_local int Engine::cur_lane = 0;
+thread_local bool Engine::capturing = false;
 
 Engine::Engine(cudaStream_t s, int prec, double cut) : stream(s), precision(prec), cutoff(cut) {
     const char* dr = getenv("SCTM_DRYRUN");
@@ -200,6 +223,8 @@ Engine::Engine(cudaStream_t s, int prec, double cut) : stream(s), precision(prec
         }
     }
     SOLVER_OK(cusolverDnCreateParams(&solver_params));
+    for (int l = 0; l < kLanes; ++l)
+        CUDA_OK(cudaStreamCreateWithFlags(&cap_stream[l], cudaStreamNonBlocking));
     const char* pf = getenv("SCTM_PROFILE");
     profile = pf && pf[0] == '1';
 }
@@ -208,6 +233,8 @@ Engine::~Engine() {
     for (int l = 0; l < kLanes; ++l)
         for (int i = 0; i < kStreams; ++i)
             if (lanes[l].streams[i]) cudaStreamSynchronize(lanes[l].streams[i]);
+    for (int l = 0; l < kLanes; ++l)
+        if (cap_stream[l]) cudaStreamDestroy(cap_stream[l]);
     for (void* p : allocs_) cudaFree(p);
     for (cudaEvent_t ev : owned_events_) cudaEventDestroy(ev);
     for (int l = 0; l < kLanes; ++l) {
@@ -229,7 +256,7 @@ int Engine::record(int sid) {
         L.ev_pool[sid].push_back(ev);
     }
     const int idx = (int)L.ev_used[sid]++;
-    cudaEventRecord(L.ev_pool[sid][idx], L.streams[sid]);
+    cudaEventRecord(L.ev_pool[sid][idx], strm(sid));
     return idx;
 }
 
@@ -280,9 +307,12 @@ void Engine::harvest() {
                     kern_flops[r.variant] += r.flops;
                     kern_bytes[r.variant] +=
                         8LL * r.nb * ((long long)r.m * r.k + (long long)r.k * r.n + (long long)r.m * r.n);
-                } else {
+                } else if (r.kind == KIND_SVD) {
                     svd_ms += ms;
                     svd_calls += 1;
+                } else {
+                    kern_ms[r.variant] += ms;
+                    kern_launches[r.variant] += 1;
                 }
             }
             L.ev_recs[sid].clear();
@@ -299,7 +329,13 @@ double* Engine::dalloc(long long n) {
     allocs_.push_back(p);
     bytes += std::max<long long>(n, 1) * sizeof(double);
     CUDA_OK(cudaMemset(p, 0, std::max<long long>(n, 1) * sizeof(double)));
+    sizes_[(const double*)p] = std::max<long long>(n, 1);
     return (double*)p;
+}
+
+long long Engine::size_of(const double* base) const {
+    auto it = sizes_.find(base);
+    return it == sizes_.end() ? 0 : it->second;
 }
 
 int* Engine::ialloc(const std::vector<int>& host) {
@@ -365,7 +401,7 @@ static std::vector<int> offsets(const std::string& labs, const std::map<char, in
 }
 
 Ten Engine::ctr(Network& net, Plan& P, const std::string& spec, const Ten& X, const Ten& Y,
-                const Ten* out, const double* rowscale, const double* colscale) {
+                const Ten* out, const double* rowscale, const double* colscale, bool accumulate) {
     const size_t comma = spec.find(','), arrow = spec.find("->");
     if (comma == std::string::npos || arrow == std::string::npos)
         throw Error(SCTM_EINVAL, "bad contraction spec " + spec);
@@ -475,10 +511,41 @@ Ten Engine::ctr(Network& net, Plan& P, const std::string& spec, const Ten& X, co
     const int max_splits = mixed_build ? std::max(a.splits, a.tc_splits) : a.splits;
     if (max_splits > 1) st->partial_need = (size_t)a.nb * max_splits * (size_t)a.M * a.N;
     st->flops = 2LL * a.M * a.N * (long long)a.K * a.nb;
+    // SCTM_PLAN_DUMP=<file>: append "d_int stream M N K nb mixed_ok spec" per contraction built
+    // (a diagnostic of the plan's shape mix; works with SCTM_DRYRUN=1 on a machine without a GPU)
+    if (const char* pd = getenv("SCTM_PLAN_DUMP")) {
+        if (pd[0]) {
+            if (FILE* fp = fopen(pd, "a")) {
+                fprintf(fp, "%d %d %d %d %d %d %d %s\n", net.d, cur_stream, a.M, a.N, a.K, a.nb,
+                        mixed_build ? 1 : 0, spec.c_str());
+                fclose(fp);
+            }
+        }
+    }
+    a.accumulate = accumulate ? 1 : 0;
     net.ctr_steps.push_back(st.get());
     net.splitk_need[cur_stream] = std::max(net.splitk_need[cur_stream], st->partial_need);
     push(P, std::move(st));
+    if (tape && !in_proj) {
+        TapeOp op;
+        op.kind = TapeOp::CTR;
+        op.spec = spec;
+        op.X = X;
+        op.Y = Y;
+        op.O = O;
+        tape->push_back(op);
+    }
     return O;
+}
+
+void Engine::assign_workspace(Network& net, size_t first) {
+    size_t need = 0;
+    for (size_t i = first; i < net.ctr_steps.size(); ++i)
+        need = std::max(need, net.ctr_steps[i]->partial_need);
+    if (need == 0) return;
+    double* ws = dalloc((long long)need);
+    for (size_t i = first; i < net.ctr_steps.size(); ++i)
+        if (net.ctr_steps[i]->partial_need > 0) net.ctr_steps[i]->a.partial = ws;
 }
 
 Engine::PPair Engine::projector(Network& net, Plan& P, const Ten& U, const Ten& L,
@@ -519,6 +586,7 @@ Engine::PPair Engine::projector(Network& net, Plan& P, const Ten& U, const Ten& 
             s *= rdims[i];
         }
     }
+    ++in_proj;  // the contractions below are the PROJ record's, not separate tape entries
     ctr(net, P, Llab + "," + labels + "->" + rlL + rl, L, U, &M);
     const bool mixed = mixed_build;
     mixed_build = false;  // the SVD and the projector formation stay FP64
@@ -527,6 +595,11 @@ Engine::PPair Engine::projector(Network& net, Plan& P, const Ten& U, const Ten& 
     double* Vs = dalloc((long long)n * n);
     // V layout: columns (gesvdp, partial SVD) or rows = V^T (gesvd)
     const int vt = svd_mode == SCTM_SVD_QR ? 1 : 0;
+    // where the full right singular basis is after a full (gesvd / gesvdp) solve, for the
+    // reverse mode: V^T rows, and the columns that the sign gauge may have flipped
+    double* VT_full = vt ? Vs : nullptr;
+    double* V_cols = vt ? nullptr : Vs;
+    int kc_full = vt ? 0 : n;
     auto make_svd = [&](double* Vout) {
         auto sv = std::make_unique<SvdStep>();
         sv->M = M.p;
@@ -565,6 +638,9 @@ Engine::PPair Engine::projector(Network& net, Plan& P, const Ten& U, const Ten& 
             const int kc = ps->can_warm ? k : chi;
             push(C, std::make_unique<FnStep>(
                         [=](cudaStream_t s) { launch_vt_columns(VT, Vs, n, kc, s); }));
+            VT_full = VT;
+            V_cols = Vs;
+            kc_full = kc;
         }
         if (ps->can_warm) {
             Plan& W = ps->warm;
@@ -608,7 +684,8 @@ Engine::PPair Engine::projector(Network& net, Plan& P, const Ten& U, const Ten& 
                     ctr(net, W, "ac,ad->cd", x, x, &Gt);
                     const double sh = pass < 2 ? shift : 0.0;
                     push(W, std::make_unique<FnStep>(
-                                [=](cudaStream_t s) { launch_chol_orth(G, k, sh, Tm, Xg, s); }));
+                                [=](cudaStream_t s) { launch_chol_orth(G, k, sh, Tm, Xg, s); },
+                                SCTM_KERNEL_CHOL));
                     ctr(net, W, "ac,cd->ad", x, Tt, &y);
                 }
             };
@@ -621,7 +698,7 @@ Engine::PPair Engine::projector(Network& net, Plan& P, const Ten& U, const Ten& 
             ctr(net, W, "ac,ad->cd", Zbt, Qzt, &Bt);  // B = Z^T Q_z = Q_y^T M Q_z
             push(W, std::make_unique<FnStep>([=](cudaStream_t s) {
                 launch_jacobi_svd(R1, k, S, Ur, Wr, np->svd_info + info_idx, Vg, s);
-            }));
+            }, SCTM_KERNEL_JACOBI));
             ctr(net, W, "ac,cd->ad", Qyt, Urt, &Ut);  // U = Q_y U_B
             ctr(net, W, "ac,cd->ad", Qzt, Wt, &Vb);   // V = Q_z V_B
             const unsigned long long salt = 0x5EEDull * (unsigned long long)(info_idx + 1);
@@ -666,6 +743,31 @@ Engine::PPair Engine::projector(Network& net, Plan& P, const Ten& U, const Ten& 
     pp.PB = ctr(net, P, labels + "," + rl + K + "->" + tl + K, U, V, nullptr, nullptr, scale);
     pp.PT = ctr(net, P, rlL + K + "," + Llab + "->" + K + tl, Uv, L, nullptr, scale, nullptr);
     mixed_build = mixed;
+    --in_proj;
+    if (tape && !in_proj) {
+        TapeOp op;
+        op.kind = TapeOp::PROJ;
+        op.spec = labels;
+        op.X = U;
+        op.Y = L;
+        op.tl = tl;
+        op.rl = rl;
+        op.rlL = rlL;
+        op.Llab = Llab;
+        op.M = M;
+        op.PB = pp.PB;
+        op.PT = pp.PT;
+        op.S = S;
+        op.Us = Us;
+        op.Vcols = V_cols;
+        op.VT = VT_full;
+        op.kc = kc_full;
+        op.vt = vt != 0;
+        op.scale = scale;
+        op.n = n;
+        op.chi = chi;
+        tape->push_back(op);
+    }
     return pp;
 }
 
@@ -943,10 +1045,17 @@ static void build_left_move(Engine& e, Network& net, Plan& P, const Frame& f) {
                            cudaMemcpyHostToDevice));
     const int cnt = (int)items.size();
     e.push(P, std::make_unique<FnStep>([=](cudaStream_t s) { launch_normalize(dev, cnt, s); }));
+    if (e.tape) {
+        TapeOp op;
+        op.kind = TapeOp::NORM;
+        op.items = {{C1n, f.C[0]}, {T4kn, f.T[3][0]}, {T4in, f.T[3][1]}, {T4bn, f.T[3][2]},
+                    {C4n, f.C[3]}};
+        e.tape->push_back(op);
+    }
 }
 
 // convergence check (Sec. III.D): singular values of rho_eff = C1 C2 C3 C4 / Tr
-static void build_spectrum(Engine& e, Network& net) {
+void build_spectrum(Engine& e, Network& net) {
     Plan& P = net.spectrum;
     const int chi = net.chi;
     const Ten R1 = e.ctr(net, P, "ab,ac->bc", net.C[0], net.C[1]);
@@ -967,7 +1076,7 @@ static void build_spectrum(Engine& e, Network& net) {
         const Network* np = &net;
         e.push(P, std::make_unique<FnStep>([=](cudaStream_t s) {
             launch_jacobi_svd(rho_p, chi, Sraw, Ub, Wb, np->svd_info + info_idx, Vg, s);
-        }));
+        }, SCTM_KERNEL_JACOBI));
         e.push(P, std::make_unique<FnStep>(
             [=](cudaStream_t s) { launch_spectrum_update(Sraw, rho_p, chi, S_old, dS, s); }));
         return;
@@ -1047,6 +1156,63 @@ static void build_local(Engine& e, Network& net) {
     net.z[3] = z11;
     e.push(P, std::make_unique<FnStep>(
         [=](cudaStream_t s) { launch_lnkappa(z00, z10, z01, z11, lnk, s); }));
+    if (e.tape) {
+        TapeOp op;
+        op.kind = TapeOp::LNK;
+        op.z[0] = z00;
+        op.z[1] = z10;
+        op.z[2] = z01;
+        op.z[3] = z11;
+        e.tape->push_back(op);
+    }
+}
+
+bool Engine::all_warm(const Network& net) const {
+    if (net.psvd_steps.empty()) return false;
+    for (const PartialSvdStep* p : net.psvd_steps)
+        if (!p->is_warm || !p->can_warm) return false;
+    return true;
+}
+
+bool Engine::capture_iteration(Network& net) {
+    if (dry || serial || profile) return false;
+    cudaStream_t cs = cap_stream[cur_lane];
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const long long before = kernel_launches.load();
+    capturing = true;
+    bool ok = true;
+    try {
+        for (int m = 0; m < 4; ++m) run(net.move[m]);
+        run(net.spectrum);
+    } catch (...) {
+        ok = false;
+    }
+    capturing = false;
+    cudaGraph_t g = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(cs, &g);
+    // the capture only recorded launches: take them back out of the running launch count
+    const long long recorded = kernel_launches.load() - before;
+    kernel_launches -= recorded;
+    if (!ok || ee != cudaSuccess || !g) {
+        cudaGetLastError();
+        if (g) cudaGraphDestroy(g);
+        return false;
+    }
+    cudaGraphExec_t ex = nullptr;
+    if (cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) {
+        cudaGetLastError();
+        cudaGraphDestroy(g);
+        return false;
+    }
+    if (net.graph_exec) cudaGraphExecDestroy(net.graph_exec);
+    if (net.graph) cudaGraphDestroy(net.graph);
+    net.graph = g;
+    net.graph_exec = ex;
+    net.graph_launches = recorded;
+    return true;
 }
 
 void Engine::cold_svd(Network& net) {
@@ -1079,11 +1245,18 @@ void Engine::build_network(Network& net) {
     net.lnk = dalloc(2);
     net.E = alloc({net.p, D, D, D, D});
     mixed_build = true;
-    for (int m = 0; m < 4; ++m) build_left_move(*this, net, net.move[m], make_frame(net, m));
+    for (int m = 0; m < 4; ++m) {
+        tape = &net.tape_move[m];
+        build_left_move(*this, net, net.move[m], make_frame(net, m));
+    }
     mixed_build = false;
+    tape = nullptr;
     build_spectrum(*this, net);
+    tape = &net.tape_local;
     build_local(*this, net);
+    tape = nullptr;
     finalize(net);
+    if (precision == SCTM_PREC_F64EMU) autotune(net);
     set_precision(net, precision);
 }
 
@@ -1113,15 +1286,83 @@ double Engine::switch_level(int prec) {
     }
 }
 
-// The FP64 emulation pays off for long contractions only: measured per shape at D=4, chi=64,
-// it took 0.3-0.6x the FP64 kernel's time for K >= 512 (M >= 128, N >= 64) and 1.2-2.5x for
-// K <= 64, where the digit split and the per-block read-back outweigh the tensor-core speed.
-static bool emu_worth(const CtrLaunch& a) { return a.K >= 512 && a.M >= 128 && a.N >= 64; }
+// Which kernel runs each FP64-accurate contraction: the FP64 kernels or the FP64 emulation on
+// the tensor cores.  The emulation pays off where its fixed costs (digit split of both operands,
+// row exponents, one accumulator read-back per 128 K) are small against the multiply-adds it
+// moves to the tensor cores, which depends on M, N, K and the batch together; so it is measured.
+// autotune() times both kernels once per distinct contraction shape on this context's own buffers
+// (one launch to warm up, then the best of three, CUDA events on the caller's stream) and keeps
+// the faster; shapes below 4 MFLOP stay FP64 untimed (launch overheads dominate there).
+void Engine::autotune(Network& net) {
+    if (dry) return;
+    struct Choice {
+        bool emu;
+        float t64, temu;
+    };
+    std::map<std::tuple<int, int, int, int>, Choice> seen;
+    cudaStream_t s = lanes[0].streams[0];
+    cudaEvent_t e0, e1;
+    CUDA_OK(cudaEventCreate(&e0));
+    CUDA_OK(cudaEventCreate(&e1));
+    auto time_it = [&](CtrLaunch a, int prec) {
+        a.precision = prec;
+        if (prec != SCTM_PREC_FP64) {  // the tensor-core paths split K with their own tiles
+            a.splits = a.tc_splits;
+            a.kchunk = a.tc_kchunk;
+        }
+        launch_ctr(a, s);
+        float best = 1e30f;
+        for (int r = 0; r < 3; ++r) {
+            cudaEventRecord(e0, s);
+            launch_ctr(a, s);
+            cudaEventRecord(e1, s);
+            CUDA_OK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            best = std::min(best, ms);
+        }
+        return best;
+    };
+    net.tuned_emu = 0;
+    net.tuned_total = 0;
+    for (CtrStep* st : net.ctr_steps) {
+        st->emu_ok = false;
+        if (!st->mixed_ok) continue;
+        ++net.tuned_total;
+        if (st->flops < 4000000LL) continue;
+        const auto key = std::make_tuple(st->a.M, st->a.N, st->a.K, st->a.nb);
+        auto it = seen.find(key);
+        if (it == seen.end()) {
+            Choice c;
+            c.t64 = time_it(st->a, SCTM_PREC_FP64);
+            c.temu = time_it(st->a, SCTM_PREC_F64EMU);
+            c.emu = c.temu < 0.9f * c.t64;
+            it = seen.emplace(key, c).first;
+            if (const char* tf = getenv("SCTM_AUTOTUNE_LOG")) {
+                if (tf[0]) {
+                    if (FILE* fp = fopen(tf, "a")) {
+                        fprintf(fp, "%d %d %d %d %d %.4f %.4f %d\n", net.d, st->a.M, st->a.N,
+                                st->a.K, st->a.nb, c.t64, c.temu, c.emu ? 1 : 0);
+                        fclose(fp);
+                    }
+                }
+            }
+        }
+        st->emu_ok = it->second.emu;
+        if (st->emu_ok) ++net.tuned_emu;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CUDA_OK(cudaGetLastError());
+    int err[2] = {0, 0};
+    CUDA_OK(cudaMemcpy(err, dev_err, sizeof(err), cudaMemcpyDeviceToHost));
+    if (err[0]) throw Error(SCTM_ETIMEOUT, "autotune: a tensor-core contraction wait timed out");
+}
 
 void Engine::set_precision(Network& net, int prec) {
     for (CtrStep* s : net.ctr_steps) {
         int p = s->mixed_ok ? prec : SCTM_PREC_FP64;
-        if (p == SCTM_PREC_F64EMU && !emu_worth(s->a)) p = SCTM_PREC_FP64;
+        if (p == SCTM_PREC_F64EMU && !s->emu_ok) p = SCTM_PREC_FP64;
         s->a.precision = p;
     }
     net.precision = prec;

@@ -5,6 +5,7 @@
 #include <functional>
 #include <memory>
 #include <thread>
+#include <unordered_map>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -36,6 +37,28 @@ Ten view(double* p, const std::vector<int>& dims);                 // contiguous
 Ten permute(const Ten& t, const std::vector<int>& perm);           // out axis k = t axis perm[k]
 
 class Engine;
+
+// One operation of a plan as the reverse mode sees it, recorded while the plan is built (the
+// tape): a contraction, a projector pair (Eqs. "projector construction" / "projector
+// construction 2" as one unit with its own backward), the Frobenius normalisation that ends a
+// move, or the ln kappa of the local contractions.
+struct TapeOp {
+    enum Kind { CTR, PROJ, NORM, LNK } kind = CTR;
+    std::string spec;   // CTR: einsum spec; PROJ: the cut labels
+    Ten X, Y, O;        // CTR operands / output; PROJ: X = U (rho_T), Y = L (rho_B)
+    // PROJ
+    std::string tl, rl, rlL, Llab;  // truncated legs, remaining legs (U / L naming), L's labels
+    Ten M, PB, PT;
+    double *S = nullptr, *Us = nullptr, *Vcols = nullptr, *VT = nullptr, *scale = nullptr;
+    int n = 0, chi = 0, kc = 0;
+    bool vt = false;   // right vectors stored as V^T (gesvd) rather than as columns
+    // NORM: (source, destination view) pairs
+    std::vector<std::pair<Ten, Ten>> items;
+    // LNK: Z00, Z10, Z01, Z11 scalars
+    double* z[4] = {nullptr, nullptr, nullptr, nullptr};
+};
+using Tape = std::vector<TapeOp>;
+struct Adjoint;  // backward plans and buffers of one network (adjoint.cu)
 
 constexpr int kStreams = 10;  // stream 0 = the caller's stream; 1..9 run independent sub-plans
 struct EvRec {
@@ -88,6 +111,19 @@ struct Network {
     int precision = SCTM_PREC_FP64;  // form of the mixed-eligible contractions (set_precision)
     double cutoff_now = 0.0;         // pseudo-inverse cutoff in use (raised for mixed forms)
     std::vector<struct SvdStep*> svd_steps;
+    int method = SCTM_METHOD_SPLIT;       // SCTM_METHOD_SPLIT or SCTM_METHOD_REDUCED
+    Plan site;                            // reduced method: the fused site tensor from A, O, A-bar
+    Ten fused;                            // reduced method: a[m, m, m, m], m = D d D
+    int tuned_emu = 0, tuned_total = 0;  // autotune: contractions on the emulation / eligible
+    cudaGraph_t graph = nullptr;          // one captured warm iteration (moves + spectrum)
+    cudaGraphExec_t graph_exec = nullptr;
+    long long graph_launches = 0;         // this library's kernels in one replay
+    Tape tape_move[4];               // reverse-mode records of the moves and the local plan
+    Tape tape_local;
+    std::unique_ptr<Adjoint> adj;    // built on the first adjoint gradient
+    double adj_gcut = 1e-6;          // adjoint: kept singular values below this s_0 held fixed
+    Network();
+    ~Network();
 };
 
 class Engine {
@@ -111,6 +147,26 @@ public:
     Lane lanes[kLanes];
     static thread_local int cur_lane;
     Lane& lane() { return lanes[cur_lane]; }
+    // Serialised execution (profiling): every step of every plan on the lane's stream 0, the
+    // parallel sub-plans one after the other, so that an event pair around a launch measures that
+    // launch alone.
+    bool serial = false;
+    // While an iteration is captured into a CUDA graph (this thread only), stream 0 of the lane is
+    // replaced by a capture stream: the caller's stream may be the legacy default stream, which
+    // cannot be captured.  The parallel sub-plans are then recorded from this thread.
+    static thread_local bool capturing;
+    cudaStream_t cap_stream[2] = {nullptr, nullptr};
+    cudaStream_t strm(int sid) {
+        if (serial || sid == 0) return capturing ? cap_stream[cur_lane] : lane().streams[0];
+        return lane().streams[sid];
+    }
+    cusolverDnHandle_t solv(int sid) { return lane().solver[serial ? 0 : sid]; }
+    // Capture one iteration of a network (its four moves and the convergence spectrum) on the
+    // calling thread's lane into net.graph; false if the plan cannot be captured.
+    bool capture_iteration(Network& net);
+    // every partial SVD of the network holds a warm-start subspace (the next iteration takes the
+    // warm path throughout; false in the other SVD modes)
+    bool all_warm(const Network& net) const;
     cusolverDnParams_t solver_params = nullptr;
     int precision;      // SCTM_PREC_* currently set on the move plans' contractions
     double cutoff;
@@ -122,6 +178,9 @@ public:
     // rho_B rho_T, renormalisation); projector formation, the spectrum and the local
     // contractions stay FP64.
     void set_precision(Network& net, int prec);
+    // per contraction shape, time the FP64 kernels against the FP64 emulation on the tensor cores
+    // and keep the faster for SCTM_PREC_F64EMU (run at creation of an F64EMU context)
+    void autotune(Network& net);
     // Smallest useful pseudo-inverse cutoff s_k/s_1 for a contraction form: below it the
     // singular values of rho_B rho_T are rounding noise of that form.
     static double cutoff_floor(int prec);
@@ -139,9 +198,10 @@ public:
     long long ctr_launches = 0, ctr_flops = 0, svd_calls = 0;
     // per contraction kernel (SCTM_KERNEL_*): event time, launches, algorithmic FLOPs, and the
     // bytes the contraction must move at least (operands read once, output written once)
-    double kern_ms[4] = {0, 0, 0, 0};
-    long long kern_launches[4] = {0, 0, 0, 0}, kern_flops[4] = {0, 0, 0, 0},
-              kern_bytes[4] = {0, 0, 0, 0};
+    static constexpr int kKernels = 6;  // SCTM_KERNEL_F64 .. SCTM_KERNEL_CHOL
+    double kern_ms[kKernels] = {0};
+    long long kern_launches[kKernels] = {0}, kern_flops[kKernels] = {0},
+              kern_bytes[kKernels] = {0};
     std::atomic<long long> kernel_launches{0};  // own kernels only (cuSOLVER's are not counted)
     int record(int sid);                                       // event index in pool sid
     void record_done(int sid, int kind, long long flops, int e0, const CtrLaunch* a = nullptr);
@@ -160,9 +220,12 @@ public:
     // Contraction O = X * Y written as an einsum spec over single-character labels.  Labels
     // present in X and Y but not in the output are summed; labels of X (Y) only must appear in
     // the output.  With out == nullptr a contiguous output in the spec's order is allocated.
+    // accumulate: O += X * Y (FP64 kernels only; used by the reverse mode).
     Ten ctr(Network& net, Plan& P, const std::string& spec, const Ten& X, const Ten& Y,
             const Ten* out = nullptr, const double* rowscale = nullptr,
-            const double* colscale = nullptr);
+            const double* colscale = nullptr, bool accumulate = false);
+    // split-K workspace for the contractions net.ctr_steps[first..] built after finalize()
+    void assign_workspace(Network& net, size_t first);
 
     struct PPair {
         Ten PB, PT;
@@ -174,6 +237,9 @@ public:
                     const std::string& tl);
 
     void build_network(Network& net);
+    // the reduced method (reduced.cu): fused site tensor, moves, spectrum, local contractions
+    void build_reduced_network(Network& net);
+    void init_reduced_env(Network& net);
     void finalize(Network& net);
     void run(Plan& P);
     void init_env(Network& net, unsigned long long seed);
@@ -188,10 +254,29 @@ public:
     }
     void run_sub(Plan& P);
 
+    // ---- reverse mode (adjoint.cu)
+    Tape* tape = nullptr;   // while a plan is built: where its operations are recorded
+    int in_proj = 0;        // > 0 inside projector(): its contractions belong to the PROJ record
+    bool force_full_svd = false;  // partial-SVD steps run their full (gesvd) solve
+    long long size_of(const double* base) const;  // doubles of a dalloc'd buffer (0 if unknown)
+    // d f / d A of one network's ln kappa at its converged environment, by implicit
+    // differentiation of the split-CTMRG fixed point (restarted GMRES on (I - J^T) lambda = w,
+    // J the Jacobian of one iteration, w = d ln kappa / d E).  dA: p D^4 device doubles (set).
+    // Returns the matrix-vector products used and the final relative residual.
+    void adjoint_lnk_grad(Network& net, double* dA, double tol, int max_mv, int* mv_used,
+                          double* residual);
+    // build the backward plans from the tapes (done by the first adjoint_lnk_grad; with
+    // SCTM_DRYRUN=1 it only checks every backward contraction's labels and shapes)
+    void build_adjoint(Network& net);
+
 private:
+    std::unordered_map<const double*, long long> sizes_;
     std::vector<void*> allocs_;
     std::vector<cudaEvent_t> owned_events_;
     char dry_base_[64] = {0};
 };
+
+// the convergence spectrum plan (Sec. III.D), shared by both methods
+void build_spectrum(Engine& e, Network& net);
 
 }  // namespace sctm

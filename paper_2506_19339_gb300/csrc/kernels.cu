@@ -117,7 +117,8 @@ __global__ void __launch_bounds__(NT) ctr_f64_kernel(const CtrLaunch a) {
             if (n >= a.N) continue;
             double v = acc[i][j] * rs;
             if (a.colscale) v *= a.colscale[n];
-            a.O[om_ + a.on[n]] = v;
+            double* dst = a.O + om_ + a.on[n];
+            *dst = a.accumulate ? *dst + v : v;
         }
     }
 }
@@ -136,7 +137,8 @@ __global__ void ctr_splitk_reduce_kernel(const CtrLaunch a) {
         if (a.rowscale) v *= a.rowscale[m];
         if (a.colscale) v *= a.colscale[n];
         const long long obo = a.ob ? a.ob[b] : 0;
-        a.O[obo + a.om[m] + a.on[n]] = v;
+        double* dst = a.O + obo + a.om[m] + a.on[n];
+        *dst = a.accumulate ? *dst + v : v;
     }
 }
 
@@ -175,7 +177,8 @@ __global__ void __launch_bounds__(kSkinnyRows) ctr_skinny_kernel(const CtrLaunch
             if (n >= a.N) continue;
             double v = acc[n] * rs;
             if (a.colscale) v *= a.colscale[n];
-            a.O[om_ + a.on[n]] = v;
+            double* dst = a.O + om_ + a.on[n];
+            *dst = a.accumulate ? *dst + v : v;
         }
     }
 }

@@ -29,6 +29,7 @@
 //     the rows of the triangular factor of Z, graded by the singular values, which is the
 //     ordering under which one-sided Jacobi converges fastest.
 #include <algorithm>
+#include <cstdlib>
 #include <mutex>
 
 #include "sctm_internal.h"
@@ -72,45 +73,44 @@ __device__ void block_cholesky(double* R, double* rinv, int k) {
     }
 }
 
-// Scratch of one Jacobi round, one entry per column pair.
-struct RoundScratch {
-    double* c;   // cosine of each pair's rotation
-    double* s;   // sine
-    int* act;    // 1 if the pair rotates
-    int* pi;     // the pair's columns i, j (this round)
-    int* pj;
-};
-
 // One sweep of one-sided Jacobi rotations over all column pairs (circle-method rounds) of the
-// kp x kp column-major matrix A (leading dimension ld), accumulating into V (same layout).  Per
-// round: thread q < kp/2 forms pair q's three dot products and its rotation (one pair per
-// thread, so the FP64 square roots and divisions are not repeated across a warp), then every
-// thread applies the rotations, one (pair, row) element at a time.  Pairs with
-// |a_i . a_j| <= tol |a_i| |a_j| are left alone.  Returns (to every thread) the largest
-// |a_i . a_j| / (|a_i| |a_j|) seen.
+// kp x kp column-major matrix A (leading dimension ld), accumulating into V (same layout).  The
+// pairs of one round touch disjoint columns, so a warp takes a pair from start to end: its lanes
+// form the three dot products over the rows (shuffle-reduced, fixed order), lane 0 forms the
+// rotation (the FP64 square roots and divisions once per pair, not once per lane) and
+// broadcasts it, and the lanes rotate the two columns of A and V; one block barrier per round.
+// Pairs with |a_i . a_j| <= tol |a_i| |a_j| are left alone.  Returns (to every thread) the
+// largest |a_i . a_j| / (|a_i| |a_j|) seen.
 template <typename F>
-__device__ float jacobi_sweep(F* A, F* V, int kp, int ld, F tol, RoundScratch rs, float* s_max) {
-    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
+__device__ float jacobi_sweep(F* A, F* V, int kp, int ld, F tol, float* s_max) {
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5,
+              nw = nt >> 5;
     const int np = kp / 2;
     if (tid == 0) *s_max = 0.0f;
     float wmax = 0.0f;
     for (int round = 0; round < kp - 1; ++round) {
-        for (int q = tid; q < np; q += nt) {
+        for (int q = warp; q < np; q += nw) {
             const int p0 = q, p1 = kp - 1 - q;
             const int i = p0 == 0 ? 0 : 1 + (p0 - 1 + round) % (kp - 1);
             const int j = 1 + (p1 - 1 + round) % (kp - 1);
-            const F* ai = A + (long long)i * ld;
-            const F* aj = A + (long long)j * ld;
+            F* ai = A + (long long)i * ld;
+            F* aj = A + (long long)j * ld;
             F al = 0, be = 0, ga = 0;
-            for (int r = 0; r < kp; ++r) {
+            for (int r = lane; r < kp; r += 32) {
                 const F x = ai[r], y = aj[r];
                 al = fma(x, x, al);
                 be = fma(y, y, be);
                 ga = fma(x, y, ga);
             }
-            int act = 0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                al += __shfl_xor_sync(0xffffffffu, al, o);
+                be += __shfl_xor_sync(0xffffffffu, be, o);
+                ga += __shfl_xor_sync(0xffffffffu, ga, o);
+            }
             F c = 1, sn = 0;
-            if (al > F(0) && be > F(0)) {
+            int act = 0;
+            if (lane == 0 && al > F(0) && be > F(0)) {
                 const F rel = fabs(ga) / (sqrt(al) * sqrt(be));
                 wmax = fmaxf(wmax, (float)rel);
                 if (rel > tol) {
@@ -121,22 +121,13 @@ __device__ float jacobi_sweep(F* A, F* V, int kp, int ld, F tol, RoundScratch rs
                     act = 1;
                 }
             }
-            rs.c[q] = (double)c;
-            rs.s[q] = (double)sn;
-            rs.act[q] = act;
-            rs.pi[q] = i;
-            rs.pj[q] = j;
-        }
-        __syncthreads();
-        // rotations: warp per pair, lane per row (no integer division in the inner loop)
-        for (int q = tid >> 5; q < np; q += nt >> 5) {
-            if (!rs.act[q]) continue;
-            const F c = (F)rs.c[q], sn = (F)rs.s[q];
-            F* ai = A + (long long)rs.pi[q] * ld;
-            F* aj = A + (long long)rs.pj[q] * ld;
-            F* vi = V + (long long)rs.pi[q] * ld;
-            F* vj = V + (long long)rs.pj[q] * ld;
-            for (int r = tid & 31; r < kp; r += 32) {
+            act = __shfl_sync(0xffffffffu, act, 0);
+            if (!act) continue;
+            c = __shfl_sync(0xffffffffu, c, 0);
+            sn = __shfl_sync(0xffffffffu, sn, 0);
+            F* vi = V + (long long)i * ld;
+            F* vj = V + (long long)j * ld;
+            for (int r = lane; r < kp; r += 32) {
                 const F x = ai[r], y = aj[r];
                 ai[r] = c * x - sn * y;
                 aj[r] = sn * x + c * y;
@@ -214,19 +205,13 @@ __global__ void __launch_bounds__(kPsvdThreads)
     jacobi_svd_kernel(const double* __restrict__ B, int k, double* __restrict__ S,
                       double* __restrict__ U, double* __restrict__ W, int* info, double* Vg) {
     extern __shared__ double sm[];
-    const int kp = k + (k & 1), ld = kp + 1, np = kp / 2;
+    const int kp = k + (k & 1), ld = kp + 1;
     double* A = sm;                        // FP64 phase: column j at A + j ld
     double* V = Vg ? Vg : sm + kp * ld;    // W, column j at V + j ld (global above kPsvdSmemK)
     float* A32 = (float*)A;                // FP32 phase: both FP32 matrices inside A's space
     float* V32 = A32 + kp * ld;
     double* sig = sm + (Vg ? 1 : 2) * kp * ld;
-    RoundScratch rs;
-    rs.c = sig + kp;
-    rs.s = rs.c + np;
-    int* rank = (int*)(rs.s + np);
-    rs.act = rank + kp;
-    rs.pi = rs.act + np;
-    rs.pj = rs.pi + np;
+    int* rank = (int*)(sig + kp);
     __shared__ float s_max;
     __shared__ int s_exp;
     __shared__ double s_wmax[kPsvdThreads / 32];
@@ -261,7 +246,7 @@ __global__ void __launch_bounds__(kPsvdThreads)
     __syncthreads();
     const float tol32 = 4.0f * (float)kp * 5.9604645e-8f;
     for (int sw = 0; sw < kJacobiMaxSweeps32; ++sw)
-        if (jacobi_sweep<float>(A32, V32, kp, ld, tol32, rs, &s_max) <= tol32) break;
+        if (jacobi_sweep<float>(A32, V32, kp, ld, tol32, &s_max) <= tol32) break;
     // 2. W = V32 in FP64, re-orthonormalised: W <- W F^-1 with F^T F = W^T W
     for (int e = tid; e < kp * kp; e += nt) {
         const int r = e % kp, c = e / kp;
@@ -302,7 +287,7 @@ __global__ void __launch_bounds__(kPsvdThreads)
     {
         int sw = 0;
         for (; sw < kJacobiMaxSweeps64; ++sw) {
-            const float mx = jacobi_sweep<double>(A, V, kp, ld, tol64, rs, &s_max);
+            const float mx = jacobi_sweep<double>(A, V, kp, ld, tol64, &s_max);
             if (mx <= tol64 || mx < 1e-7f) break;
         }
         if (sw >= kJacobiMaxSweeps64) bad = 1;
@@ -368,19 +353,34 @@ void launch_refill(double* V, int n, int k, const double* S, unsigned long long 
 size_t chol_orth_smem(int k, bool global_x) {
     return (size_t)((global_x ? 1 : 2) * k * k + 2 * k) * sizeof(double);
 }
-size_t jacobi_svd_smem(int k, bool global_v) {
-    const int kp = k + (k & 1), ld = kp + 1, np = kp / 2;
-    return (size_t)((global_v ? 1 : 2) * kp * ld + kp + 2 * np) * sizeof(double) +
-           (size_t)(kp + 3 * np) * sizeof(int);
+size_t jacobi_svd_smem(int k, bool global_v) {  // A (and W), the singular values, the ranks
+    const int kp = k + (k & 1), ld = kp + 1;
+    return (size_t)((global_v ? 1 : 2) * kp * ld + kp) * sizeof(double) + (size_t)kp * sizeof(int);
+}
+
+// The one-CTA kernels are bound by the FP64 throughput of their SM, which every warp resident on
+// that SM shares.  Contraction CTAs of other streams would otherwise fill the rest of the SM and
+// take most of that throughput, so these launches request enough shared memory (220 KB) that
+// nothing else fits beside them: each runs on an SM of its own.  SCTM_SHARED_SM=1 requests only
+// what the kernel uses (for comparison).
+constexpr size_t kExclusiveSmem = 220 * 1024;
+
+static size_t one_cta_smem(size_t need) {
+    static const bool shared = [] {
+        const char* v = getenv("SCTM_SHARED_SM");
+        return v && v[0] == '1';
+    }();
+    return shared ? need : std::max(need, kExclusiveSmem);
 }
 
 void launch_chol_orth(const double* G, int k, double shift, double* T, double* Xg,
                       cudaStream_t s) {
-    const size_t smem = chol_orth_smem(k, Xg != nullptr);
+    const size_t smem = one_cta_smem(chol_orth_smem(k, Xg != nullptr));
     static std::once_flag once;
     std::call_once(once, [] {
         // the largest request: all in shared memory at kPsvdSmemK, or X in global at kPsvdMaxK
-        const size_t mx = std::max(chol_orth_smem(kPsvdSmemK, false), chol_orth_smem(kPsvdMaxK, true));
+        const size_t mx = std::max({chol_orth_smem(kPsvdSmemK, false), chol_orth_smem(kPsvdMaxK, true),
+                                    kExclusiveSmem});
         cudaFuncSetAttribute(chol_orth_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
     });
     chol_orth_kernel<<<1, kPsvdThreads, smem, s>>>(G, k, shift, T, Xg);
@@ -388,11 +388,11 @@ void launch_chol_orth(const double* G, int k, double shift, double* T, double* X
 
 void launch_jacobi_svd(const double* B, int k, double* S, double* U, double* W, int* info,
                        double* Vg, cudaStream_t s) {
-    const size_t smem = jacobi_svd_smem(k, Vg != nullptr);
+    const size_t smem = one_cta_smem(jacobi_svd_smem(k, Vg != nullptr));
     static std::once_flag once;
     std::call_once(once, [] {
-        const size_t mx =
-            std::max(jacobi_svd_smem(kPsvdSmemK, false), jacobi_svd_smem(kPsvdMaxK, true));
+        const size_t mx = std::max({jacobi_svd_smem(kPsvdSmemK, false),
+                                    jacobi_svd_smem(kPsvdMaxK, true), kExclusiveSmem});
         cudaFuncSetAttribute(jacobi_svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
     });
     jacobi_svd_kernel<<<1, kPsvdThreads, smem, s>>>(B, k, S, U, W, info, Vg);

@@ -45,6 +45,11 @@ struct CtrLaunch {
     void* pack_x = nullptr;            // tensor-core operands, converted once per launch into
     void* pack_y = nullptr;            //   hi (then lo) tiles in shared-memory image order
     int* rexp = nullptr;               // nb * (M + N) row / column exponents (SCTM_PREC_F64EMU)
+    int accumulate = 0;                // FP64 kernels: O += result instead of O = result
+    // tensor-core kernels: spin limit of the first mbarrier wait of each CTA (-1 = the normal
+    // bound).  0 makes that wait give up at once, which exercises the timeout path (drain, error
+    // flag, SCTM_ETIMEOUT) without a hang or a fault; used by the tests only.
+    int first_wait_limit = -1;
 };
 // bytes of the packed tensor-core operands (hi and lo, TF32: the largest form)
 size_t tc_pack_bytes_x(const CtrLaunch& a);
@@ -102,6 +107,9 @@ void launch_lnkappa(const double* Z00, const double* Z10, const double* Z01, con
                     double* lnk, cudaStream_t s);
 // out[0] = -T (lnk_num - lnk_den)
 void launch_free_energy(const double* lnk_num, const double* lnk_den, double T, double* out,
+                        cudaStream_t s);
+// g = -T (dnum - dden): the adjoint gradient from the two networks' d ln kappa / dA
+void launch_adj_combine(const double* dnum, const double* dden, double T, int n, double* g,
                         cudaStream_t s);
 // g = -2T (Enum / Z11num - Eden / Z11den)
 void launch_grad_combine(const double* Enum, const double* lnk_num, const double* Eden,

@@ -20,6 +20,7 @@ SCTM_PREC_FP64, SCTM_PREC_TF32, SCTM_PREC_TF32X3, SCTM_PREC_BF16, SCTM_PREC_BF16
 SCTM_GRAD_ENV, SCTM_GRAD_ADJOINT = 0, 1
 SCTM_SVD_QR, SCTM_SVD_POLAR, SCTM_SVD_PARTIAL, SCTM_SVD_PARTIAL_RANDOM = 0, 1, 2, 3
 SCTM_NET_NUM, SCTM_NET_DEN = 0, 1
+SCTM_METHOD_SPLIT, SCTM_METHOD_REDUCED = 0, 1
 SCTM_MOVE_LEFT, SCTM_MOVE_RIGHT, SCTM_MOVE_UP, SCTM_MOVE_DOWN = range(4)
 
 
@@ -28,7 +29,7 @@ class SctmOpts(ctypes.Structure):
                 ('d', ctypes.c_int), ('precision', ctypes.c_int), ('grad_mode', ctypes.c_int),
                 ('svd_cutoff', ctypes.c_double), ('init_seed', ctypes.c_ulonglong),
                 ('batch', ctypes.c_int), ('cuda_stream', ctypes.c_void_p),
-                ('svd_mode', ctypes.c_int)]
+                ('svd_mode', ctypes.c_int), ('method', ctypes.c_int)]
 
 
 class SctmError(RuntimeError):
@@ -75,6 +76,9 @@ def load():
         'sctm_iterate_batch': (I, [ctypes.POINTER(P), I, I, D, ctypes.POINTER(I),
                                    ctypes.POINTER(I), ctypes.POINTER(D)]),
         'sctm_device_bytes': (S, [P]),
+        'sctm_set_grad_mode': (I, [P, I, D, I, D]),
+        'sctm_autotune_info': (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I)]),
+        'sctm_adjoint_info': (I, [P, ctypes.POINTER(I), ctypes.POINTER(D)]),
         'sctm_set_profiling': (I, [P, I]),
         'sctm_profile': (I, [P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong),
                              ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(D),
@@ -203,12 +207,31 @@ def sctm_iterate_batch(ctxs, max_it, tol):
     return s, list(st), list(it), list(ds)
 
 
+def sctm_set_grad_mode(ctx, mode, tol=1e-10, max_matvecs=400, svd_grad_cutoff=1e-6):
+    return load().sctm_set_grad_mode(ctx, int(mode), float(tol), int(max_matvecs),
+                                     float(svd_grad_cutoff))
+
+
+def sctm_adjoint_info(ctx):
+    mv = (ctypes.c_int * 2)()
+    res = (ctypes.c_double * 2)()
+    st = load().sctm_adjoint_info(ctx, mv, res)
+    return st, list(mv), list(res)
+
+
+def sctm_autotune_info(ctx, network):
+    emu, total = ctypes.c_int(0), ctypes.c_int(0)
+    st = load().sctm_autotune_info(ctx, int(network), ctypes.byref(emu), ctypes.byref(total))
+    return st, emu.value, total.value
+
+
 def sctm_device_bytes(ctx):
     return int(load().sctm_device_bytes(ctx))
 
 
-def sctm_set_profiling(ctx, on):
-    return load().sctm_set_profiling(ctx, int(bool(on)))
+def sctm_set_profiling(ctx, mode):
+    """mode 0 off, 1 events around launches (concurrent streams), 2 serialised execution."""
+    return load().sctm_set_profiling(ctx, int(mode))
 
 
 def sctm_profile(ctx, reset=False):
@@ -220,7 +243,8 @@ def sctm_profile(ctx, reset=False):
                 'svd_ms': svd_ms.value, 'svd_calls': sc_.value, 'kernel_launches': kl.value}
 
 
-SCTM_KERNEL_F64, SCTM_KERNEL_SKINNY, SCTM_KERNEL_TC, SCTM_KERNEL_F64EMU = range(4)
+SCTM_KERNEL_F64, SCTM_KERNEL_SKINNY, SCTM_KERNEL_TC, SCTM_KERNEL_F64EMU, SCTM_KERNEL_JACOBI, \
+    SCTM_KERNEL_CHOL = range(6)
 
 
 def sctm_profile_kernel(ctx, kernel):
@@ -247,16 +271,31 @@ def unpack_env(buf, chi, D, d):
     return env
 
 
+def unpack_env_reduced(buf, chi, m):
+    """The reduced method's environment: {'C1'..'C4': (chi, chi), 'T1'..'T4': (chi, chi, m)}."""
+    env = {}
+    off = 0
+    for c in ('C1', 'C2', 'C3', 'C4'):
+        env[c] = buf[off:off + chi * chi].reshape(chi, chi)
+        off += chi * chi
+    for t in ('T1', 'T2', 'T3', 'T4'):
+        env[t] = buf[off:off + chi * chi * m].reshape(chi, chi, m)
+        off += chi * chi * m
+    return env
+
+
 class SplitCTMRG:
     """Convenience owner of one context: create / iterate / f / g / destroy."""
 
     def __init__(self, peps, pepo, chi, T, precision=SCTM_PREC_FP64, cutoff=1e-12, seed=0,
-                 svd_mode=SCTM_SVD_QR):
+                 svd_mode=SCTM_SVD_QR, method=SCTM_METHOD_SPLIT):
         st, o = sctm_default_opts()
         p, D = peps.shape[0], peps.shape[1]
         o.T, o.D, o.p, o.d = float(T), D, p, pepo.shape[2]
         o.precision, o.svd_cutoff, o.init_seed = precision, cutoff, seed
         o.svd_mode = svd_mode
+        o.method = method
+        self.method = method
         self.chi, self.D, self.p, self.d = chi, D, p, pepo.shape[2]
         st, self.ctx = sctm_create(np.ascontiguousarray(peps, dtype=np.float64),
                                    np.ascontiguousarray(pepo, dtype=np.float64), chi, o)
@@ -286,7 +325,10 @@ class SplitCTMRG:
     def env(self, network):
         st, buf = sctm_env_export(self.ctx, network)
         self._check(st)
-        return unpack_env(buf, self.chi, self.D, self.d if network == SCTM_NET_NUM else 1)
+        d = self.d if network == SCTM_NET_NUM else 1
+        if self.method == SCTM_METHOD_REDUCED:
+            return unpack_env_reduced(buf, self.chi, self.D * d * self.D)
+        return unpack_env(buf, self.chi, self.D, d)
 
     def close(self):
         if self.ctx:

@@ -73,7 +73,8 @@ def test_plans_build_without_gpu(lib, D, d, chi, svd):
     """SCTM_DRYRUN=1 builds every plan (four moves, convergence, local contractions) of both
     networks with placeholder pointers: every contraction's labels, dimensions and ranks are
     checked on the CPU, for the full (svd 0) and the partial (svd 2) SVD plans; chi = 100 has
-    subspaces above the one-CTA limit, which stay on the full SVD."""
+    subspaces above the one-CTA limit, which stay on the full SVD.  SCTM_DRYRUN_ADJOINT=1 also
+    builds the reverse-mode (adjoint) plans from the tapes, checking every backward contraction."""
     import subprocess
     import sys
     code = ('import numpy as np\n'
@@ -83,7 +84,7 @@ def test_plans_build_without_gpu(lib, D, d, chi, svd):
             'A = np.zeros((2,) + (%d,) * 4); O = np.zeros((2, 2) + (%d,) * 4)\n'
             'st, ctx = sctm.sctm_create(A, O, %d, o)\n'
             'print(st)\n') % (D, d, svd, D, d, chi)
-    env = dict(os.environ, SCTM_DRYRUN='1')
+    env = dict(os.environ, SCTM_DRYRUN='1', SCTM_DRYRUN_ADJOINT='1')
     out = subprocess.run([sys.executable, '-c', code], cwd=ROOT, env=env, capture_output=True,
                          text=True, timeout=300)
     assert out.returncode == 0, out.stderr
@@ -104,3 +105,40 @@ def test_binding_constants_match_header():
             assert getattr(sctm, name) == val, name
     for name in ('SCTM_PREC_F64EMU', 'SCTM_SVD_PARTIAL_RANDOM', 'SCTM_KERNEL_F64EMU', 'SCTM_ETIMEOUT'):
         assert getattr(sctm, name) == values[name], name
+
+
+@pytest.mark.parametrize('D,chi,svd', [(2, 6, 0), (4, 16, 3), (3, 9, 2)])
+def test_reduced_plans_build_without_gpu(lib, D, chi, svd):
+    """SCTM_DRYRUN=1 with the reduced method (Sec. II, Fig. 3): the fused-tensor plan, the four
+    moves, the spectrum and the local contractions build with every label and dimension checked."""
+    import subprocess
+    import sys
+    code = ('import numpy as np\n'
+            'from paper_2506_19339_gb300 import sctm\n'
+            'st, o = sctm.sctm_default_opts()\n'
+            'o.D, o.d, o.svd_mode, o.method = %d, 2, %d, sctm.SCTM_METHOD_REDUCED\n'
+            'A = np.zeros((2,) + (%d,) * 4); O = np.zeros((2, 2) + (2,) * 4)\n'
+            'st, ctx = sctm.sctm_create(A, O, %d, o)\n'
+            'print(st)\n') % (D, svd, D, chi)
+    env = dict(os.environ, SCTM_DRYRUN='1')
+    out = subprocess.run([sys.executable, '-c', code], cwd=ROOT, env=env, capture_output=True,
+                         text=True, timeout=300)
+    assert out.returncode == 0, out.stderr
+    assert out.stdout.strip() == '0', out.stdout + out.stderr
+
+
+def test_reduced_method_option_checks(lib):
+    """The reduced method is FP64 with the environment gradient only: other combinations are
+    rejected on entry."""
+    A = np.zeros((2, 2, 2, 2, 2))
+    O = np.zeros((2, 2, 2, 2, 2, 2))
+    st, o = sctm.sctm_default_opts()
+    o.method = sctm.SCTM_METHOD_REDUCED
+    o.precision = sctm.SCTM_PREC_TF32
+    assert sctm.sctm_create(A, O, 4, o)[0] == sctm.SCTM_EINVAL
+    o.precision = sctm.SCTM_PREC_FP64
+    o.grad_mode = sctm.SCTM_GRAD_ADJOINT
+    assert sctm.sctm_create(A, O, 4, o)[0] == sctm.SCTM_EINVAL
+    o.grad_mode = sctm.SCTM_GRAD_ENV
+    o.method = 7
+    assert sctm.sctm_create(A, O, 4, o)[0] == sctm.SCTM_EINVAL

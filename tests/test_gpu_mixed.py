@@ -168,8 +168,10 @@ def test_mixed_full_size_moves(prec):
     (3, 10, 4.4, 4, 0.1, 30),
 ])
 def test_f64emu_parity_with_oracle(D, chi, T, seed, eps, iters):
-    """The FP64 emulation on the tensor cores in the move contractions: the same tolerances as the
-    FP64 path (f 1e-10, g 1e-8 against the oracle) on the contractive inputs."""
+    """SCTM_PREC_F64EMU at small sizes: no contraction here reaches the emulation's K >= 512 gate,
+    so every contraction runs on the FP64 kernels and the FP64 tolerances (f 1e-10, g 1e-8
+    against the oracle) must hold unchanged.  The emulation kernel itself is held to the same
+    tolerances at full size in tests/test_gpu_configs.py, where it launches."""
     A = inputs.perturbed_product_peps(D, seed, eps=eps)
     r = _ctx(A, T, chi, sctm.SCTM_PREC_F64EMU)
     try:
@@ -180,3 +182,24 @@ def test_f64emu_parity_with_oracle(D, chi, T, seed, eps, iters):
     ref = sc.evaluate(A, ising.ising_pepo(1 / T), ising.identity_pepo(), T, chi, iters)
     assert abs(f - ref['f']) <= 1e-10 * abs(ref['f']), (f, ref['f'])
     assert np.linalg.norm(g - ref['g']) <= 1e-8 * np.linalg.norm(ref['g'])
+
+
+@pytest.mark.parametrize('prec', [sctm.SCTM_PREC_TF32X3, sctm.SCTM_PREC_F64EMU])
+def test_bounded_wait_timeout_is_reported(prec, monkeypatch):
+    """Failure detection without a fault: with the test switch SCTM_TEST_FIRST_WAIT_ZERO=1 the
+    first mbarrier wait of every tensor-core CTA gives up at once; the kernel drains its copies and
+    MMAs with the normal bounded waits, frees its tensor memory, sets the error flag and returns,
+    so sctm_gemm reports SCTM_ETIMEOUT.  The next call, without the switch, succeeds and is
+    correct: the context is intact."""
+    X = inputs.random_matrix(300, 200, 31)
+    Y = inputs.random_matrix(200, 130, 32)
+    dX, dY = torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()
+    dO = torch.zeros((300, 130), dtype=torch.float64, device='cuda')
+    s = torch.cuda.current_stream().cuda_stream
+    monkeypatch.setenv('SCTM_TEST_FIRST_WAIT_ZERO', '1')
+    assert sctm.sctm_gemm(dX, dY, dO, 300, 130, 200, prec, s) == sctm.SCTM_ETIMEOUT
+    monkeypatch.delenv('SCTM_TEST_FIRST_WAIT_ZERO')
+    assert sctm.sctm_gemm(dX, dY, dO, 300, 130, 200, prec, s) == sctm.SCTM_OK
+    c, rel = FORMS[prec]
+    O = dO.cpu().numpy()
+    assert np.all(np.abs(O - X @ Y) <= c * (np.abs(X) @ np.abs(Y)) + 1e-300)

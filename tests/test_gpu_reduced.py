@@ -1,0 +1,57 @@
+"""GPU: the reduced method (Sec. II, Fig. 3), the comparison method of Sec. IV.A, against the
+oracle's independent reduced CTMRG (oracle/reduced_ctmrg.py): the same fused tensor, moves,
+projectors and cold start, so converged f and g agree to the FP64 tolerances; and the split
+method approaches it as chi grows (Sec. IV.A, the paper's own accuracy check)."""
+import numpy as np
+import pytest
+
+from oracle import ising, reduced_ctmrg
+from paper_2506_19339_gb300 import build, inputs, sctm
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope='module', autouse=True)
+def lib():
+    build.build()
+    return sctm.load()
+
+
+def _gpu(A, T, chi, method, svd_mode=sctm.SCTM_SVD_QR, tol=1e-11, max_it=400):
+    st, O = sctm.sctm_ising_pepo(T)
+    r = sctm.SplitCTMRG(A, O, chi, T, svd_mode=svd_mode, method=method)
+    try:
+        st, it, ds = r.iterate(max_it, tol)
+        return r.free_energy(), r.grad(), st, it
+    finally:
+        r.close()
+
+
+@pytest.mark.parametrize('D,chi,T,seed,eps', [(2, 16, 4.6, 7, 0.3), (3, 18, 4.5, 4, 0.1)])
+@pytest.mark.parametrize('svd_mode', [sctm.SCTM_SVD_QR, sctm.SCTM_SVD_PARTIAL_RANDOM])
+def test_reduced_matches_oracle(D, chi, T, seed, eps, svd_mode):
+    A = inputs.perturbed_product_peps(D, seed, eps=eps)
+    f, g, st, it = _gpu(A, T, chi, sctm.SCTM_METHOD_REDUCED, svd_mode)
+    assert st == sctm.SCTM_OK, (st, it)
+    ref = reduced_ctmrg.evaluate(A, ising.ising_pepo(1 / T), ising.identity_pepo(), T, chi, 400,
+                                 1e-12)
+    print('reduced D=%d chi=%d svd %d: %d iterations, |df|/|f| = %.1e, |dg|/|g| = %.1e' % (
+        D, chi, svd_mode, it, abs(f - ref['f']) / abs(ref['f']),
+        np.linalg.norm(g - ref['g']) / np.linalg.norm(ref['g'])))
+    assert abs(f - ref['f']) <= 1e-10 * abs(ref['f']), (f, ref['f'])
+    assert np.linalg.norm(g - ref['g']) <= 1e-8 * np.linalg.norm(ref['g'])
+
+
+def test_split_approaches_reduced_as_chi_grows():
+    """Sec. IV.A: the split result approaches the reduced method's at large chi, the gap shrinking
+    as chi grows (the paper's accuracy check, here with both methods on the GPU)."""
+    T, D = 4.6, 2
+    A = inputs.perturbed_product_peps(D, 7)
+    f_ref, *_ = _gpu(A, T, 48, sctm.SCTM_METHOD_REDUCED, sctm.SCTM_SVD_PARTIAL_RANDOM)
+    gaps = []
+    for chi in (8, 16, 24):
+        f, *_ = _gpu(A, T, chi, sctm.SCTM_METHOD_SPLIT, sctm.SCTM_SVD_PARTIAL_RANDOM, tol=1e-10)
+        gaps.append(abs(f - f_ref))
+    print('split vs reduced (chi=48) gaps at chi 8, 16, 24: %s' % ['%.1e' % x for x in gaps])
+    assert gaps[0] > gaps[1] > gaps[2]
+    assert gaps[2] < 1e-7
