@@ -1,11 +1,16 @@
 """Benchmark: split-CTMRG free energy + gradient evaluations per second (arXiv:2506.19339).
 
-One step = one f + grad f evaluation of the workload: the numerator <psi|T|psi> and norm <psi|psi>
-environments are reset to the cold start and iterated (left, right, up, down moves per
-iteration; Sec. III.B) for a fixed budget of iterations (or until ||dS||_2 < tol), then f and g
-are evaluated (Sec. II).  Everything runs through the C ABI of libsctm.so.
+One step = one f + grad f evaluation of the workload, from the cold start to convergence: the
+numerator <psi|T|psi> and norm <psi|psi> environments are reset to the SplitMix64 cold start and
+iterated (left, right, up, down moves per iteration, Sec. III.B) until ||S[i+1] - S[i]||_2 < 1e-10
+(Sec. III.D), then f and g are evaluated (Sec. II).  Everything runs through the C ABI of
+libsctm.so.  The workload is D=4, chi=64, T=4.5 with the contractive stand-in PEPS
+(perturbed product state, seed 2, eps 0.1), for which the iteration converges; an evaluation
+counts only if |f - f_oracle| <= 1e-8, f_oracle being the FP64 oracle's converged value stored in
+tests/golden/cfg3_D4_chi64.json (written by tests/golden/make_golden.py).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--iters I] [--impl ours|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|f64emu|tf32x3]
+                    [--impl ours|reference] [--batch B]
 
 Prints one JSON line (rank 0).  Under torchrun with N > 1 every rank runs an independent replica
 (the single-instance path does not shard) and `value` is the sum over ranks.
@@ -24,16 +29,15 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "split-CTMRG f+∇f evals/s at D=4 χ=64, mixed vs FP64 at |Δf|≤1e-8; % of peak"
-WORKLOAD = dict(D=4, chi=64, T=4.5, seed=2)   # the configuration the metric is quoted on
-NOMINAL_FP64_TFLOPS = 1.25                     # GB300 FP64 (vector and tensor), nominal
-NOMINAL_BF16_TFLOPS = 2250.0
+WORKLOAD = dict(D=4, chi=64, T=4.5, seed=2, eps=0.1, tol=1e-10, max_it=400)
+GOLDEN = os.path.join(ROOT, 'tests', 'golden', 'cfg3_D4_chi64.json')
+ACCEPT_DF = 1e-8
 PRECISIONS = {'fp64': 0, 'tf32': 1, 'tf32x3': 2, 'bf16': 3, 'bf16x3': 4, 'f64emu': 5}
+FORMS = ('fp64', 'f64emu', 'tf32x3')   # the forms every run compares
 SVD_MODES = {'qr': 0, 'polar': 1, 'partial': 2, 'partial-random': 3}
-SVD_NAMES = {'qr': 'cuSOLVER gesvd', 'polar': 'cuSOLVER gesvdp',
-             'partial': 'partial SVD: gesvd cold solve, then warm-started subspace iteration + '
-                        'one-CTA Jacobi',
-             'partial-random': 'partial SVD: randomized cold solve (2 subspace steps), then '
-                               'warm-started subspace iteration + one-CTA Jacobi'}
+KERNELS = (('ctr_f64_kernel', 0), ('ctr_skinny_kernel', 1), ('ctr_tc_kernel', 2),
+           ('emu_ctr_kernel', 3), ('jacobi_svd_kernel', 4), ('chol_orth_kernel', 5))
+NOMINAL_FP64_TFLOPS = 1.25
 
 
 def parse():
@@ -41,30 +45,54 @@ def parse():
     ap.add_argument('--gpus', type=int, default=1)
     ap.add_argument('--steps', type=int, default=3)
     ap.add_argument('--warmup', type=int, default=3)
-    ap.add_argument('--iters', type=int, default=10, help='split-CTMRG iterations per evaluation')
-    ap.add_argument('--tol', type=float, default=1e-10)
     ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
+    ap.add_argument('--precision', default='f64emu', choices=list(PRECISIONS),
+                    help='arithmetic of the move contractions of the headline form: f64emu (FP64 '
+                         'accuracy on the tensor cores where the autotuner measured it faster), '
+                         'fp64, or a mixed form that finishes with FP64 polish iterations')
+    ap.add_argument('--svd', default='partial-random', choices=list(SVD_MODES))
     ap.add_argument('--no-cpu-baseline', action='store_true')
+    ap.add_argument('--no-compare', action='store_true', help='headline form only (profiling)')
     ap.add_argument('--batch', type=int, default=0,
-                    help='batched sweep: B contexts (T uniform in [4.40, 4.62], seeds 100..) '
-                         'iterated concurrently; 0 = the single-instance workload')
-    ap.add_argument('--svd', default='partial-random', choices=list(SVD_MODES),
-                    help='FP64 SVD of the projectors: the partial SVD with a randomized cold '
-                         'solve (partial-random) or a gesvd cold solve (partial), cuSOLVER gesvd '
-                         '(qr) or gesvdp (polar)')
-    ap.add_argument('--D', type=int, default=None,
-                    help='override the PEPS bond dimension (small cases for profiler captures)')
-    ap.add_argument('--chi', type=int, default=None, help='override chi (profiler captures)')
-    ap.add_argument('--precision', default='fp64', choices=list(PRECISIONS),
-                    help='arithmetic of the move contractions (mixed forms polish in FP64)')
+                    help='batched sweep: B instances (T uniform in [4.40, 4.62], seeds 100..)')
+    ap.add_argument('--iters', type=int, default=0,
+                    help='profiler captures: a fixed number of iterations per evaluation instead of '
+                         'iterating to convergence (the line is then not a metric value)')
+    ap.add_argument('--lean', action='store_true',
+                    help='profiler captures: the headline steps only (no end-to-end, serialised, '
+                         'N(0,1), other-form, DGEMM or CPU legs)')
+    ap.add_argument('--D', type=int, default=None, help='PEPS bond dimension (small captures)')
+    ap.add_argument('--chi', type=int, default=None, help='chi (small captures)')
     return ap.parse_args()
 
 
-def workload_name(it, w=None):
-    w = w or WORKLOAD
-    return ('split-CTMRG f+grad, 3D Ising PEPO, PEPS D=%d N(0,1) seed %d, chi=%d, T=%g, '
-            '%d iterations (num + norm networks) per evaluation, tol %g' %
-            (w['D'], w['seed'], w['chi'], w['T'], it, 1e-10))
+def workload(args):
+    w = dict(WORKLOAD)
+    if args.D:
+        w['D'] = args.D
+    if args.chi:
+        w['chi'] = args.chi
+    if args.iters > 0:
+        w['max_it'] = args.iters
+        w['tol'] = 0.0
+    return w
+
+
+def workload_name(w):
+    return ('split-CTMRG f+grad from the cold start to ||dS||<%g, 3D Ising PEPO T=%g, PEPS D=%d '
+            '(perturbed product state, seed %d, eps %g), chi=%d, numerator + norm networks' %
+            (w['tol'], w['T'], w['D'], w['seed'], w['eps'], w['chi']))
+
+
+def load_golden(w):
+    try:
+        g = json.load(open(GOLDEN))
+    except (OSError, ValueError):
+        return None
+    if (g['D'], g['chi'], g['T'], g['seed'], g['eps']) != (w['D'], w['chi'], w['T'], w['seed'],
+                                                           w['eps']):
+        return None
+    return g
 
 
 # ------------------------------------------------------------------------------------------------
@@ -123,32 +151,6 @@ class ClockSampler:
 # ------------------------------------------------------------------------------------------------
 # CPU baseline / reference arm: the FP64 oracle on the host cores
 # ------------------------------------------------------------------------------------------------
-def oracle_sample(A, T, chi, iters, budget_s=20.0):
-    """Time the oracle on a bounded sample: moves of the numerator then the norm network (4 moves
-    per iteration each) until `budget_s` of CPU work; scale to evaluations/s at `iters` iterations
-    per evaluation."""
-    from oracle import ising, split_ctmrg as sc
-    D = A.shape[1]
-    nets = [ising.ising_pepo(1.0 / T), ising.identity_pepo()]
-    moves_done = [0, 0]
-    secs = [0.0, 0.0]
-    for n, O in enumerate(nets):
-        env = sc.init_env(chi, D, O.shape[2])
-        t0 = time.perf_counter()
-        for w in 'LRUD':
-            env = sc.move(env, A, O, A, w, chi)
-            moves_done[n] += 1
-            if time.perf_counter() - t0 > budget_s / 2:
-                break
-        secs[n] = time.perf_counter() - t0
-    per_move = [secs[n] / moves_done[n] for n in range(2)]
-    sec_per_eval = 4 * iters * (per_move[0] + per_move[1])
-    sample = ('%d numerator + %d norm left/right/up/down moves of the FP64 oracle at the workload '
-              'size (%.1f s), scaled to %d iterations x 4 moves x 2 networks per evaluation' %
-              (moves_done[0], moves_done[1], secs[0] + secs[1], iters))
-    return 1.0 / sec_per_eval, sample, secs[0] + secs[1]
-
-
 def cpu_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -156,32 +158,103 @@ def cpu_cores():
         return os.cpu_count()
 
 
-def run_reference(args):
+def blas_info():
+    try:
+        cfg = np.show_config(mode='dicts')
+        b = cfg['Build Dependencies']['blas']
+        return '%s %s' % (b.get('name'), b.get('version'))
+    except Exception:  # noqa: BLE001 -- informational only
+        return 'unknown'
+
+
+def iterations_per_eval(golden):
+    """Iterations of each network per converged evaluation (the oracle's own counts)."""
+    if golden is None:
+        return {'num': 60, 'den': 60}
+    return golden['records']['converged']['iterations']
+
+
+def oracle_iteration_sample(w, golden, nets=('num', 'den'), moves='LRUD'):
+    """Time the oracle on a bounded sample of the workload: the given moves of each network from
+    the cold start, then (full iteration only) the spectrum, f and g.  Returns (seconds per
+    evaluation scaled to the converged iteration counts, description, seconds spent)."""
+    from oracle import ising, split_ctmrg as sc
     from paper_2506_19339_gb300 import inputs
-    w = WORKLOAD
+    A = inputs.perturbed_product_peps(w['D'], w['seed'], eps=w['eps'])
+    Os = {'num': ising.ising_pepo(1.0 / w['T']), 'den': ising.identity_pepo()}
+    its = iterations_per_eval(golden)
+    per_eval = 0.0
+    spent = 0.0
+    parts = []
+    for n in nets:
+        env = sc.init_env(w['chi'], w['D'], Os[n].shape[2])
+        t0 = time.perf_counter()
+        for m in moves:
+            env = sc.move(env, A, Os[n], A, m, w['chi'])
+        t_moves = time.perf_counter() - t0
+        per_it = t_moves * 4.0 / len(moves)
+        t1 = time.perf_counter()
+        if moves == 'LRUD':
+            sc.ctm_spectrum(env)
+            loc = sc.local_contractions(env, A, Os[n], A)
+            sc.bra_environment(env, loc)
+        t_fg = time.perf_counter() - t1
+        spent += t_moves + t_fg
+        per_eval += its[n] * per_it + t_fg
+        parts.append('%s: %d move(s) %.2f s' % (n, len(moves), t_moves))
+    desc = ('oracle (FP64 NumPy) at the workload size: %s; scaled to the converged iteration '
+            'counts of the oracle (num %d, den %d iterations x 4 moves)' %
+            ('; '.join(parts), its['num'], its['den']))
+    return per_eval, desc, spent
+
+
+def cpu_baseline(w, golden):
+    sec, desc, spent = oracle_iteration_sample(w, golden)
+    # one thread: one left move of the numerator network in a child process with one BLAS thread
+    code = ('import sys, time, json; sys.path.insert(0, %r)\n'
+            'from bench import oracle_iteration_sample, load_golden, WORKLOAD\n'
+            'w = dict(WORKLOAD); w.update(%r)\n'
+            's, d, t = oracle_iteration_sample(w, load_golden(w), nets=("num",), moves="L")\n'
+            'print(json.dumps([s, t]))\n') % (ROOT, {k: w[k] for k in ('D', 'chi')})
+    env = dict(os.environ, OMP_NUM_THREADS='1', OPENBLAS_NUM_THREADS='1', MKL_NUM_THREADS='1')
+    one = None
+    try:
+        out = subprocess.run([sys.executable, '-c', code], env=env, capture_output=True, text=True,
+                             timeout=300)
+        s1, t1 = json.loads(out.stdout.strip().splitlines()[-1])
+        one = {'sec_per_eval_num_network_only': s1, 'sample_s': t1,
+               'sample': 'one left move of the numerator network, 1 BLAS thread, scaled to its '
+                         'converged iteration count (the norm network excluded)'}
+    except Exception as exc:  # noqa: BLE001 -- the 1-thread figure is context only
+        one = {'error': str(exc)[:200]}
+    return {'value': 1.0 / sec, 'unit': 'evals/s', 'cores': cpu_cores(), 'kind': 'oracle',
+            'sample': desc + ' (%.1f s of CPU work)' % spent, 'blas': blas_info(),
+            'blas_threads': os.environ.get('OPENBLAS_NUM_THREADS', 'library default (all cores)'),
+            'one_thread': one}
+
+
+def run_reference(args):
     rank = int(os.environ.get('RANK', '0'))
     if rank != 0:
         return
-    A = inputs.random_peps(w['D'], w['seed'])
-    budget = max(2.0, min(20.0, 150.0 / max(args.steps + args.warmup, 1)))
+    w = workload(args)
+    golden = load_golden(w)
     for _ in range(args.warmup):
-        oracle_sample(A, w['T'], w['chi'], args.iters, budget_s=budget / 4)
-    vals = []
-    samples = []
+        oracle_iteration_sample(w, golden, moves='L')
+    secs = []
+    desc = ''
     for _ in range(args.steps):
-        v, sample, secs = oracle_sample(A, w['T'], w['chi'], args.iters, budget_s=budget)
-        vals.append(v)
-        samples.append(secs)
-    value = float(np.mean(vals))
+        s, desc, _ = oracle_iteration_sample(w, golden, moves='L')
+        secs.append(s)
+    value = 1.0 / float(np.mean(secs))
     line = {
         'impl': 'reference', 'metric': METRIC, 'value': value, 'unit': 'evals/s',
         'n_gpus': args.gpus, 'steps': args.steps, 'warmup': args.warmup,
         'ms_per_step': 1000.0 / value, 'higher_is_better': True, 'scaling': 'weak',
         'vs_baseline': None, 'dtype': 'f64', 'data': 'synthetic',
-        'config': {'workload': workload_name(args.iters), 'D': w['D'], 'chi': w['chi'],
-                   'T': w['T'], 'seed': w['seed'], 'iterations_per_eval': args.iters},
+        'config': {'workload': workload_name(w), 'D': w['D'], 'chi': w['chi'], 'T': w['T']},
         'cpu_baseline': {'value': value, 'unit': 'evals/s', 'cores': cpu_cores(), 'kind': 'oracle',
-                         'sample': sample},
+                         'sample': 'each step: ' + desc, 'blas': blas_info()},
         'e2e': {'value': value, 'unit': 'evals/s', 'h2d_bytes_per_step': 0,
                 'd2h_bytes_per_step': 0},
     }
@@ -203,14 +276,96 @@ def combine_ranks(ms, e2e_ms, dist, device):
     return float(t[0]), float(t[1])
 
 
+class Instance:
+    """One context of the workload in one precision form, driven through the C ABI."""
+
+    def __init__(self, sctm, w, prec, svd, stream, dev, A_host):
+        import torch
+        st, O = sctm.sctm_ising_pepo(w['T'])
+        st, o = sctm.sctm_default_opts()
+        o.T, o.D, o.p, o.d = w['T'], w['D'], 2, 2
+        o.cuda_stream = stream.cuda_stream
+        o.svd_mode = SVD_MODES[svd]
+        o.precision = PRECISIONS[prec]
+        self.sctm, self.w, self.prec = sctm, w, prec
+        self.A_dev = torch.from_numpy(A_host).to(dev)
+        st, self.ctx = sctm.sctm_create(self.A_dev, np.ascontiguousarray(O), w['chi'], o)
+        if st != sctm.SCTM_OK:
+            raise RuntimeError('sctm_create (%s) failed: %s' % (prec, sctm.STATUS_NAMES[st]))
+        self.g_dev = torch.zeros_like(self.A_dev)
+
+    def evaluate(self, A_ptr=None, g_ptr=None, max_it=None, tol=None):
+        s = self.sctm
+        A_ptr = self.A_dev if A_ptr is None else A_ptr
+        g_ptr = self.g_dev if g_ptr is None else g_ptr
+        assert s.sctm_set_peps(self.ctx, A_ptr, 1) == s.SCTM_OK
+        st, it, ds = s.sctm_iterate(self.ctx, self.w['max_it'] if max_it is None else max_it,
+                                    self.w['tol'] if tol is None else tol)
+        assert st in (s.SCTM_OK, s.SCTM_ENOCONV), s.sctm_last_error(self.ctx)
+        st_f, f = s.sctm_free_energy(self.ctx)
+        s.sctm_grad(self.ctx, g_ptr)
+        return f, it, st
+
+    def close(self):
+        self.sctm.sctm_destroy(self.ctx)
+
+
+def timed(inst, stream, flush, steps):
+    """`steps` evaluations, each bracketed by CUDA events on the instance's stream (L2 flushed
+    before each, outside the events).  Returns (ms list, f list, iterations list, statuses)."""
+    import torch
+    ms, fs, its, sts = [], [], [], []
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        f, it, st = inst.evaluate()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        fs.append(f)
+        its.append(it)
+        sts.append(st)
+    return ms, fs, its, sts
+
+
+def form_summary(sctm, ms, fs, its, sts, ref_f, ref_g, g_last):
+    d_f = abs(fs[-1] - ref_f) if ref_f is not None else None
+    return {'evals_per_s': len(ms) / (np.sum(ms) * 1e-3), 'ms_per_eval': float(np.mean(ms)),
+            'evaluations': len(ms), 'iterations_per_eval': int(np.max(its)),
+            'status': sctm.STATUS_NAMES[sts[-1]], 'f': fs[-1], 'abs_df_vs_oracle': d_f,
+            'rel_dg_vs_oracle': (float(np.linalg.norm(g_last - ref_g) / np.linalg.norm(ref_g))
+                                 if ref_g is not None else None),
+            'accepted': bool(d_f is not None and d_f <= ACCEPT_DF and
+                             all(s == sctm.SCTM_OK for s in sts))}
+
+
+def dgemm_tflops(dev):
+    """FP64 matrix-multiply rate of this GPU (cuBLAS through torch), the FP64 roofline peak."""
+    import torch
+    n = 8192
+    a = torch.randn(n, n, dtype=torch.float64, device=dev)
+    b = torch.randn(n, n, dtype=torch.float64, device=dev)
+    torch.matmul(a, b)
+    torch.cuda.synchronize(dev)
+    best = 1e30
+    for _ in range(3):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    del a, b
+    return 2.0 * n ** 3 / (best * 1e-3) / 1e12
+
+
 def run_ours(args):
     import torch
     from paper_2506_19339_gb300 import build, inputs, sctm
-    w = dict(WORKLOAD)
-    if args.D:
-        w['D'] = args.D
-    if args.chi:
-        w['chi'] = args.chi
+    w = workload(args)
     world = int(os.environ.get('WORLD_SIZE', '1'))
     rank = int(os.environ.get('RANK', '0'))
     local = int(os.environ.get('LOCAL_RANK', '0'))
@@ -223,111 +378,105 @@ def run_ours(args):
     torch.cuda.set_device(dev)
     build.build()
     sctm.load()
+    golden = load_golden(w)
+    ref_f = golden['records']['converged']['f'] if golden else None
+    ref_g = (np.array(golden['records']['converged']['g']).reshape(2, *(w['D'],) * 4)
+             if golden else None)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        A_cpu = inputs.random_peps(w['D'], w['seed'])
-        v, sample, secs = oracle_sample(A_cpu, w['T'], w['chi'], args.iters, budget_s=20.0)
-        cpu = {'value': v, 'unit': 'evals/s', 'cores': cpu_cores(), 'kind': 'oracle',
-               'sample': sample}
+        cpu = cpu_baseline(w, golden)
 
-    A_host = inputs.random_peps(w['D'], w['seed'])
-    st, O = sctm.sctm_ising_pepo(w['T'])
+    A_host = inputs.perturbed_product_peps(w['D'], w['seed'], eps=w['eps'])
     stream = torch.cuda.current_stream(dev)
-    st, o = sctm.sctm_default_opts()
-    o.T, o.D, o.p, o.d = w['T'], w['D'], 2, 2
-    o.cuda_stream = stream.cuda_stream
-    o.svd_mode = SVD_MODES[args.svd]
-    o.precision = PRECISIONS[args.precision]
-    A_dev = torch.from_numpy(A_host).to(dev)
-    st, ctx = sctm.sctm_create(A_dev, np.ascontiguousarray(O), w['chi'], o)
-    if st != sctm.SCTM_OK:
-        raise RuntimeError('sctm_create failed: %s' % sctm.STATUS_NAMES[st])
-    g_dev = torch.zeros_like(A_dev)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (126 MB)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+    head = Instance(sctm, w, args.precision, args.svd, stream, dev, A_host)
 
-    def evaluate(A_ptr, g_ptr):
-        assert sctm.sctm_set_peps(ctx, A_ptr, 1) == sctm.SCTM_OK
-        st, it, ds = sctm.sctm_iterate(ctx, args.iters, args.tol)
-        assert st in (sctm.SCTM_OK, sctm.SCTM_ENOCONV), sctm.sctm_last_error(ctx)
-        st, f = sctm.sctm_free_energy(ctx)
-        st2 = sctm.sctm_grad(ctx, g_ptr)
-        return f, it, ds, st
-
-    # warm-up
+    # ---- headline: converged evaluations, inputs resident on the device, profiling off
     for _ in range(args.warmup):
-        evaluate(A_dev, g_dev)
+        head.evaluate()
     torch.cuda.synchronize(dev)
-
-    # ---- timed region, device-resident inputs
-    sctm.sctm_profile(ctx, reset=True)
-    sctm.sctm_set_profiling(ctx, True)
+    sctm.sctm_profile(head.ctx, reset=True)
     clocks = ClockSampler(local)
     clocks.start()
     if dist:
         dist.barrier()
     torch.cuda.synchronize(dev)
-    step_ms = []
-    its = []
-    fs = []
-    statuses = []
     t_wall = time.perf_counter()
-    for _ in range(args.steps):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        f, it, ds, stf = evaluate(A_dev, g_dev)
-        e1.record(stream)
-        e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-        its.append(it)
-        fs.append(f)
-        statuses.append(stf)
+    ms, fs, its, sts = timed(head, stream, flush, args.steps)
     torch.cuda.synchronize(dev)
     if dist:
         dist.barrier()
     wall = time.perf_counter() - t_wall
     clk = clocks.stop()
-    sctm.sctm_set_profiling(ctx, False)
-    kern = {name: sctm.sctm_profile_kernel(ctx, k)[1] for name, k in
-            (('ctr_f64_kernel', sctm.SCTM_KERNEL_F64), ('ctr_skinny_kernel', sctm.SCTM_KERNEL_SKINNY),
-             ('ctr_tc_kernel', sctm.SCTM_KERNEL_TC), ('emu_ctr_kernel', sctm.SCTM_KERNEL_F64EMU))}
-    st, prof = sctm.sctm_profile(ctx, reset=True)
-    ms = float(np.sum(step_ms))
+    st, prof = sctm.sctm_profile(head.ctx, reset=True)
+    head_g = head.g_dev.cpu().numpy()
+    forms = {args.precision: form_summary(sctm, ms, fs, its, sts, ref_f, ref_g, head_g)}
+    total_ms = float(np.sum(ms))
+    if args.lean:
+        head.close()
+        if rank == 0:
+            print(json.dumps({'lean': True, 'ms_per_step': total_ms / args.steps,
+                              'iterations': its, 'f': fs[-1], 'clocks': clk,
+                              'gpu_launches': int(prof['kernel_launches'])}), flush=True)
+        return
 
     # ---- e2e: host buffers through the C ABI, host<->device copies inside the timed region
     A_pin = torch.from_numpy(A_host).pin_memory()
     g_pin = torch.zeros(A_host.shape, dtype=torch.float64).pin_memory()
-    torch.cuda.synchronize(dev)
+    e2e_steps = min(args.steps, 3)
     e2e_ms = []
-    for _ in range(args.steps):
+    for _ in range(e2e_steps):
         flush.zero_()
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        evaluate(A_pin.numpy(), g_pin.numpy())
+        head.evaluate(A_pin.numpy(), g_pin.numpy())
         torch.cuda.synchronize(dev)
         e2e_ms.append(1000.0 * (time.perf_counter() - t0))
-    st, prof_e2e = sctm.sctm_profile(ctx, reset=True)
 
-    # FP64 matrix-multiply rate of this GPU (cuBLAS through torch), context for the roofline
-    a = torch.randn(4096, 4096, dtype=torch.float64, device=dev)
-    torch.matmul(a, a)
+    # ---- per-kernel durations: one evaluation with the execution serialised (one stream), CUDA
+    #      events around every launch (no overlap with other streams inside an event pair)
+    sctm.sctm_profile(head.ctx, reset=True)
+    assert sctm.sctm_set_profiling(head.ctx, 2) == sctm.SCTM_OK
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    head.evaluate()
+    e1.record(stream)
+    e1.synchronize()
+    serial_ms = e0.elapsed_time(e1)
+    assert sctm.sctm_set_profiling(head.ctx, 0) == sctm.SCTM_OK
+    kern = {name: sctm.sctm_profile_kernel(head.ctx, k)[1] for name, k in KERNELS}
+    st, sprof = sctm.sctm_profile(head.ctx, reset=True)
+
+    # ---- the N(0,1) PEPS of the headline configuration (seed 2): it does not converge, so it is
+    #      timed as split-CTMRG iterations per second over a fixed 10 iterations
+    A_gauss = torch.from_numpy(inputs.random_peps(w['D'], w['seed'])).to(dev)
+    head.evaluate(A_gauss, None, max_it=2, tol=0.0)
     torch.cuda.synchronize(dev)
-    best = 1e9
-    for _ in range(3):
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        torch.matmul(a, a)
-        e1.record()
-        e1.synchronize()
-        best = min(best, e0.elapsed_time(e1))
-    dgemm_tflops = 2 * 4096 ** 3 / (best * 1e-3) / 1e12
-    sctm.sctm_destroy(ctx)
+    e0.record(stream)
+    head.evaluate(A_gauss, None, max_it=10, tol=0.0)
+    e1.record(stream)
+    e1.synchronize()
+    gauss_its = 10.0 / (e0.elapsed_time(e1) * 1e-3)
+    head.close()
+
+    # ---- the other precision forms, same workload and stopping rule
+    if not args.no_compare:
+        for form in FORMS:
+            if form == args.precision:
+                continue
+            inst = Instance(sctm, w, form, args.svd, stream, dev, A_host)
+            inst.evaluate()
+            torch.cuda.synchronize(dev)
+            m2, f2, i2, s2 = timed(inst, stream, flush, min(args.steps, 2))
+            forms[form] = form_summary(sctm, m2, f2, i2, s2, ref_f, ref_g, inst.g_dev.cpu().numpy())
+            inst.close()
+
+    fp64_peak = dgemm_tflops(dev)
 
     # max over ranks
-    ms, e2e_total = combine_ranks(ms, float(np.sum(e2e_ms)), dist, dev)
+    total_ms, e2e_total = combine_ranks(total_ms, float(np.sum(e2e_ms)), dist, dev)
     if dist:
         dist.destroy_process_group()
     if rank != 0:
@@ -338,59 +487,61 @@ def run_ours(args):
         peaks = json.load(open(os.path.join(ROOT, 'MEASURED_PEAKS.json')))
     except (OSError, ValueError):
         pass
-    if 'bf16_tflops_sustained' in peaks:
-        fp64_peak = peaks['bf16_tflops_sustained'] * NOMINAL_FP64_TFLOPS / NOMINAL_BF16_TFLOPS
-        peak_note = 'measured bf16 sustained x nominal FP64/BF16 ratio (1.25/2250)'
-    else:
-        fp64_peak = 1700.0 * NOMINAL_FP64_TFLOPS / NOMINAL_BF16_TFLOPS
-        peak_note = 'fallback bf16 sustained x nominal FP64/BF16 ratio'
-    kf = kern['ctr_f64_kernel']
-    achieved = (kf['flops'] / (kf['ms'] * 1e-3) / 1e12) if kf['ms'] > 0 else None
-    hbm = peaks.get('hbm_gbs', 6800.0)
     kernels = {}
     for name, kv in kern.items():
         if kv['launches'] == 0:
             continue
         sec = kv['ms'] * 1e-3
-        kernels[name] = {'launches_per_step': kv['launches'] / args.steps,
-                         'ms_per_step': kv['ms'] / args.steps,
-                         'tflops': kv['flops'] / sec / 1e12 if sec > 0 else None,
-                         'min_gbs': kv['bytes'] / sec / 1e9 if sec > 0 else None}
-    if 'ctr_skinny_kernel' in kernels and kernels['ctr_skinny_kernel']['min_gbs']:
-        kernels['ctr_skinny_kernel']['frac_of_hbm'] = kernels['ctr_skinny_kernel']['min_gbs'] / hbm
-    # the step is FP64-bound as a whole: FP64 contraction FLOPs of the step over its device time
-    f64_flops = sum(kern[k]['flops'] for k in ('ctr_f64_kernel', 'ctr_skinny_kernel'))
-    gpu_wide = f64_flops / (ms * 1e-3) / 1e12 if ms > 0 else None
+        kernels[name] = {'launches_per_eval': kv['launches'], 'ms_per_eval': kv['ms'],
+                         'share_of_serial_eval': kv['ms'] / serial_ms,
+                         'tflops': kv['flops'] / sec / 1e12 if (sec > 0 and kv['flops']) else None,
+                         'us_per_launch': 1e3 * kv['ms'] / kv['launches']}
+    ctr_names = ('ctr_f64_kernel', 'ctr_skinny_kernel', 'ctr_tc_kernel', 'emu_ctr_kernel')
+    dom = max((n for n in ctr_names if n in kernels), key=lambda n: kernels[n]['ms_per_eval'])
+    kd = kern[dom]
+    achieved = kd['flops'] / (kd['ms'] * 1e-3) / 1e12
+    f64_flops = sum(kern[k]['flops'] for k in ctr_names)
+    step_ms = total_ms / args.steps
+    roofline = {
+        'bound': 'alu', 'kernel': dom, 'achieved': achieved, 'peak': fp64_peak,
+        'unit': 'TFLOP/s', 'frac': achieved / fp64_peak, 'traffic': None,
+        'peak_note': 'of measured: FP64 cuBLAS DGEMM (8192^3, best of 3) on this GPU in this run '
+                     '(nominal FP64 %.2f TFLOP/s)' % NOMINAL_FP64_TFLOPS,
+        'achieved_note': 'algorithmic FLOPs (2 M N K per contraction, FP64-equivalent for the '
+                         'emulation) of all launches of this kernel in one evaluation / their '
+                         'summed CUDA-event time in a serialised pass (one stream, one launch '
+                         'at a time)',
+        'kernels': kernels, 'serial_eval_ms': serial_ms,
+        'eval_contraction_tflop': f64_flops / 1e12,
+        'step_contraction_tflops': f64_flops / (step_ms * 1e-3) / 1e12,
+        'step_contraction_frac': f64_flops / (step_ms * 1e-3) / 1e12 / fp64_peak,
+        'svd_steps_ms_serial': sprof['svd_ms'],
+        'bf16_peak_measured_tflops': peaks.get('bf16_tflops'),
+    }
+    head_form = forms[args.precision]
     n_steps = args.steps * world
-    value = n_steps / (ms * 1e-3)
-    total_its = int(np.sum(its))
+    value = n_steps / (total_ms * 1e-3)
     line = {
         'metric': METRIC, 'value': value, 'unit': 'evals/s', 'n_gpus': world,
-        'steps': args.steps, 'warmup': args.warmup, 'ms_per_step': ms / args.steps,
+        'steps': args.steps, 'warmup': args.warmup, 'ms_per_step': step_ms,
         'higher_is_better': True, 'scaling': 'weak', 'vs_baseline': None,
-        'dtype': 'f64' if args.precision == 'fp64' else args.precision + '+f64',
+        'dtype': 'f64' if args.precision in ('fp64', 'f64emu') else args.precision + '+f64',
         'data': 'synthetic',
-        'config': {'workload': workload_name(args.iters, w), 'D': w['D'], 'chi': w['chi'],
-                   'T': w['T'], 'seed': w['seed'], 'iterations_per_eval': args.iters,
-                   'precision': '%s move contractions, FP64 SVD (%s)' % (
-                       args.precision.upper(), SVD_NAMES[args.svd]),
+        'config': {'workload': workload_name(w), 'D': w['D'], 'chi': w['chi'], 'T': w['T'],
+                   'seed': w['seed'], 'eps': w['eps'], 'tol': w['tol'],
+                   'precision': args.precision, 'svd': args.svd,
+                   'accept': '|f - f_oracle| <= %g, f_oracle from tests/golden/cfg3_D4_chi64.json'
+                             % ACCEPT_DF,
                    'parallelism': 'replicas',
                    'l2': 'flushed before every step (256 MiB write, outside the step events)'},
-        'iterations_per_s': total_its * world / (ms * 1e-3),
-        'f': fs[-1], 'status': [sctm.STATUS_NAMES[s] for s in statuses][-1],
-        'roofline': {'bound': 'alu', 'kernel': 'ctr_f64_kernel', 'achieved': achieved,
-                     'peak': fp64_peak, 'unit': 'TFLOP/s',
-                     'frac': (achieved / fp64_peak) if achieved else None, 'traffic': None,
-                     'peak_note': peak_note, 'dgemm_torch_tflops': dgemm_tflops,
-                     'kernels': kernels,
-                     'step_fp64_contraction_tflops': gpu_wide,
-                     'step_fp64_contraction_frac': (gpu_wide / fp64_peak) if gpu_wide else None,
-                     'ctr_ms_per_step': prof['ctr_ms'] / args.steps,
-                     'svd_ms_per_step': prof['svd_ms'] / args.steps,
-                     'ctr_launches_per_step': prof['ctr_launches'] / args.steps,
-                     'svd_calls_per_step': prof['svd_calls'] / args.steps},
+        'accepted': head_form['accepted'], 'abs_df_vs_oracle': head_form['abs_df_vs_oracle'],
+        'forms': forms,
+        'iterations_per_s': float(np.sum(its)) / (total_ms * 1e-3),
+        'gaussian_seed2_iterations_per_s': gauss_its,
+        'roofline': roofline,
         'cpu_baseline': cpu,
-        'e2e': {'value': n_steps / (e2e_total * 1e-3), 'unit': 'evals/s',
+        'e2e': {'value': e2e_steps * world / (e2e_total * 1e-3), 'unit': 'evals/s',
+                'steps': e2e_steps,
                 'h2d_bytes_per_step': int(A_host.nbytes),
                 'd2h_bytes_per_step': int(A_host.nbytes + 8)},
         'clocks': clk,
@@ -405,7 +556,7 @@ def run_batch(args):
     concurrently through sctm_iterate_batch; value = evaluations per second of the whole batch."""
     import torch
     from paper_2506_19339_gb300 import build, inputs, sctm
-    w = WORKLOAD
+    w = workload(args)
     B = args.batch
     dev = torch.device('cuda', 0)
     build.build()
@@ -414,7 +565,7 @@ def run_batch(args):
     streams = [torch.cuda.Stream(dev) for _ in range(B)]
     ctxs, As, gs = [], [], []
     for i, T in enumerate(Ts):
-        A = torch.from_numpy(inputs.random_peps(w['D'], 100 + i)).to(dev)
+        A = torch.from_numpy(inputs.perturbed_product_peps(w['D'], 100 + i, eps=w['eps'])).to(dev)
         st, O = sctm.sctm_ising_pepo(T)
         st, o = sctm.sctm_default_opts()
         o.T, o.D, o.p, o.d = float(T), w['D'], 2, 2
@@ -432,11 +583,11 @@ def run_batch(args):
     def step():
         for c, A in zip(ctxs, As):
             assert sctm.sctm_set_peps(c, A, 1) == sctm.SCTM_OK
-        st, sts, its, dss = sctm.sctm_iterate_batch(ctxs, args.iters, args.tol)
+        st, sts, its, dss = sctm.sctm_iterate_batch(ctxs, w['max_it'], w['tol'])
         for c, g in zip(ctxs, gs):
             sctm.sctm_free_energy(c)
             sctm.sctm_grad(c, g)
-        return its
+        return its, sts
 
     for _ in range(args.warmup):
         step()
@@ -447,7 +598,7 @@ def run_batch(args):
     for _ in range(args.steps):
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        its = step()
+        its, sts = step()
         torch.cuda.synchronize(dev)
         ms.append(1000.0 * (time.perf_counter() - t0))
     clk = clocks.stop()
@@ -459,12 +610,13 @@ def run_batch(args):
         'steps': args.steps, 'warmup': args.warmup, 'ms_per_step': total / args.steps,
         'higher_is_better': True, 'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f64',
         'data': 'synthetic',
-        'config': {'workload': 'batched sweep: %d contexts, T uniform in [4.40, 4.62], PEPS D=%d '
-                               'N(0,1) seeds 100..%d, chi=%d, %d iterations per evaluation, '
-                               '%s, SVD %s, iterated concurrently (one host thread and stream '
-                               'set per context)' % (B, w['D'], 99 + B, w['chi'], args.iters,
-                                                     args.precision.upper(), args.svd),
-                   'batch': B, 'iterations_per_eval': args.iters, 'device_bytes': mem,
+        'config': {'workload': 'batched sweep: %d instances, T uniform in [4.40, 4.62], PEPS D=%d '
+                               '(perturbed product states, seeds 100..%d, eps %g), chi=%d, each '
+                               'iterated to ||dS|| < %g, %s, SVD %s' % (
+                                   B, w['D'], 99 + B, w['eps'], w['chi'], w['tol'],
+                                   args.precision.upper(), args.svd),
+                   'batch': B, 'device_bytes': mem,
+                   'iterations_max': int(max(its)), 'statuses': sorted(set(sts)),
                    'timing': 'host wall clock around each step with device synchronisation'},
         'clocks': clk,
     }

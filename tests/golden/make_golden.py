@@ -28,12 +28,13 @@ from oracle import ising, split_ctmrg as sc  # noqa: E402
 from paper_2506_19339_gb300 import inputs  # noqa: E402
 
 # name: (D, chi, T, seed, eps, records, tol, max_iter); records are iteration counts and/or
-# 'converged'
+# 'converged'.  Only the converged records are compared: the first iterations from the random
+# cold start are chaotic (a relative 1e-15 change of A, or another BLAS thread count, moves f
+# after two iterations by percents at D=4, chi=64), so a fixed-iteration record is context only.
 CASES = {
     'cfg2_D3_chi36': (3, 36, 4.5115, 1, 0.1, [2, 'converged'], 1e-12, 400),
     'cfg3_D4_chi64': (4, 64, 4.5, 2, 0.1, [2, 'converged'], 1e-11, 300),
     'cfg4_D5_chi100': (5, 100, 4.52, 3, 0.1, [2, 'converged'], 1e-11, 300),
-    'cfg5b_D6_chi144': (6, 144, 4.5115, 4, 0.1, [2], None, 2),
 }
 
 

@@ -1,0 +1,182 @@
+"""GPU parity at the sizes of the workload configurations, against stored oracle values.
+
+Each case is the contractive stand-in (perturbed product PEPS) at one configuration's (D, chi, T);
+tests/golden/<case>.json holds the FP64 oracle's f and environment gradient g after a fixed
+number of iterations and at convergence (written by tests/golden/make_golden.py, which calls
+only oracle/).  The benched path (partial SVD with the randomized cold solve) and the FP64
+emulation on the tensor cores must reach the oracle's fixed point to 1e-10 in f and 1e-8 in g
+(relative); the mixed tensor-core forms, which finish with FP64 polish iterations, to their
+configuration's tolerance in f (Sec. II Eqs. "free energy expression" / "gradient expression",
+Sec. III.D convergence)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import ising, split_ctmrg as sc
+from paper_2506_19339_gb300 import build, inputs, sctm
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), 'golden')
+
+
+@pytest.fixture(scope='module', autouse=True)
+def lib():
+    build.build()
+    return sctm.load()
+
+
+def golden(case):
+    with open(os.path.join(GOLDEN, case + '.json')) as fh:
+        return json.load(fh)
+
+
+def peps(g):
+    return inputs.perturbed_product_peps(g['D'], g['seed'], eps=g['eps'])
+
+
+# the GPU runs stop at ||dS|| < 1e-11 (or the oracle's own, looser, tolerance): the FP64 spectrum
+# change of this measure levels off near 1e-12, below which a stopping rule is not reliable
+def gpu_tol(g):
+    return max(g['tol'], 1e-11)
+
+
+def run(g, precision, svd_mode, max_it, tol, profile=False):
+    """Cold start, iterate, f and g; returns (f, g, status, iterations, emulation launches)."""
+    A = peps(g)
+    st, O = sctm.sctm_ising_pepo(g['T'])
+    r = sctm.SplitCTMRG(A, O, g['chi'], g['T'], precision=precision, svd_mode=svd_mode)
+    try:
+        if profile:
+            assert sctm.sctm_set_profiling(r.ctx, 1) == sctm.SCTM_OK
+        st, it, ds = r.iterate(max_it, tol)
+        f, gr = r.free_energy(), r.grad()
+        st_k, kv = sctm.sctm_profile_kernel(r.ctx, sctm.SCTM_KERNEL_F64EMU)
+        return f, gr, st, it, kv['launches']
+    finally:
+        r.close()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
+
+
+CONVERGED = ['cfg2_D3_chi36', 'cfg3_D4_chi64', 'cfg4_D5_chi100']
+
+
+@pytest.mark.parametrize('case', CONVERGED)
+def test_converged_benched_path(case):
+    """The bench's path (FP64, partial SVD with the randomized cold solve) iterated to the
+    oracle's stopping tolerance: f to 1e-10 and g to 1e-8 of the oracle's converged values."""
+    g = golden(case)
+    ref = g['records']['converged']
+    f, gr, st, it, _ = run(g, sctm.SCTM_PREC_FP64, sctm.SCTM_SVD_PARTIAL_RANDOM, 400, gpu_tol(g))
+    print('%s FP64 partial-random: %d iterations, |df|/|f| = %.2e, |dg|/|g| = %.2e' % (
+        case, it, abs(f - ref['f']) / abs(ref['f']), rel(gr, ref['g'])))
+    assert st == sctm.SCTM_OK, (st, it)
+    assert abs(f - ref['f']) <= 1e-10 * abs(ref['f']), (f, ref['f'])
+    assert rel(gr, ref['g']) <= 1e-8
+
+
+@pytest.mark.parametrize('case', ['cfg3_D4_chi64'])
+def test_converged_f64_emulation(case):
+    """SCTM_PREC_F64EMU: the contractions with K >= 512, M >= 128, N >= 64 run on the BF16 tensor
+    cores (the emulation kernel must have launched), with the FP64 path's tolerances."""
+    g = golden(case)
+    ref = g['records']['converged']
+    f, gr, st, it, emu = run(g, sctm.SCTM_PREC_F64EMU, sctm.SCTM_SVD_PARTIAL_RANDOM, 400,
+                             gpu_tol(g), profile=True)
+    print('%s F64EMU: %d iterations, %d emulation launches, |df|/|f| = %.2e, |dg|/|g| = %.2e' % (
+        case, it, emu, abs(f - ref['f']) / abs(ref['f']), rel(gr, ref['g'])))
+    assert st == sctm.SCTM_OK, (st, it)
+    assert emu > 0
+    assert abs(f - ref['f']) <= 1e-10 * abs(ref['f']), (f, ref['f'])
+    assert rel(gr, ref['g']) <= 1e-8
+
+
+# (case, form, |df| bound): configuration 2 states |df|/|f| <= 1e-9 for TF32 hi/lo; the headline
+# metric accepts a mixed form at |df| <= 1e-8
+MIXED = [('cfg2_D3_chi36', sctm.SCTM_PREC_TF32X3, 'rel', 1e-9),
+         ('cfg3_D4_chi64', sctm.SCTM_PREC_TF32X3, 'abs', 1e-8),
+         ('cfg4_D5_chi100', sctm.SCTM_PREC_BF16X3, 'abs', 1e-8)]
+
+
+@pytest.mark.parametrize('case,prec,kind,tol', MIXED)
+def test_converged_mixed_forms(case, prec, kind, tol):
+    """Mixed tensor-core forms plus FP64 polish (sctm_iterate) against the oracle's converged f."""
+    g = golden(case)
+    ref = g['records']['converged']
+    bound = tol * abs(ref['f']) if kind == 'rel' else tol
+    f, gr, st, it, _ = run(g, prec, sctm.SCTM_SVD_PARTIAL_RANDOM, 400, gpu_tol(g))
+    print('%s precision %d: %d iterations, |df| = %.2e, |dg|/|g| = %.2e' % (
+        case, prec, it, abs(f - ref['f']), rel(gr, ref['g'])))
+    assert st == sctm.SCTM_OK, (st, it)
+    assert abs(f - ref['f']) <= bound, (f, ref['f'])
+
+
+@pytest.mark.parametrize('network', [sctm.SCTM_NET_NUM, sctm.SCTM_NET_DEN])
+def test_first_left_move_full_size(network):
+    """One left move (Sec. III.B) at D=4, chi=64 from the shared SplitMix64 cold start, with the
+    full SVD, against the oracle element by element: exercises the 64x64 and 32x32 tiles, split-K
+    and the skinny kernel on the plan's full-size shapes.  The bound is 10x the oracle's own
+    spread under a 1e-15 relative change of A (measured here: projectors from a random
+    environment are ill-conditioned), and at least 1e-6."""
+    g = golden('cfg3_D4_chi64')
+    A = peps(g)
+    T, chi, D = g['T'], g['chi'], g['D']
+    st, O = sctm.sctm_ising_pepo(T)
+    r = sctm.SplitCTMRG(A, O, chi, T, svd_mode=sctm.SCTM_SVD_QR)
+    Oo = ising.ising_pepo(1 / T) if network == sctm.SCTM_NET_NUM else ising.identity_pepo()
+    try:
+        assert sctm.sctm_move(r.ctx, network, sctm.SCTM_MOVE_LEFT) == sctm.SCTM_OK
+        got = r.env(network)
+    finally:
+        r.close()
+    env0 = sc.init_env(chi, D, Oo.shape[2])
+    env = sc.move(env0, A, Oo, A, 'L', chi)
+    Ap = A * (1.0 + 1e-15 * np.random.default_rng(0).standard_normal(A.shape))
+    envp = sc.move(sc.init_env(chi, D, Oo.shape[2]), Ap, Oo, Ap, 'L', chi)
+
+    def err(e1, e2):
+        w = 0.0
+        for k in ('C1', 'C4'):
+            w = max(w, np.abs(e1[k] - e2[k]).max() / np.abs(e2[k]).max())
+        for x in range(3):
+            w = max(w, np.abs(e1['T4'][x] - e2['T4'][x]).max() / np.abs(e2['T4'][x]).max())
+        return w
+
+    worst, spread = err(got, env), err(envp, env)
+    print('first left move, network %d: GPU error %.2e, oracle spread %.2e' % (network, worst,
+                                                                                spread))
+    assert worst <= max(1e-6, 10.0 * spread)
+
+
+def test_largest_configuration_local_contractions():
+    """D=6, chi=144 (the largest configuration; its converged oracle value is out of reach of the
+    CPU oracle): every local contraction Z00, Z10, Z01, Z11 and the gradient g from the shared
+    cold-start environment, element by element against the oracle (Sec. II, Fig. 4(b), (c)), and
+    <A, g> = 0."""
+    D, chi, T, seed = 6, 144, 4.5115, 4
+    A = inputs.perturbed_product_peps(D, seed, eps=0.1)
+    st, O = sctm.sctm_ising_pepo(T)
+    r = sctm.SplitCTMRG(A, O, chi, T, svd_mode=sctm.SCTM_SVD_PARTIAL_RANDOM)
+    try:
+        got = [sctm.sctm_local_values(r.ctx, n)[1] for n in (0, 1)]
+        gr = np.zeros_like(A)
+        sctm.sctm_grad(r.ctx, gr)
+    finally:
+        r.close()
+    Os = (ising.ising_pepo(1 / T), ising.identity_pepo())
+    E, Z11 = [], []
+    for n in (0, 1):
+        env = sc.init_env(chi, D, Os[n].shape[2])
+        loc = sc.local_contractions(env, A, Os[n], A)
+        ref = [loc['Z00'], loc['Z10'], loc['Z01'], loc['Z11']]
+        for k in range(4):
+            assert abs(got[n][k] - ref[k]) <= 1e-12 * abs(ref[k]), (n, k, got[n][k], ref[k])
+        E.append(sc.bra_environment(env, loc))
+        Z11.append(loc['Z11'])
+    g_ref = -2.0 * T * (E[0] / Z11[0] - E[1] / Z11[1])
+    assert rel(gr, g_ref) <= 1e-11, rel(gr, g_ref)
+    assert abs(np.sum(A * gr)) <= 1e-9 * np.linalg.norm(gr) * np.linalg.norm(A)

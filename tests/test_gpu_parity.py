@@ -36,20 +36,51 @@ def _rel(a, b):
     return np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b))
 
 
+def _oracle_move_spread(A, Oo, chi, rel=1e-15, trials=3, seed=0):
+    """The oracle's own sensitivity over the same eight moves: the largest elementwise change
+    (relative to each tensor's largest entry) that a relative perturbation `rel` of A causes, per
+    tensor class.  It measures the conditioning of the moves (the pseudo-inverse S^-1/2 amplifies
+    rounding in the smallest kept singular directions), independently of the GPU."""
+    rng = np.random.default_rng(seed)
+    D = A.shape[1]
+    worst = {'corner': 0.0, 'edge': 0.0, 'int edge': 0.0}
+    for _ in range(trials):
+        Ap = A * (1.0 + rel * rng.standard_normal(A.shape))
+        e1 = sc.init_env(chi, D, Oo.shape[2])
+        e2 = sc.init_env(chi, D, Oo.shape[2])
+        for _ in range(2):
+            for w in 'LRUD':
+                e1 = sc.move(e1, A, Oo, A, w, chi)
+                e2 = sc.move(e2, Ap, Oo, Ap, w, chi)
+                for k in ('C1', 'C2', 'C3', 'C4'):
+                    worst['corner'] = max(worst['corner'],
+                                          np.abs(e1[k] - e2[k]).max() / np.abs(e1[k]).max())
+                for t in ('T1', 'T2', 'T3', 'T4'):
+                    for x in range(3):
+                        cls = 'int edge' if x == 1 else 'edge'
+                        worst[cls] = max(worst[cls], np.abs(e1[t][x] - e2[t][x]).max() /
+                                         np.abs(e1[t][x]).max())
+    return worst
+
+
 @pytest.mark.parametrize('network', [sctm.SCTM_NET_NUM, sctm.SCTM_NET_DEN])
 def test_single_moves_match_oracle(network):
     """Each directional move (left, right, up, down; Sec. III.B) from the same cold start gives the
-    same renormalised environment as the oracle, element by element (same SVD sign gauge).  In
-    the norm network the int-layer edge tensors carry no in-plane leg: they sit between two
-    projectors that nearly invert each other, so their entries inherit the conditioning of the
-    smallest kept singular vectors and are compared to 1e-4 instead of 1e-6."""
+    same renormalised environment as the oracle, element by element (same SVD sign gauge).  The
+    bound per tensor class is 10x the oracle's own spread under a 1e-15 relative change of A
+    (measured here, _oracle_move_spread), and at least 1e-6.  Measured on this input: the
+    numerator moves amplify such a change to ~1e-8, so its bound stays 1e-6; the norm network's
+    (d = 1: the int layer carries no in-plane leg and the projector pairs nearly invert each
+    other) to ~1e-5 on every tensor class, so its bound is ~1e-4.  The GPU's errors are printed."""
     T, D, chi = 4.6, 2, 6
-    tol = 1e-6 if network == sctm.SCTM_NET_NUM else 1e-4
     A = inputs.perturbed_product_peps(D, 7)
     st, O = sctm.sctm_ising_pepo(T)
     r = sctm.SplitCTMRG(A, O, chi, T)
     Oo = ising.ising_pepo(1 / T) if network == sctm.SCTM_NET_NUM else ising.identity_pepo()
+    spread = _oracle_move_spread(A, Oo, chi)
+    bound = {k: max(1e-6, 10.0 * v) for k, v in spread.items()}
     env = sc.init_env(chi, D, Oo.shape[2])
+    worst = {'corner': 0.0, 'edge': 0.0, 'int edge': 0.0}
     try:
         got = r.env(network)
         for k in ('C1', 'C2', 'C3', 'C4'):
@@ -60,13 +91,20 @@ def test_single_moves_match_oracle(network):
                 env = sc.move(env, A, Oo, A, w, chi)
                 got = r.env(network)
                 for k in ('C1', 'C2', 'C3', 'C4'):
-                    assert np.abs(got[k] - env[k]).max() <= tol * np.abs(env[k]).max(), (w, k)
+                    err = np.abs(got[k] - env[k]).max() / np.abs(env[k]).max()
+                    worst['corner'] = max(worst['corner'], err)
+                    assert err <= bound['corner'], (w, k, err, bound)
                 for t in ('T1', 'T2', 'T3', 'T4'):
                     for x in range(3):
-                        err = np.abs(got[t][x] - env[t][x]).max()
-                        assert err <= tol * np.abs(env[t][x]).max(), (w, t, x)
+                        err = np.abs(got[t][x] - env[t][x]).max() / np.abs(env[t][x]).max()
+                        cls = 'int edge' if x == 1 else 'edge'
+                        worst[cls] = max(worst[cls], err)
+                        assert err <= bound[cls], (w, t, x, err, bound)
     finally:
         r.close()
+    print('single moves, network %d: GPU error %s; oracle spread %s' % (network, worst, spread))
+    if network == sctm.SCTM_NET_NUM:
+        assert max(bound.values()) <= 1e-6
 
 
 @pytest.mark.parametrize('D,chi,T,seed,eps,iters', [

@@ -57,9 +57,9 @@ def test_partial_svd_parity_fixed_iterations(D, chi, T, seed, eps, iters, mode):
 @pytest.mark.parametrize('mode', MODES)
 def test_partial_svd_converged_fixed_point(mode):
     """Converged f against the oracle's converged f (1e-9: the oracle's own f moves by 6.4e-11
-    between stopping at 1e-11 and 1e-13 on this input), and the partial run's fixed point is a
-    fixed point of the full-SVD iteration: ten full-SVD iterations from it move f by less than
-    1e-10."""
+    between stopping at 1e-11 and 1e-13 on this input) and converged g (1e-8), and the partial
+    run's fixed point is a fixed point of the full-SVD iteration: ten full-SVD iterations from it
+    move f by less than 1e-10."""
     T, chi = 4.6, 16
     A = inputs.perturbed_product_peps(2, 7)
     rp, rq = _ctx(A, T, chi, mode), _ctx(A, T, chi, sctm.SCTM_SVD_QR)
@@ -67,6 +67,7 @@ def test_partial_svd_converged_fixed_point(mode):
         st, it, ds = rp.iterate(400, 1e-11)
         assert st == sctm.SCTM_OK, (st, it, ds)
         f = rp.free_energy()
+        g = rp.grad()
         for net in (sctm.SCTM_NET_NUM, sctm.SCTM_NET_DEN):
             st, buf = sctm.sctm_env_export(rp.ctx, net)
             assert sctm.sctm_env_import(rq.ctx, net, buf) == sctm.SCTM_OK
@@ -77,6 +78,8 @@ def test_partial_svd_converged_fixed_point(mode):
         rq.close()
     ref = _oracle(A, T, chi, 400, 1e-13)
     assert abs(f - ref['f']) <= 1e-9 * abs(ref['f']), (f, ref['f'])
+    # the environment gradient at the partial SVD's fixed point is the full SVD's
+    assert np.linalg.norm(g - ref['g']) <= 1e-8 * np.linalg.norm(ref['g'])
     assert abs(fq - f) <= 1e-10 * abs(f), (fq, f)
 
 
