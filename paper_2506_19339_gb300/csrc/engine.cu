@@ -12,6 +12,7 @@
 #include <cstring>
 #include <functional>
 #include <map>
+#include <mutex>
 #include <tuple>
 
 namespace sctm {
@@ -1292,14 +1293,26 @@ double Engine::switch_level(int prec) {
 // moves to the tensor cores, which depends on M, N, K and the batch together; so it is measured.
 // autotune() times both kernels once per distinct contraction shape on this context's own buffers
 // (one launch to warm up, then the best of three, CUDA events on the caller's stream) and keeps
-// the faster; shapes below 4 MFLOP stay FP64 untimed (launch overheads dominate there).
+// the faster; shapes below 4 MFLOP stay FP64 untimed (launch overheads dominate there).  The
+// decisions are kept per device and shape for the life of the process, so later contexts (a
+// batched sweep) reuse them.
+namespace {
+struct TuneChoice {
+    bool emu;
+    float t64, temu;
+};
+// decisions per (device, M, N, K, batch), shared by every context of the process
+std::mutex g_tune_mutex;
+std::map<std::tuple<int, int, int, int, int>, TuneChoice> g_tune;
+}  // namespace
+
 void Engine::autotune(Network& net) {
     if (dry) return;
-    struct Choice {
-        bool emu;
-        float t64, temu;
-    };
-    std::map<std::tuple<int, int, int, int>, Choice> seen;
+    using Choice = TuneChoice;
+    int dev = 0;
+    CUDA_OK(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    std::map<std::tuple<int, int, int, int, int>, Choice>& seen = g_tune;
     cudaStream_t s = lanes[0].streams[0];
     cudaEvent_t e0, e1;
     CUDA_OK(cudaEventCreate(&e0));
@@ -1330,7 +1343,7 @@ void Engine::autotune(Network& net) {
         if (!st->mixed_ok) continue;
         ++net.tuned_total;
         if (st->flops < 4000000LL) continue;
-        const auto key = std::make_tuple(st->a.M, st->a.N, st->a.K, st->a.nb);
+        const auto key = std::make_tuple(dev, st->a.M, st->a.N, st->a.K, st->a.nb);
         auto it = seen.find(key);
         if (it == seen.end()) {
             Choice c;
