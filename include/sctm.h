@@ -19,7 +19,9 @@
  *     from sctm_last_error().  A NULL context returns SCTM_EINVAL.
  *   - Calls on one context are not thread-safe; different contexts are independent.
  *   - Results are deterministic: the same inputs and options give the same bits on the same GPU
- *     (all reductions have a fixed order).
+ *     (all reductions have a fixed order).  In SCTM_PREC_F64EMU the kernel of each contraction
+ *     shape is chosen by timing (sctm_autotune_info) once per process and device: contexts of one
+ *     process agree bit for bit, two processes may differ in the last bits (both FP64-accurate).
  */
 #ifndef SCTM_H
 #define SCTM_H
@@ -252,8 +254,9 @@ sctm_status sctm_iterate_batch(sctm_ctx* const* ctxs, int count, int max_it, dou
 /* sctm_autotune_info -- for an SCTM_PREC_F64EMU context: how many of one network's
  * FP64-accurate move contractions run on the emulation kernel (*emu) out of those that may
  * (*eligible), as chosen at creation by timing both kernels once per contraction shape (shapes
- * below 4 MFLOP stay on the FP64 kernels).  Both are 0 for other forms.  Either pointer may be
- * NULL.  Errors: EINVAL (NULL ctx, bad network). */
+ * below 4 MFLOP stay on the FP64 kernels; the decisions are kept per device and shape for the
+ * life of the process).  Both are 0 for other forms.  Either pointer may be NULL.
+ * Errors: EINVAL (NULL ctx, bad network). */
 sctm_status sctm_autotune_info(sctm_ctx* ctx, int network, int* emu, int* eligible);
 
 /* sctm_device_bytes -- device memory held by the context (all of it is allocated at create). */

@@ -17,6 +17,9 @@ Modules (each function cites the passage of arXiv:2506.19339 it follows):
                         insertion/absorption, six projectors, renormalisation, convergence,
                         free energy (Eq. "free energy expression") and gradient (Eq. "gradient
                         expression").
+* ``split_ctmrg_d2`` -- the D2-symmetric split-CTMRG (Sec. III.B, Eq. "Symmetry constraints"):
+                        one projector set per iteration, corners absorbing a row and a column
+                        at once, A and g projected onto the D4-invariant tensors.
 * ``reduced_ctmrg``  -- the traditional reduced method (Sec. II, Fig. 3): an independent
                         reference algorithm for the same f and g.
 

@@ -282,9 +282,13 @@ def test_polar_svd_mode():
     assert _rel(g, ref['g']) <= 1e-5
 
 
-def test_batched_sweep_matches_single_runs():
+@pytest.mark.parametrize('svd_mode,prec', [(sctm.SCTM_SVD_QR, sctm.SCTM_PREC_FP64),
+                                           (sctm.SCTM_SVD_PARTIAL_RANDOM, sctm.SCTM_PREC_F64EMU)])
+def test_batched_sweep_matches_single_runs(svd_mode, prec):
     """sctm_iterate_batch over contexts at several temperatures (the batched sweep) gives, for
-    each context, the same bits as iterating that context alone."""
+    each context, the same bits as iterating that context alone: with cuSOLVER's SVD, and with the
+    randomized partial SVD whose warm iterations replay captured CUDA graphs in the FP64
+    emulation form (the autotuner's decisions are shared within the process)."""
     import torch
     D, chi = 2, 8
     Ts = inputs.temperature_sweep(3)
@@ -297,10 +301,11 @@ def test_batched_sweep_matches_single_runs():
             st, o = sctm.sctm_default_opts()
             o.T, o.D, o.p, o.d = T, D, 2, 2
             o.cuda_stream = streams[i].cuda_stream
+            o.svd_mode, o.precision = svd_mode, prec
             st, ctx = sctm.sctm_create(A, O, chi, o)
             assert st == sctm.SCTM_OK
             runs.append(ctx)
-            r = sctm.SplitCTMRG(A, O, chi, T)
+            r = sctm.SplitCTMRG(A, O, chi, T, svd_mode=svd_mode, precision=prec)
             r.iterate(5)
             alone.append(r.free_energy())
             r.close()

@@ -1,0 +1,139 @@
+"""Pins of the oracle's D2-symmetric split-CTMRG (arXiv:2506.19339 Sec. III.B, Eq. "Symmetry
+constraints" and the symmetric corner absorption), no GPU needed.
+
+The symmetric scheme is pinned against things it does not compute itself: the group axioms of
+D4, the frame relabellings of the directional oracle (``split_ctmrg.frame_transpose`` /
+``frame_rotate``, pinned in test_oracle_pins.py), the directional scheme's converged free energy
+and gradient (a fixed point of one is a fixed point of the other), Onsager's closed form, and
+the exact symmetry that a correct corner update has before any symmetrisation (a leg of the
+wrong layer or bond fails it; one such mistake is planted below).
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+from oracle import ising, onsager, split_ctmrg as sc, split_ctmrg_d2 as sd
+from paper_2506_19339_gb300 import inputs
+
+
+def _compose(p, q):
+    """(p o q): A.transpose(q).transpose(p) == A.transpose(_compose(p, q))."""
+    return tuple(q[i] for i in p)
+
+
+def test_d4_group_and_projection():
+    """The eight permutations are distinct and closed under composition (a group of order 8 on
+    the four virtual legs), contain the two D2 generators the frames use (main-diagonal
+    reflection u<->l, d<->r; 180-degree rotation u<->d, l<->r), and no permutation that breaks
+    the square (u<->d alone keeps adjacency, so it must be there; u<->l alone does not, so it
+    must not).  The group average is an orthogonal projector onto the invariant tensors."""
+    G = sd.d4_permutations()
+    assert len(set(G)) == 8
+    for p, q in itertools.product(G, G):
+        assert _compose(p, q) in G
+    assert (0, 2, 1, 4, 3) in G and (0, 3, 4, 1, 2) in G
+    assert (0, 3, 2, 1, 4) in G          # reflection about the horizontal axis (u <-> d)
+    assert (0, 2, 1, 3, 4) not in G      # u <-> l alone is not a symmetry of the square
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((2, 3, 3, 3, 3))
+    B = rng.standard_normal((2, 3, 3, 3, 3))
+    PA = sd.d4_project(A)
+    assert np.allclose(sd.d4_project(PA), PA, atol=1e-15)
+    for p in G:
+        assert np.allclose(PA.transpose(p), PA, atol=1e-15)
+    assert abs(np.sum(PA * B) - np.sum(A * sd.d4_project(B))) < 1e-12
+    assert abs(np.sum((A - PA) * PA)) < 1e-12
+
+
+def _sym_problem(seed, chi, D, d):
+    rng = np.random.default_rng(seed)
+    C1 = rng.standard_normal((chi, chi))
+    C4 = rng.standard_normal((chi, chi))
+    T4 = [rng.standard_normal((chi, chi, m)) for m in (D, d, D)]
+    env = sd.sym_env(C1 + C1.T, C4 + C4.T, T4)
+    A = sd.d4_project(rng.standard_normal((2, D, D, D, D)))
+    return env, A
+
+
+def test_symmetric_environment_is_invariant_under_the_frames():
+    """Eq. "Symmetry constraints" as ``sym_env`` writes them is exactly the invariance of the
+    environment under the two frame maps of the directional oracle (reflection about the main
+    diagonal; rotation by 180 degrees with ket <-> bra) for a D4-symmetric A and the Ising
+    PEPO; those frames are pinned independently (test_frames_relabel_the_same_network)."""
+    env, A = _sym_problem(5, 4, 2, 2)
+    O = ising.ising_pepo(1 / 4.5)
+    assert sd.constraint_residual(env) == 0.0
+    for frame in (sc.frame_transpose, sc.frame_rotate):
+        e, a, o, b = frame(env, A, O, A)
+        assert np.allclose(a, A, rtol=0, atol=1e-15) and np.allclose(b, A, rtol=0, atol=1e-15)
+        assert np.allclose(o, O, rtol=0, atol=1e-15)
+        for k in ('C1', 'C2', 'C3', 'C4'):
+            assert np.array_equal(e[k], env[k]), k
+        for k in ('T1', 'T2', 'T3', 'T4'):
+            for x in range(3):
+                assert np.array_equal(e[k][x], env[k][x]), (k, x)
+
+
+def test_enlarged_corners_carry_the_symmetry():
+    """The corner with its column and row absorbed is symmetric under the exchange of its two
+    legs: C1's (h, A.r, O.r, B.r) <-> (v, A.d, O.d, B.d) by the main-diagonal reflection, C4's
+    (v, A.u, O.u, B.u) <-> (h, B.r, O.r, A.r) by the anti-diagonal one, which also exchanges
+    ket and bra."""
+    env, A = _sym_problem(6, 3, 2, 2)
+    O = ising.ising_pepo(1 / 4.5)
+    C1 = sd.enlarged_c1(env, A, O, A)
+    assert np.allclose(C1, C1.transpose(4, 5, 6, 7, 0, 1, 2, 3), rtol=0,
+                       atol=1e-13 * np.max(np.abs(C1)))
+    C4 = sd.enlarged_c4(env, A, O, A)
+    assert np.allclose(C4, C4.transpose(4, 7, 6, 5, 0, 3, 2, 1), rtol=0,
+                       atol=1e-13 * np.max(np.abs(C4)))
+    # without the ket <-> bra exchange the anti-diagonal map is not a symmetry
+    assert not np.allclose(C4, C4.transpose(4, 5, 6, 7, 0, 1, 2, 3), rtol=0,
+                           atol=1e-6 * np.max(np.abs(C4)))
+
+
+@pytest.mark.parametrize('net', ['num', 'den'])
+def test_corner_update_is_symmetric_before_symmetrisation(net):
+    """From the symmetric cold start, one iteration without the final symmetrisation already
+    gives C1 = C1^T and C4 = C4^T to rounding (both corner legs carry the one alpha pair).
+    Planted mistake: the C4 column-cut leg read without the ket <-> bra exchange breaks it."""
+    T, D, chi = 4.5, 2, 6
+    A = sd.d4_project(inputs.perturbed_product_peps(D, 5, eps=0.2))
+    O = ising.ising_pepo(1 / T) if net == 'num' else ising.identity_pepo()
+    env = sd.sym_init_env(chi, D, O.shape[2])
+    info = {}
+    sd.sym_iteration(env, A, O, A, chi, symmetrise=False, info=info)
+    assert max(info['asym']) < 1e-13
+    # the planted mistake, on the oracle: P_B's (bond, A_v, O_v, B_v) met by (h, A.r, O.r, B.r)
+    PaB, _ = info['projectors']['alpha']
+    Ct4 = sd.enlarged_c4(env, A, O, A)
+    X = np.einsum('vabchpqr,vabck->hpqrk', Ct4, PaB)
+    wrong = np.einsum('hpqrk,hpqrj->jk', X, PaB)
+    assert np.linalg.norm(wrong - wrong.T) / np.linalg.norm(wrong) > 1e-6
+
+
+def test_symmetric_scheme_matches_directional():
+    """A fixed point of the directional scheme that is symmetric up to gauge is a fixed point of
+    the symmetric one: on a D4-symmetric PEPS (D = 2, chi = 8, T = 4.5, 40 iterations each) both
+    give the same f and the same projected gradient; f(cA) = f(A) gives <A, g> = 0."""
+    T, D, chi, n = 4.5, 2, 8, 40
+    A = sd.d4_project(inputs.perturbed_product_peps(D, 5, eps=0.2))
+    On, Od = ising.ising_pepo(1 / T), ising.identity_pepo()
+    rs = sd.sym_evaluate(A, On, Od, T, chi, n)
+    rd = sc.evaluate(A, On, Od, T, chi, n)
+    assert abs(rs['f'] - rd['f']) < 1e-11
+    gd = sd.d4_project(rd['g'])
+    assert np.linalg.norm(rs['g'] - gd) < 1e-7 * np.linalg.norm(gd)
+    assert abs(np.sum(A * rs['g'])) < 1e-9 * np.linalg.norm(A) * np.linalg.norm(rs['g'])
+    for p in sd.d4_permutations():
+        assert np.allclose(rs['g'].transpose(p), rs['g'], rtol=0, atol=1e-15)
+
+
+def test_symmetric_plus_state_is_onsager():
+    """The |+> product state (D = 1) through the symmetric scheme gives cosh(beta) times the 2D
+    Ising network, Onsager's closed form (T = 10, chi = 8, as for the directional scheme)."""
+    T = 10.0
+    A = inputs.product_plus_peps()
+    r = sd.sym_evaluate(A, ising.ising_pepo(1 / T), ising.identity_pepo(), T, 8, 100, 1e-13)
+    assert abs(r['f'] - onsager.f_plus_state(T)) < 1e-10 * abs(r['f'])
