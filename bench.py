@@ -10,7 +10,8 @@ counts only if |f - f_oracle| <= 1e-8, f_oracle being the FP64 oracle's converge
 tests/golden/cfg3_D4_chi64.json (written by tests/golden/make_golden.py).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|f64emu|tf32x3]
-                    [--impl ours|reference] [--batch B]
+                    [--impl ours|reference] [--batch B] [--method split|split-d2]
+                    [--gemm M,N,K]
 
 Prints one JSON line (rank 0).  Under torchrun with N > 1 every rank runs an independent replica
 (the single-instance path does not shard) and `value` is the sum over ranks.
@@ -30,7 +31,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "split-CTMRG f+∇f evals/s at D=4 χ=64, mixed vs FP64 at |Δf|≤1e-8; % of peak"
 WORKLOAD = dict(D=4, chi=64, T=4.5, seed=2, eps=0.1, tol=1e-10, max_it=400)
-GOLDEN = os.path.join(ROOT, 'tests', 'golden', 'cfg3_D4_chi64.json')
+GOLDENS = {'split': os.path.join(ROOT, 'tests', 'golden', 'cfg3_D4_chi64.json'),
+           'split-d2': os.path.join(ROOT, 'tests', 'golden', 'd2_D4_chi64.json')}
+METHODS = {'split': 0, 'split-d2': 2}
 ACCEPT_DF = 1e-8
 PRECISIONS = {'fp64': 0, 'tf32': 1, 'tf32x3': 2, 'bf16': 3, 'bf16x3': 4, 'f64emu': 5}
 FORMS = ('fp64', 'f64emu', 'tf32x3')   # the forms every run compares
@@ -61,6 +64,14 @@ def parse():
     ap.add_argument('--lean', action='store_true',
                     help='profiler captures: the headline steps only (no end-to-end, serialised, '
                          'N(0,1), other-form, DGEMM or CPU legs)')
+    ap.add_argument('--method', default='split', choices=list(METHODS),
+                    help='split: the four directional moves per iteration (Sec. III.B); split-d2: '
+                         'the D2-symmetric scheme (one projector set per iteration) on the D4 '
+                         'group average of the same PEPS, accepted against the oracle\'s stored '
+                         'value of that scheme')
+    ap.add_argument('--gemm', default=None,
+                    help='M,N,K: time one plain contraction O = X Y through sctm_gemm in the '
+                         'headline precision instead (kernel isolation and profiler captures)')
     ap.add_argument('--D', type=int, default=None, help='PEPS bond dimension (small captures)')
     ap.add_argument('--chi', type=int, default=None, help='chi (small captures)')
     return ap.parse_args()
@@ -78,15 +89,20 @@ def workload(args):
     return w
 
 
-def workload_name(w):
+def workload_name(w, method='split'):
+    if method == 'split-d2':
+        return ('D2-symmetric split-CTMRG f+grad from the cold start to ||dS||<%g, 3D Ising PEPO '
+                'T=%g, PEPS D=%d (D4 group average of the perturbed product state, seed %d, eps '
+                '%g), chi=%d, numerator + norm networks' %
+                (w['tol'], w['T'], w['D'], w['seed'], w['eps'], w['chi']))
     return ('split-CTMRG f+grad from the cold start to ||dS||<%g, 3D Ising PEPO T=%g, PEPS D=%d '
             '(perturbed product state, seed %d, eps %g), chi=%d, numerator + norm networks' %
             (w['tol'], w['T'], w['D'], w['seed'], w['eps'], w['chi']))
 
 
-def load_golden(w):
+def load_golden(w, method='split'):
     try:
-        g = json.load(open(GOLDEN))
+        g = json.load(open(GOLDENS[method]))
     except (OSError, ValueError):
         return None
     if (g['D'], g['chi'], g['T'], g['seed'], g['eps']) != (w['D'], w['chi'], w['T'], w['seed'],
@@ -279,7 +295,7 @@ def combine_ranks(ms, e2e_ms, dist, device):
 class Instance:
     """One context of the workload in one precision form, driven through the C ABI."""
 
-    def __init__(self, sctm, w, prec, svd, stream, dev, A_host):
+    def __init__(self, sctm, w, prec, svd, stream, dev, A_host, method='split'):
         import torch
         st, O = sctm.sctm_ising_pepo(w['T'])
         st, o = sctm.sctm_default_opts()
@@ -287,6 +303,7 @@ class Instance:
         o.cuda_stream = stream.cuda_stream
         o.svd_mode = SVD_MODES[svd]
         o.precision = PRECISIONS[prec]
+        o.method = METHODS[method]
         self.sctm, self.w, self.prec = sctm, w, prec
         self.A_dev = torch.from_numpy(A_host).to(dev)
         st, self.ctx = sctm.sctm_create(self.A_dev, np.ascontiguousarray(O), w['chi'], o)
@@ -378,19 +395,19 @@ def run_ours(args):
     torch.cuda.set_device(dev)
     build.build()
     sctm.load()
-    golden = load_golden(w)
+    golden = load_golden(w, args.method)
     ref_f = golden['records']['converged']['f'] if golden else None
     ref_g = (np.array(golden['records']['converged']['g']).reshape(2, *(w['D'],) * 4)
              if golden else None)
 
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(w, golden)
+    if rank == 0 and not args.no_cpu_baseline and args.method == 'split':
+        cpu = cpu_baseline(w, load_golden(w))
 
     A_host = inputs.perturbed_product_peps(w['D'], w['seed'], eps=w['eps'])
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
-    head = Instance(sctm, w, args.precision, args.svd, stream, dev, A_host)
+    head = Instance(sctm, w, args.precision, args.svd, stream, dev, A_host, args.method)
 
     # ---- headline: converged evaluations, inputs resident on the device, profiling off
     for _ in range(args.warmup):
@@ -462,7 +479,7 @@ def run_ours(args):
     head.close()
 
     # ---- the other precision forms, same workload and stopping rule
-    if not args.no_compare:
+    if not args.no_compare and args.method == 'split':
         for form in FORMS:
             if form == args.precision:
                 continue
@@ -527,11 +544,11 @@ def run_ours(args):
         'higher_is_better': True, 'scaling': 'weak', 'vs_baseline': None,
         'dtype': 'f64' if args.precision in ('fp64', 'f64emu') else args.precision + '+f64',
         'data': 'synthetic',
-        'config': {'workload': workload_name(w), 'D': w['D'], 'chi': w['chi'], 'T': w['T'],
-                   'seed': w['seed'], 'eps': w['eps'], 'tol': w['tol'],
-                   'precision': args.precision, 'svd': args.svd,
-                   'accept': '|f - f_oracle| <= %g, f_oracle from tests/golden/cfg3_D4_chi64.json'
-                             % ACCEPT_DF,
+        'config': {'workload': workload_name(w, args.method), 'D': w['D'], 'chi': w['chi'],
+                   'T': w['T'], 'seed': w['seed'], 'eps': w['eps'], 'tol': w['tol'],
+                   'precision': args.precision, 'svd': args.svd, 'method': args.method,
+                   'accept': '|f - f_oracle| <= %g, f_oracle from tests/golden/%s' % (
+                       ACCEPT_DF, os.path.basename(GOLDENS[args.method])),
                    'parallelism': 'replicas',
                    'l2': 'flushed before every step (256 MiB write, outside the step events)'},
         'accepted': head_form['accepted'], 'abs_df_vs_oracle': head_form['abs_df_vs_oracle'],
@@ -623,8 +640,52 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def run_gemm(args):
+    """One plain contraction O = X Y (row-major FP64 operands from inputs.random_matrix) through
+    sctm_gemm in the headline precision: CUDA events around each call on its stream, L2 flushed
+    before each.  Prints the isolated rate against the measured FP64 matrix-multiply rate (and the
+    BF16 tensor peak for the emulation, which runs on the BF16 tensor cores)."""
+    import torch
+    from paper_2506_19339_gb300 import build, inputs, sctm
+    M, N, K = (int(x) for x in args.gemm.split(','))
+    dev = torch.device('cuda', 0)
+    build.build()
+    sctm.load()
+    X = torch.from_numpy(inputs.random_matrix(M, K, 1)).to(dev)
+    Y = torch.from_numpy(inputs.random_matrix(K, N, 2)).to(dev)
+    O = torch.zeros((M, N), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    prec = PRECISIONS[args.precision]
+    for _ in range(args.warmup):
+        assert sctm.sctm_gemm(X, Y, O, M, N, K, prec, stream.cuda_stream) == sctm.SCTM_OK
+    ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        assert sctm.sctm_gemm(X, Y, O, M, N, K, prec, stream.cuda_stream) == sctm.SCTM_OK
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    ref = X.cpu().numpy() @ Y.cpu().numpy()
+    err = float(np.max(np.abs(O.cpu().numpy() - ref)) / np.max(np.abs(ref)))
+    fp64 = dgemm_tflops(dev)
+    t = float(np.median(ms)) * 1e-3
+    print(json.dumps({'gemm': [M, N, K], 'precision': args.precision, 'ms_median': t * 1e3,
+                      'tflops_fp64_equivalent': 2.0 * M * N * K / t / 1e12,
+                      'fp64_dgemm_tflops_measured': fp64, 'max_rel_err_vs_numpy': err,
+                      'note': 'sctm_gemm includes its index-table set-up and a stream '
+                              'synchronisation; a kernel profile of the same command isolates '
+                              'the contraction kernel'}), flush=True)
+
+
 def main():
     args = parse()
+    if args.gemm:
+        run_gemm(args)
+        return
     if args.batch > 0:
         run_batch(args)
         return

@@ -106,8 +106,39 @@ enum { SCTM_NET_NUM = 0, SCTM_NET_DEN = 1 };          /* <psi|T|psi> and <psi|ps
  *                        only (precision must be SCTM_PREC_FP64), environment gradient only; its
  *                        edge tensors are exported in the ket slots (leg m = D d D, grouped
  *                        (A, O, A-bar)), the int and bra slots are empty; cold start
- *                        C = e_0 e_0^T, T[0][0][:] = 1. */
-enum { SCTM_METHOD_SPLIT = 0, SCTM_METHOD_REDUCED = 1 };
+ *                        C = e_0 e_0^T, T[0][0][:] = 1.
+ *   SCTM_METHOD_SPLIT_D2 the D2-symmetric split-CTMRG (Sec. III.B, Eq. "Symmetry constraints"):
+ *                        for a PEPS whose virtual legs are D4-invariant and a PEPO invariant under
+ *                        the reflection about the main diagonal (O[t,s,u,l,d,r] = O[t,s,l,u,r,d])
+ *                        and the 180-degree rotation with s_up <-> s_dn
+ *                        (O[t,s,u,l,d,r] = O[s,t,d,r,u,l]), checked at creation to 1e-12 of
+ *                        max|O| (else SCTM_EINVAL).  The environment is C1, C4 and the left edge
+ *                        T4^{k,i,b}; C3 = C1 = C1^T, C2 = C4 = C4^T, T1 = T4, T2 = T3 = T4 with
+ *                        ket <-> bra and its two chain bonds exchanged.  One iteration is one
+ *                        set of six projector pairs (the left move's; the opposite boundary's
+ *                        stage-1 pairs are the images of this boundary's under the 180-degree
+ *                        rotation, P^R_1T = P_1B, P^R_2T = P_3B, P^R_3T = P_2B and the same
+ *                        with T <-> B, Appendix, so each iteration takes six SVDs instead of 36):
+ *                        T4 is renormalised as in the left move, and C1 and C4 each absorb one
+ *                        column and one row at once with both legs truncated by the alpha pair,
+ *                        then are symmetrised.  The PEPS is
+ *                        replaced by its D4 group average on entry (sctm_create, sctm_set_peps)
+ *                        and sctm_grad returns the group average of the gradient.  Environment
+ *                        gradient only.  sctm_move accepts SCTM_MOVE_LEFT only (one symmetric
+ *                        iteration); sctm_env_export writes all sixteen slots (the derived ones
+ *                        from the constraints), sctm_env_import reads C1, C4 and T4 and
+ *                        symmetrises the corners. */
+enum { SCTM_METHOD_SPLIT = 0, SCTM_METHOD_REDUCED = 1, SCTM_METHOD_SPLIT_D2 = 2 };
+/* Patch of the stage-2 alpha projector (projector 4, Appendix):
+ *   SCTM_P4_FULL  the 2x2-cell patch (both columns, the bra lines renormalised by projector 1 of
+ *                 this and of the opposite boundary), cost O(chi^3 D^4 d)
+ *   SCTM_P4_HALF  the 2x1-cell patch: the two enlarged left corners (C1 and C4 each with one
+ *                 column and one row absorbed), the bra lines of both their legs renormalised by
+ *                 projector 1 -- on the column cut by the up / down moves' projector 1, which the
+ *                 D2 symmetry gives as the transposed P_1T / P_1B (in the down move's frame ket
+ *                 and bra trade places, so the lower corner's column-cut projector acts on its
+ *                 ket line).  Cost O(chi^3 D^3 d^3); SCTM_METHOD_SPLIT_D2 only. */
+enum { SCTM_P4_FULL = 0, SCTM_P4_HALF = 1 };
 enum { SCTM_MOVE_LEFT = 0, SCTM_MOVE_RIGHT = 1, SCTM_MOVE_UP = 2, SCTM_MOVE_DOWN = 3 };
 
 typedef struct {
@@ -122,7 +153,8 @@ typedef struct {
     int batch;                    /* reserved, must be 1                                    */
     void* cuda_stream;            /* cudaStream_t for all work, NULL = legacy default       */
     int svd_mode;                 /* SCTM_SVD_* (default SCTM_SVD_QR)                       */
-    int method;                   /* SCTM_METHOD_SPLIT (default) or SCTM_METHOD_REDUCED     */
+    int method;                   /* SCTM_METHOD_SPLIT (default), _REDUCED or _SPLIT_D2     */
+    int p4_mode;                  /* SCTM_P4_FULL (default) or SCTM_P4_HALF (SPLIT_D2 only) */
 } sctm_opts;
 
 /* Fill *o with the defaults: T=1, D=2, p=2, d=2, FP64, env gradient, cutoff 1e-12, seed 0,

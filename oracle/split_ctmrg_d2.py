@@ -147,7 +147,71 @@ def enlarged_c4(env, A, O, B):
     return X.transpose(5, 6, 3, 1, 0, 7, 4, 2)
 
 
-def sym_iteration(env, A, O, B, chi, cutoff=1e-12, symmetrise=True, info=None):
+def mirror_stage1(left):
+    """The opposite boundary's stage-1 pairs as the images of this boundary's under the rotation
+    by 180 degrees with ket <-> bra (Appendix, captions of projectors 4-6: in the D2-symmetric
+    scheme P^R_1T = P_1B, P^R_1B = P_1T, P^R_2T = P_3B, P^R_2B = P_3T, P^R_3T = P_2B,
+    P^R_3B = P_2T).  The rotation puts the right column's alpha cut onto the left column's alpha
+    cut, its kappa cut (ket | int) onto the left iota cut (int | bra) and its iota cut onto the
+    left kappa cut, with the right environment bond onto the left one, the ket lines onto the
+    bra lines and the physical line A-O onto O-A-bar.  Leg orders as ``split_ctmrg``:
+        right alpha (xr, A_v)      <- left alpha (xl, B_v)
+        right kappa (xr, A.d, s)   <- left iota  (xl, s', B.u)
+        right iota  (xr, A.d, s')  <- left kappa (xl, s, B.u)"""
+    PBa, PTa, Sa = left['alpha']
+    PBk, PTk, Sk = left['kappa']
+    PBi, PTi, Si = left['iota']
+    return {
+        'alpha': (PTa.transpose(1, 2, 0), PBa.transpose(2, 0, 1), Sa),
+        'kappa': (PTi.transpose(1, 3, 2, 0), PBi.transpose(3, 0, 2, 1), Si),
+        'iota': (PTk.transpose(1, 3, 2, 0), PBk.transpose(3, 0, 2, 1), Sk),
+    }
+
+
+def half_p4_halves(env, A, O, B, left):
+    """(rho_T, rho_B) of the half projector 4 (Appendix, projector 4(b)): the 2x1 patch of the
+    two enlarged left corners, the bra lines of both their legs renormalised by projector 1 --
+    P_1T / P_1B on the row cut, and on the column cut the up / down moves' projector 1, which the
+    D2 symmetry gives as P_1T^T for the upper corner and P_1B^T for the lower one (in the frame of
+    the down move ket and bra trade places, so there it acts on the ket line A.r).  Leg orders:
+        rho_T (k1, A.d, O.d | k2, A.r, O.r)    rho_B (k1, A.u, O.u | k2, B.r, O.r)
+    the first three legs cut by projector 4, the last three remaining."""
+    PBa, PTa, _ = left['alpha']                      # [xl, B_v, k], [k, xl, B_v]
+    Ct1 = enlarged_c1(env, A, O, B)                   # [h, A.r, O.r, B.r, v, A.d, O.d, B.d]
+    X = sc._c2('hpqrvabc,kvc->hpqrkab', Ct1, PTa)
+    U = sc._c2('hpqrkab,jhr->kabjpq', X, PTa)
+    Ct4 = enlarged_c4(env, A, O, B)                   # [v, A.u, O.u, B.u, h, A.r, O.r, B.r]
+    X = sc._c2('vabchpqr,vck->kabhpqr', Ct4, PBa)
+    L = sc._c2('kabhpqr,hpj->kabjrq', X, PBa)
+    return U, L
+
+
+def sym_projectors(env, A, O, B, chi, cutoff=1e-12, p4='full', pr='mirror', info=None):
+    """The six composite projector pairs of one symmetric iteration (the left move's cuts,
+    Sec. III.C and Appendix): stage 1 (P1, P2, P3) from the one-column patches; the opposite
+    boundary's stage-1 pairs by symmetry (pr='mirror', the paper's D2 scheme) or by their own SVDs
+    (pr='svd', as in the directional scheme); stage 2: P5, P6 from the 1x2-cell patches, P4 from
+    the 2x2-cell patch (p4='full') or the 2x1-cell patch (p4='half')."""
+    halves = sc.one_column_halves(env, A, O, B)
+    left = {cut: sc.projector_pair(U, L, sc.T_AXES_LEFT[cut], chi, cutoff)
+            for cut, (U, L) in halves.items()}
+    if pr == 'mirror':
+        right = mirror_stage1(left)
+    else:
+        right = {cut: sc.projector_pair(U, L, sc.T_AXES_RIGHT[cut], chi, cutoff)
+                 for cut, (U, L) in halves.items()}
+    halves2 = sc.two_column_halves(env, A, O, B, left, right)
+    if p4 == 'half':
+        halves2['alpha'] = half_p4_halves(env, A, O, B, left)
+    stage2 = {cut: sc.projector_pair(U2, L2, (0, 1, 2), chi, cutoff)
+              for cut, (U2, L2) in halves2.items()}
+    if info is not None:
+        info['left'], info['right'], info['stage2'] = left, right, stage2
+    return sc.composite_projectors(left, stage2)
+
+
+def sym_iteration(env, A, O, B, chi, cutoff=1e-12, symmetrise=True, info=None, p4='full',
+                  pr='mirror'):
     """One iteration of the symmetric scheme on a symmetric environment (module docstring).
     The projectors are the left move's; the edge is the left move's T4'.  Each corner absorbs
     its column and row at once (``enlarged_c1`` / ``enlarged_c4``) and both of its legs are
@@ -157,9 +221,10 @@ def sym_iteration(env, A, O, B, chi, cutoff=1e-12, symmetrise=True, info=None):
     (bond, A_v, O_v, B_v) meets (bond, B.r, O.r, A.r).
     symmetrise=False leaves out the final C <- (C + C^T) / 2 (to measure how symmetric the
     update comes out by itself).  Returns the new symmetric environment (``sym_env``)."""
-    linfo = {}
-    _, T4n, _ = sc.left_move(env, A, O, B, chi, cutoff, info=linfo)
-    PaB, PaT = linfo['projectors']['alpha']          # [xl, A_v, O_v, B_v, k], [k, xl, ...]
+    pinfo = {}
+    P = sym_projectors(env, A, O, B, chi, cutoff, p4, pr, pinfo)
+    _, T4n, _ = sc.renormalise(env, A, O, B, P)
+    PaB, PaT = P['alpha']                            # [xl, A_v, O_v, B_v, k], [k, xl, ...]
     Ct1 = enlarged_c1(env, A, O, B)
     X = sc._c2('hpqrvabc,kvabc->hpqrk', Ct1, PaT)
     C1n = sc._c2('hpqrk,jhpqr->jk', X, PaT)
@@ -169,8 +234,8 @@ def sym_iteration(env, A, O, B, chi, cutoff=1e-12, symmetrise=True, info=None):
     if info is not None:
         info['asym'] = (float(np.linalg.norm(C1n - C1n.T) / np.linalg.norm(C1n)),
                         float(np.linalg.norm(C4n - C4n.T) / np.linalg.norm(C4n)))
-        info['spectra'] = linfo['spectra']
-        info['projectors'] = linfo['projectors']
+        info['projectors'] = P
+        info.update(pinfo)
     if symmetrise:
         C1n = 0.5 * (C1n + C1n.T)
         C4n = 0.5 * (C4n + C4n.T)
@@ -180,14 +245,15 @@ def sym_iteration(env, A, O, B, chi, cutoff=1e-12, symmetrise=True, info=None):
     return sym_env(C1n, C4n, T4n)
 
 
-def sym_iterate(env, A, O, B, chi, max_iter, tol=None, cutoff=1e-12, trace=None):
+def sym_iterate(env, A, O, B, chi, max_iter, tol=None, cutoff=1e-12, trace=None, p4='full',
+                pr='mirror'):
     """Iterate to ||S[i+1] - S[i]||_2 < tol with the convergence measure of Sec. III.D
     (``split_ctmrg.ctm_spectrum``).  Returns (env, iterations, last dS, spectrum)."""
     S_old = np.zeros(chi)
     dS = np.inf
     it = 0
     for it in range(1, max_iter + 1):
-        env = sym_iteration(env, A, O, B, chi, cutoff)
+        env = sym_iteration(env, A, O, B, chi, cutoff, p4=p4, pr=pr)
         S = np.zeros(chi)
         s = sc.ctm_spectrum(env)
         S[:len(s)] = s[:chi]
@@ -200,7 +266,8 @@ def sym_iterate(env, A, O, B, chi, max_iter, tol=None, cutoff=1e-12, trace=None)
     return env, it, dS, S_old
 
 
-def sym_evaluate(A, O_num, O_den, T, chi, max_iter, tol=None, cutoff=1e-12, seed=0):
+def sym_evaluate(A, O_num, O_den, T, chi, max_iter, tol=None, cutoff=1e-12, seed=0, p4='full',
+                 pr='mirror'):
     """f and the projected environment gradient of the D4-projected PEPS (Eqs. "free energy
     expression" and "gradient expression", Sec. III.B for the projections), both networks
     iterated from the symmetric cold start."""
@@ -210,7 +277,7 @@ def sym_evaluate(A, O_num, O_den, T, chi, max_iter, tol=None, cutoff=1e-12, seed
     for name, O in (('num', O_num), ('den', O_den)):
         d = O.shape[2]
         env = sym_init_env(chi, D, d, seed)
-        env, it, dS, S = sym_iterate(env, A, O, A, chi, max_iter, tol, cutoff)
+        env, it, dS, S = sym_iterate(env, A, O, A, chi, max_iter, tol, cutoff, p4=p4, pr=pr)
         loc = sc.local_contractions(env, A, O, A)
         E = sc.bra_environment(env, loc)
         res[name] = {'env': env, 'iters': it, 'dS': dS, 'S': S, 'lnk': sc.ln_kappa(loc),

@@ -96,6 +96,32 @@ void check_svd_info(sctm_ctx* c) {
     }
 }
 
+// The two generators of the D2 symmetry that the symmetric split method relies on (Sec. III.B):
+// the reflection about the main diagonal (u <-> l, d <-> r) and the 180-degree rotation (u <-> d,
+// l <-> r) with the exchange s_up <-> s_dn, each to 1e-12 of max|O|.
+bool pepo_has_d2_symmetry(const double* pepo, const sctm_opts& o) {
+    const long long no = pepo_size(o);
+    std::vector<double> h((size_t)no);
+    cuda_ok(cudaMemcpy(h.data(), pepo, no * sizeof(double), cudaMemcpyDefault), "copy pepo");
+    const int p = o.p, d = o.d;
+    auto at = [&](int t, int s, int u, int l, int dd, int r) {
+        return h[((((((size_t)t * p + s) * d + u) * d + l) * d + dd) * d + r)];
+    };
+    double mx = 0.0, dev = 0.0;
+    for (double v : h) mx = std::max(mx, std::fabs(v));
+    for (int t = 0; t < p; ++t)
+        for (int s = 0; s < p; ++s)
+            for (int u = 0; u < d; ++u)
+                for (int l = 0; l < d; ++l)
+                    for (int dd = 0; dd < d; ++dd)
+                        for (int r = 0; r < d; ++r) {
+                            const double v = at(t, s, u, l, dd, r);
+                            dev = std::max(dev, std::fabs(v - at(t, s, l, u, r, dd)));
+                            dev = std::max(dev, std::fabs(v - at(s, t, dd, r, u, l)));
+                        }
+    return dev <= 1e-12 * mx;
+}
+
 // cold start of one network (and, for the reduced method, the fused site tensor from A)
 void init_network(sctm_ctx* c, int n) {
     Network& net = c->net[n];
@@ -160,9 +186,13 @@ sctm_status sctm_create(const double* peps, const double* pepo, int chi, const s
         (opts.grad_mode != SCTM_GRAD_ENV && opts.grad_mode != SCTM_GRAD_ADJOINT) ||
         !(opts.svd_cutoff >= 0.0) || opts.D > 64 || opts.d > 64 || opts.p > 64 ||
         opts.svd_mode < SCTM_SVD_QR || opts.svd_mode > SCTM_SVD_PARTIAL_RANDOM ||
-        (opts.method != SCTM_METHOD_SPLIT && opts.method != SCTM_METHOD_REDUCED) ||
+        (opts.method != SCTM_METHOD_SPLIT && opts.method != SCTM_METHOD_REDUCED &&
+         opts.method != SCTM_METHOD_SPLIT_D2) ||
         (opts.method == SCTM_METHOD_REDUCED &&
-         (opts.precision != SCTM_PREC_FP64 || opts.grad_mode != SCTM_GRAD_ENV)))
+         (opts.precision != SCTM_PREC_FP64 || opts.grad_mode != SCTM_GRAD_ENV)) ||
+        (opts.method == SCTM_METHOD_SPLIT_D2 && opts.grad_mode != SCTM_GRAD_ENV) ||
+        (opts.p4_mode != SCTM_P4_FULL && opts.p4_mode != SCTM_P4_HALF) ||
+        (opts.p4_mode == SCTM_P4_HALF && opts.method != SCTM_METHOD_SPLIT_D2))
         return SCTM_EINVAL;
     std::unique_ptr<sctm_ctx> c(new sctm_ctx());
     c->opts = opts;
@@ -186,6 +216,11 @@ sctm_status sctm_create(const double* peps, const double* pepo, int chi, const s
         c->A_stage = e.dalloc(na);
         if (!e.dry) {
             if (!peps_is_finite(c.get(), c->A_dev)) return SCTM_ENUMERIC;
+            if (opts.method == SCTM_METHOD_SPLIT_D2) {
+                if (!pepo_has_d2_symmetry(pepo, opts)) return SCTM_EINVAL;
+                launch_copy(c->A_dev, c->A_stage, na, s);
+                launch_d4_project(c->A_stage, c->A_dev, opts.p, opts.D, s);
+            }
             cuda_ok(cudaMemcpy(c->O_dev, pepo, no * sizeof(double), cudaMemcpyDefault),
                     "copy pepo");
             std::vector<double> oid((size_t)opts.p * opts.p, 0.0);
@@ -205,6 +240,7 @@ sctm_status sctm_create(const double* peps, const double* pepo, int chi, const s
             net.O = n == 0 ? view(c->O_dev, {opts.p, opts.p, opts.d, opts.d, opts.d, opts.d})
                            : view(c->Oid_dev, {opts.p, opts.p, 1, 1, 1, 1});
             net.method = opts.method;
+            net.p4_half = opts.p4_mode == SCTM_P4_HALF;
             if (opts.method == SCTM_METHOD_REDUCED)
                 e.build_reduced_network(net);
             else
@@ -212,7 +248,7 @@ sctm_status sctm_create(const double* peps, const double* pepo, int chi, const s
         }
         if (e.dry) {  // plans only: report success without a usable context
             const char* da = getenv("SCTM_DRYRUN_ADJOINT");
-            if (da && da[0] == '1')
+            if (da && da[0] == '1' && opts.method == SCTM_METHOD_SPLIT)
                 for (int n = 0; n < 2; ++n) e.build_adjoint(c->net[n]);
             c.reset();
             return SCTM_OK;
@@ -243,7 +279,10 @@ sctm_status sctm_set_peps(sctm_ctx* ctx, const double* peps, int reset_env) {
         ctx->err = "PEPS tensor has a non-finite entry (previous PEPS kept)";
         return SCTM_ENUMERIC;
     }
-    launch_copy(ctx->A_stage, ctx->A_dev, na, ctx->eng->stream);
+    if (ctx->opts.method == SCTM_METHOD_SPLIT_D2)  // kept in the D4-invariant subspace
+        launch_d4_project(ctx->A_stage, ctx->A_dev, ctx->opts.p, ctx->opts.D, ctx->eng->stream);
+    else
+        launch_copy(ctx->A_stage, ctx->A_dev, na, ctx->eng->stream);
     for (int n = 0; n < 2; ++n) {
         if (reset_env)
             init_network(ctx, n);
@@ -417,6 +456,10 @@ sctm_status sctm_grad(sctm_ctx* ctx, double* g) {
         finish_local(ctx);
         launch_grad_combine(ctx->net[0].E.p, ctx->net[0].lnk, ctx->net[1].E.p, ctx->net[1].lnk,
                             ctx->opts.T, n, ctx->g_dev, e.stream);
+        if (ctx->opts.method == SCTM_METHOD_SPLIT_D2) {  // the D4 group average of g
+            launch_copy(ctx->g_dev, ctx->A_stage, n, e.stream);
+            launch_d4_project(ctx->A_stage, ctx->g_dev, ctx->opts.p, ctx->opts.D, e.stream);
+        }
     }
     check_cuda("gradient");
     cuda_ok(cudaMemcpyAsync(g, ctx->g_dev, n * sizeof(double), cudaMemcpyDefault, e.stream),
@@ -508,15 +551,44 @@ static sctm_status env_copy(sctm_ctx* ctx, int network, double* host, size_t n, 
     for (int i = 0; i < 4; ++i) ts.push_back(&net.C[i]);
     for (int i = 0; i < 4; ++i)
         for (int x = 0; x < 3; ++x) ts.push_back(&net.T[i][x]);
+    const bool sym = net.method == SCTM_METHOD_SPLIT_D2;
     size_t off = 0;
     cuda_ok(cudaStreamSynchronize(ctx->eng->stream), "sync");
-    for (Ten* t : ts) {
-        const size_t bytes = (size_t)t->numel() * sizeof(double);
-        if (to_host)
-            cuda_ok(cudaMemcpy(host + off, t->p, bytes, cudaMemcpyDeviceToHost), "env export");
-        else
+    for (size_t k = 0; k < ts.size(); ++k) {
+        Ten* t = ts[k];
+        const size_t cnt = (size_t)t->numel(), bytes = cnt * sizeof(double);
+        // the symmetric method stores C1 (slot 0), C4 (slot 3) and T4 (slots 13..15); the other
+        // slots are views of them (possibly with permuted strides)
+        const bool stored = !sym || k == 0 || k == 3 || k >= 13;
+        if (to_host) {
+            bool contiguous = true;
+            for (int i = t->nd - 1, st = 1; i >= 0; st *= t->dim[i], --i)
+                contiguous = contiguous && t->st[i] == st;
+            if (contiguous) {
+                cuda_ok(cudaMemcpy(host + off, t->p, bytes, cudaMemcpyDeviceToHost), "env export");
+            } else {  // a permuted view of a stored tensor of the same size: gather on the host
+                std::vector<double> raw(cnt);
+                cuda_ok(cudaMemcpy(raw.data(), t->p, bytes, cudaMemcpyDeviceToHost), "env export");
+                std::vector<int> ix(t->nd, 0);
+                for (size_t e = 0; e < cnt; ++e) {
+                    long long o = 0;
+                    for (int i = 0; i < t->nd; ++i) o += ix[i] * t->st[i];
+                    host[off + e] = raw[(size_t)o];
+                    for (int i = t->nd - 1; i >= 0; --i) {
+                        if (++ix[i] < t->dim[i]) break;
+                        ix[i] = 0;
+                    }
+                }
+            }
+        } else if (stored) {
             cuda_ok(cudaMemcpy(t->p, host + off, bytes, cudaMemcpyHostToDevice), "env import");
-        off += (size_t)t->numel();
+        }
+        off += cnt;
+    }
+    if (!to_host && sym) {
+        launch_symmetrize(net.C[0].p, net.chi, ctx->eng->stream);
+        launch_symmetrize(net.C[3].p, net.chi, ctx->eng->stream);
+        check_cuda("env import");
     }
     if (!to_host) ctx->eng->cold_svd(net);  // the warm-start subspaces belong to the old state
     return SCTM_OK;
@@ -535,6 +607,8 @@ sctm_status sctm_move(sctm_ctx* ctx, int network, int direction) {
     API_BEGIN(ctx)
     if (network < 0 || network > 1 || direction < 0 || direction > 3)
         throw Error(SCTM_EINVAL, "bad network or direction");
+    if (ctx->opts.method == SCTM_METHOD_SPLIT_D2 && direction != SCTM_MOVE_LEFT)
+        throw Error(SCTM_EINVAL, "the symmetric method has one update per iteration (LEFT)");
     ctx->eng->run(ctx->net[network].move[direction]);
     check_cuda("move");
     cuda_ok(cudaStreamSynchronize(ctx->eng->stream), "move sync");

@@ -834,7 +834,10 @@ static Frame make_frame(const Network& n, int move) {
 // ---------------------------------------------------------------------------------------------
 // the left move (Sec. III.B, Fig. 5; Sec. III.C and Appendix for the projectors)
 // ---------------------------------------------------------------------------------------------
-static void build_left_move(Engine& e, Network& net, Plan& P, const Frame& f) {
+// sym: the D2-symmetric iteration (Sec. III.B, Eq. "Symmetry constraints" and the symmetric
+// corner absorption): the same projectors and edge update, but each corner absorbs its column
+// and its row at once and both of its legs are truncated by the alpha pair.
+static void build_left_move(Engine& e, Network& net, Plan& P, const Frame& f, bool sym = false) {
     auto C = [&](const char* spec, const Ten& X, const Ten& Y) { return e.ctr(net, P, spec, X, Y); };
     const Ten &C1 = f.C[0], &C2 = f.C[1], &C3 = f.C[2], &C4 = f.C[3];
     const Ten &T1k = f.T[0][0], &T1i = f.T[0][1], &T1b = f.T[0][2];
@@ -889,6 +892,7 @@ static void build_left_move(Engine& e, Network& net, Plan& P, const Frame& f) {
     Ten ULA, URA, ULAO, URAO, Q1pre, Q2pre;           // upper halves (stream 7)
     Ten LLkpre, LRkpre, LLipre, LRipre;               // lower halves, kappa and iota (stream 8)
     Ten Q4pre, Q3pre;                                 // lower halves, alpha (stream 9)
+    const bool half4 = sym && net.p4_half;
     {
         const Ten* U[6] = {&Ua, &Ua, &Uk, &Uk, &Ui, &Ui};
         const Ten* L[6] = {&La, &La, &Lk, &Lk, &Li, &Li};
@@ -896,8 +900,21 @@ static void build_left_move(Engine& e, Network& net, Plan& P, const Frame& f) {
         const char* tl[6] = {"xB", "yA", "xsb", "yes", "xtb", "yet"};
         std::vector<Plan> sub(9);
         for (int i = 0; i < 6; ++i) {
+            if (sym && (i & 1)) continue;  // the opposite boundary's pairs follow by symmetry
             e.cur_stream = i + 1;
             pr1[i] = e.projector(net, sub[i], *U[i], *L[i], lab[i], tl[i]);
+        }
+        if (sym) {
+            // D2 symmetry (Appendix, captions of projectors 4-6): the rotation by 180 degrees with
+            // ket <-> bra puts the right column's alpha / kappa / iota cut onto this column's
+            // alpha / iota / kappa cut, (xr, A_v) onto (xl, B_v), (xr, A.d, s) onto
+            // (xl, B.u, s') and (xr, A.d, s') onto (xl, B.u, s); P_B and P_T trade places
+            pr1[1].PB = permute(pr1[0].PT, {1, 2, 0});
+            pr1[1].PT = permute(pr1[0].PB, {2, 0, 1});
+            pr1[3].PB = permute(pr1[4].PT, {1, 3, 2, 0});
+            pr1[3].PT = permute(pr1[4].PB, {3, 0, 2, 1});
+            pr1[5].PB = permute(pr1[2].PT, {1, 3, 2, 0});
+            pr1[5].PT = permute(pr1[2].PB, {3, 0, 2, 1});
         }
         {
             Plan& S = sub[6];
@@ -908,7 +925,8 @@ static void build_left_move(Engine& e, Network& net, Plan& P, const Frame& f) {
             ULAO = D("hobsErXL,tsoLfR->hbErXtfR", D("hobxsEr,xXL->hobsErXL", ULA, T4i), O);
             URAO = D("hobsElYR,tsoLfR->hbElYtfL", D("hobysEl,yYR->hobsElYR", URA, T2i), O);
             Q1pre = D("hbErtfRZM,tbMgS->hErfRZgS", D("hbErXtfR,XZM->hbErtfRZM", ULAO, T4b), B);
-            Q2pre = D("hbElWtfLS,tbMgS->hElWfLMg", D("hbElYtfL,YWS->hbElWtfLS", URAO, T2b), B);
+            if (!half4)  // the upper-right quarter of the 2x2-cell patch
+                Q2pre = D("hbElWtfLS,tbMgS->hElWfLMg", D("hbElYtfL,YWS->hbElWtfLS", URAO, T2b), B);
         }
         {
             Plan& S = sub[7];
@@ -937,7 +955,12 @@ static void build_left_move(Engine& e, Network& net, Plan& P, const Frame& f) {
             Y1 = D("hEftbSXL,tsoLfR->hEbSXsoR", Y1, O);
             Y1 = D("hEbSXsoR,xXl->hEbSsoRxl", Y1, T4k);
             Q4pre = D("hEbSsoRxl,splEr->hbSoRxpr", Y1, A);
-            Y1 = D("hwEfg,WwS->hEfgWS", Ct3, T2b);
+        }
+        if (!half4) {  // the lower-right quarter of the 2x2-cell patch
+            Plan& S = sub[8];
+            e.cur_stream = 9;
+            auto D = [&](const char* spec, const Ten& X1, const Ten& Y1) { return e.ctr(net, S, spec, X1, Y1); };
+            Ten Y1 = D("hwEfg,WwS->hEfgWS", Ct3, T2b);
             Y1 = D("hEfgWS,tbMgS->hEfWtbM", Y1, B);
             Y1 = D("hEfWtbM,ZWR->hEftbMZR", Y1, T2i);
             Y1 = D("hEftbMZR,tsoLfR->hEbMZsoL", Y1, O);
@@ -957,17 +980,26 @@ static void build_left_move(Engine& e, Network& net, Plan& P, const Frame& f) {
     {
         std::vector<Plan> sub(3);
         // alpha (2 x 2 cells): (k1, A_v, O_v | O_v', B_v', kR)
+        // half (2 x 1 cells, D2 scheme): (k1, A.d, O.d | k2, A.r, O.r) above the cut and
+        // (k1, A.u, O.u | k2, B.r, O.r) below, the column-cut bra lines renormalised by the
+        // transposed projector 1 (the lower corner's in the down move's frame: its ket line)
         {
             Plan& S = sub[0];
             e.cur_stream = 1;
             auto D = [&](const char* spec, const Ten& X1, const Ten& Y1) { return e.ctr(net, S, spec, X1, Y1); };
             const Ten Q1 = D("hErfRZgS,kZg->hkEfrRS", Q1pre, Pa.PT);
-            const Ten Q2 = D("hElWfLMg,kWE->hlLMfgk", Q2pre, Qa.PT);
-            const Ten U2a = D("hkEfrRS,hrRSFGK->kEfFGK", Q1, Q2);
             const Ten Q4 = D("hbSoRxpr,xbk->hkporRS", Q4pre, Pa.PB);
-            const Ten Q3 = D("hbMoLypl,ypk->hlLMobk", Q3pre, Qa.PB);
-            const Ten L2a = D("hkporRS,hrRSOBK->kpoOBK", Q4, Q3);
-            pr2[0] = e.projector(net, S, U2a, L2a, "abcdef", "abc");
+            if (half4) {
+                const Ten U2a = D("hkEfrRS,jhS->kEfjrR", Q1, Pa.PT);
+                const Ten L2a = D("hkporRS,hrj->kpojSR", Q4, Pa.PB);
+                pr2[0] = e.projector(net, S, U2a, L2a, "abcdef", "abc");
+            } else {
+                const Ten Q2 = D("hElWfLMg,kWE->hlLMfgk", Q2pre, Qa.PT);
+                const Ten U2a = D("hkEfrRS,hrRSFGK->kEfFGK", Q1, Q2);
+                const Ten Q3 = D("hbMoLypl,ypk->hlLMobk", Q3pre, Qa.PB);
+                const Ten L2a = D("hkporRS,hrRSOBK->kpoOBK", Q4, Q3);
+                pr2[0] = e.projector(net, S, U2a, L2a, "abcdef", "abc");
+            }
         }
         // kappa (1 x 2 cells): (k2, A.d, O.u | O.u', B.u', kR)
         {
@@ -1009,8 +1041,28 @@ static void build_left_move(Engine& e, Network& net, Plan& P, const Frame& f) {
     const Ten PiT = C("kKef,Kxtb->kxeftb", P6.PT, Pi.PT);
 
     // renormalisation (Fig. 5(c)); crossing lines are summed between the two projectors
-    const Ten C1n = C("hvpob,kvpob->hk", Ct1, PaT);
-    const Ten C4n = C("hvEfg,vEfgk->hk", Ct4, PaB);
+    Ten C1n, C4n;
+    if (sym) {
+        // Q1pre is C1 with one column (T1^{k,i,b}) and one row (T4^{k,i,b} and the site)
+        // absorbed, [h, A.d, A.r, O.d, O.r, v, B.d, B.r]; P_T truncates its row-cut group
+        // (v, A.d, O.d, B.d) and, read in the diagonally reflected frame, its column-cut group
+        // (h, A.r, O.r, B.r).  Q4pre, [h, B.u, B.r, O.u, O.r, v, A.u, A.r], is the same for C4
+        // (bottom edge, last row); P_B truncates (v, A.u, O.u, B.u) and, in the frame reflected
+        // about the anti-diagonal (which exchanges ket and bra), (h, B.r, O.r, A.r).
+        X = C("hErfRZgS,kZEfg->hrRSk", Q1pre, PaT);
+        C1n = C("hrRSk,jhrRS->jk", X, PaT);
+        X = C("hbSoRxpr,xpobk->hSRrk", Q4pre, PaB);
+        C4n = C("hSRrk,hSRrj->jk", X, PaB);
+        double *c1 = C1n.p, *c4 = C4n.p;
+        const int n = net.chi;
+        e.push(P, std::make_unique<FnStep>([=](cudaStream_t s) {
+            launch_symmetrize(c1, n, s);
+            launch_symmetrize(c4, n, s);
+        }));
+    } else {
+        C1n = C("hvpob,kvpob->hk", Ct1, PaT);
+        C4n = C("hvEfg,vEfgk->hk", Ct4, PaB);
+    }
     X = C("xpobK,xXl->pobKXl", PaB, T4k);
     X = C("pobKXl,splEr->obKXsEr", X, A);
     const Ten T4kn = C("obKXsEr,kXEsob->Kkr", X, PkT);
@@ -1224,6 +1276,19 @@ void Engine::init_env(Network& net, unsigned long long seed) {
     cold_svd(net);
     if (dry) return;
     CUDA_OK(cudaMemsetAsync(dev_err, 0, 2 * sizeof(int), stream));
+    if (net.method == SCTM_METHOD_SPLIT_D2) {
+        // the stored C1, C4 and T4 take the directional cold start's draws of their slots (0, 3
+        // and 13..15); the corners are symmetrised, the other slots are views of these
+        launch_splitmix_fill(net.C[0].p, net.C[0].numel(), seed, 0, stream);
+        launch_splitmix_fill(net.C[3].p, net.C[3].numel(), seed, 3, stream);
+        for (int x = 0; x < 3; ++x)
+            launch_splitmix_fill(net.T[3][x].p, net.T[3][x].numel(), seed, 13 + x, stream);
+        launch_symmetrize(net.C[0].p, net.chi, stream);
+        launch_symmetrize(net.C[3].p, net.chi, stream);
+        launch_zero(net.S_old, net.chi, stream);
+        CUDA_OK(cudaGetLastError());
+        return;
+    }
     unsigned long long q = 0;
     for (int i = 0; i < 4; ++i) launch_splitmix_fill(net.C[i].p, net.C[i].numel(), seed, q++, stream);
     for (int i = 0; i < 4; ++i)
@@ -1235,25 +1300,48 @@ void Engine::init_env(Network& net, unsigned long long seed) {
 
 void Engine::build_network(Network& net) {
     const int chi = net.chi, D = net.D, d = net.d;
-    for (int i = 0; i < 4; ++i) net.C[i] = alloc({chi, chi});
-    for (int i = 0; i < 4; ++i) {
-        net.T[i][0] = alloc({chi, chi, D});
-        net.T[i][1] = alloc({chi, chi, d});
-        net.T[i][2] = alloc({chi, chi, D});
+    const bool sym = net.method == SCTM_METHOD_SPLIT_D2;
+    if (sym) {
+        // D2-symmetric environment (Sec. III.B, Eq. "Symmetry constraints"): only C1, C4 and the
+        // left edge are stored; C3 = C1, C2 = C4 (both symmetric), T1 = T4, and T2 = T3 = T4
+        // with ket <-> bra and the two chain bonds exchanged, as strided views
+        net.C[0] = alloc({chi, chi});
+        net.C[3] = alloc({chi, chi});
+        net.T[3][0] = alloc({chi, chi, D});
+        net.T[3][1] = alloc({chi, chi, d});
+        net.T[3][2] = alloc({chi, chi, D});
+        net.C[1] = net.C[3];
+        net.C[2] = net.C[0];
+        for (int x = 0; x < 3; ++x) {
+            net.T[0][x] = net.T[3][x];
+            net.T[1][x] = permute(net.T[3][2 - x], {1, 0, 2});
+            net.T[2][x] = net.T[1][x];
+        }
+    } else {
+        for (int i = 0; i < 4; ++i) net.C[i] = alloc({chi, chi});
+        for (int i = 0; i < 4; ++i) {
+            net.T[i][0] = alloc({chi, chi, D});
+            net.T[i][1] = alloc({chi, chi, d});
+            net.T[i][2] = alloc({chi, chi, D});
+        }
     }
     net.S_old = dalloc(chi);
     net.dS = dalloc(1);
     net.lnk = dalloc(2);
     net.E = alloc({net.p, D, D, D, D});
     mixed_build = true;
-    for (int m = 0; m < 4; ++m) {
-        tape = &net.tape_move[m];
-        build_left_move(*this, net, net.move[m], make_frame(net, m));
+    if (sym) {  // one update per iteration (moves 1..3 stay empty)
+        build_left_move(*this, net, net.move[SCTM_MOVE_LEFT], make_frame(net, SCTM_MOVE_LEFT), true);
+    } else {
+        for (int m = 0; m < 4; ++m) {
+            tape = &net.tape_move[m];
+            build_left_move(*this, net, net.move[m], make_frame(net, m));
+        }
     }
     mixed_build = false;
     tape = nullptr;
     build_spectrum(*this, net);
-    tape = &net.tape_local;
+    tape = sym ? nullptr : &net.tape_local;
     build_local(*this, net);
     tape = nullptr;
     finalize(net);

@@ -111,7 +111,8 @@ struct Network {
     int precision = SCTM_PREC_FP64;  // form of the mixed-eligible contractions (set_precision)
     double cutoff_now = 0.0;         // pseudo-inverse cutoff in use (raised for mixed forms)
     std::vector<struct SvdStep*> svd_steps;
-    int method = SCTM_METHOD_SPLIT;       // SCTM_METHOD_SPLIT or SCTM_METHOD_REDUCED
+    int method = SCTM_METHOD_SPLIT;       // SCTM_METHOD_SPLIT, _SPLIT_D2 or _REDUCED
+    bool p4_half = false;                 // projector 4 from the 2x1-cell patch (SPLIT_D2)
     Plan site;                            // reduced method: the fused site tensor from A, O, A-bar
     Ten fused;                            // reduced method: a[m, m, m, m], m = D d D
     int tuned_emu = 0, tuned_total = 0;  // autotune: contractions on the emulation / eligible

@@ -354,6 +354,60 @@ void launch_copy(const double* src, double* dst, long long n, cudaStream_t s) {
     copy_kernel<<<std::max(blocks, 1), 256, 0, s>>>(src, dst, n);
 }
 
+// C <- (C + C^T) / 2 in place, n x n row-major: one thread per pair (i < j), the diagonal kept
+// (the symmetric split-CTMRG corners, Sec. III.B, Eq. "Symmetry constraints")
+__global__ void symmetrize_kernel(double* X, int n) {
+    const long long m = (long long)n * n;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < m;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(idx / n), j = (int)(idx % n);
+        if (i >= j) continue;
+        const double v = 0.5 * (X[(long long)i * n + j] + X[(long long)j * n + i]);
+        X[(long long)i * n + j] = v;
+        X[(long long)j * n + i] = v;
+    }
+}
+
+void launch_symmetrize(double* X, int n, cudaStream_t s) {
+    const long long m = (long long)n * n;
+    int blocks = (int)std::min<long long>((m + 255) / 256, 1024);
+    symmetrize_kernel<<<std::max(blocks, 1), 256, 0, s>>>(X, n);
+}
+
+// Average of A[s, u, l, d, r] over the square's symmetry group D4 acting on the virtual legs
+// (Sec. III.B: the PEPS and its gradient kept in the D4-invariant subspace).  The group maps the
+// output index (i0, i1, i2, i3) of the legs in cyclic order u, l, d, r to the inputs
+// (i_k, i_k+1, i_k+2, i_k+3) (rotations) and (i_k, i_k-1, i_k-2, i_k-3) (reflections), k = 0..3,
+// indices mod 4.
+__global__ void d4_project_kernel(const double* in, double* out, int p, int D) {
+    const long long D2 = (long long)D * D, D4 = D2 * D2;
+    const long long n = (long long)p * D4;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long s = idx / D4;
+        long long r = idx - s * D4;
+        int c[4];
+        for (int q = 3; q >= 0; --q) {
+            c[q] = (int)(r % D);
+            r /= D;
+        }
+        double acc = 0.0;
+        for (int k = 0; k < 4; ++k)
+            for (int dir = 1; dir >= -1; dir -= 2) {
+                long long off = 0;
+                for (int q = 0; q < 4; ++q) off = off * D + c[(k + dir * q + 8) & 3];
+                acc += in[s * D4 + off];
+            }
+        out[idx] = 0.125 * acc;
+    }
+}
+
+void launch_d4_project(const double* in, double* out, int p, int D, cudaStream_t s) {
+    const long long n = (long long)p * D * D * D * D;
+    int blocks = (int)std::min<long long>((n + 255) / 256, 2048);
+    d4_project_kernel<<<std::max(blocks, 1), 256, 0, s>>>(in, out, p, D);
+}
+
 __global__ void zero_kernel(double* p, long long n) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x)

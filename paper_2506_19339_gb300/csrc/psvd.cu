@@ -73,44 +73,45 @@ __device__ void block_cholesky(double* R, double* rinv, int k) {
     }
 }
 
+// Scratch of one Jacobi round, one entry per column pair.
+struct RoundScratch {
+    double* c;   // cosine of each pair's rotation
+    double* s;   // sine
+    int* act;    // 1 if the pair rotates
+    int* pi;     // the pair's columns i, j (this round)
+    int* pj;
+};
+
 // One sweep of one-sided Jacobi rotations over all column pairs (circle-method rounds) of the
-// kp x kp column-major matrix A (leading dimension ld), accumulating into V (same layout).  The
-// pairs of one round touch disjoint columns, so a warp takes a pair from start to end: its lanes
-// form the three dot products over the rows (shuffle-reduced, fixed order), lane 0 forms the
-// rotation (the FP64 square roots and divisions once per pair, not once per lane) and
-// broadcasts it, and the lanes rotate the two columns of A and V; one block barrier per round.
-// Pairs with |a_i . a_j| <= tol |a_i| |a_j| are left alone.  Returns (to every thread) the
-// largest |a_i . a_j| / (|a_i| |a_j|) seen.
+// kp x kp column-major matrix A (leading dimension ld), accumulating into V (same layout).  Per
+// round: thread q < kp/2 forms pair q's three dot products and its rotation (one pair per
+// thread, so the FP64 square roots and divisions are not repeated across a warp), then every
+// thread applies the rotations, one (pair, row) element at a time.  Pairs with
+// |a_i . a_j| <= tol |a_i| |a_j| are left alone.  Returns (to every thread) the largest
+// |a_i . a_j| / (|a_i| |a_j|) seen.
 template <typename F>
-__device__ float jacobi_sweep(F* A, F* V, int kp, int ld, F tol, float* s_max) {
-    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5,
-              nw = nt >> 5;
+__device__ float jacobi_sweep(F* A, F* V, int kp, int ld, F tol, RoundScratch rs, float* s_max) {
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
     const int np = kp / 2;
     if (tid == 0) *s_max = 0.0f;
     float wmax = 0.0f;
     for (int round = 0; round < kp - 1; ++round) {
-        for (int q = warp; q < np; q += nw) {
+        for (int q = tid; q < np; q += nt) {
             const int p0 = q, p1 = kp - 1 - q;
             const int i = p0 == 0 ? 0 : 1 + (p0 - 1 + round) % (kp - 1);
             const int j = 1 + (p1 - 1 + round) % (kp - 1);
-            F* ai = A + (long long)i * ld;
-            F* aj = A + (long long)j * ld;
+            const F* ai = A + (long long)i * ld;
+            const F* aj = A + (long long)j * ld;
             F al = 0, be = 0, ga = 0;
-            for (int r = lane; r < kp; r += 32) {
+            for (int r = 0; r < kp; ++r) {
                 const F x = ai[r], y = aj[r];
                 al = fma(x, x, al);
                 be = fma(y, y, be);
                 ga = fma(x, y, ga);
             }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                al += __shfl_xor_sync(0xffffffffu, al, o);
-                be += __shfl_xor_sync(0xffffffffu, be, o);
-                ga += __shfl_xor_sync(0xffffffffu, ga, o);
-            }
-            F c = 1, sn = 0;
             int act = 0;
-            if (lane == 0 && al > F(0) && be > F(0)) {
+            F c = 1, sn = 0;
+            if (al > F(0) && be > F(0)) {
                 const F rel = fabs(ga) / (sqrt(al) * sqrt(be));
                 wmax = fmaxf(wmax, (float)rel);
                 if (rel > tol) {
@@ -121,13 +122,22 @@ __device__ float jacobi_sweep(F* A, F* V, int kp, int ld, F tol, float* s_max) {
                     act = 1;
                 }
             }
-            act = __shfl_sync(0xffffffffu, act, 0);
-            if (!act) continue;
-            c = __shfl_sync(0xffffffffu, c, 0);
-            sn = __shfl_sync(0xffffffffu, sn, 0);
-            F* vi = V + (long long)i * ld;
-            F* vj = V + (long long)j * ld;
-            for (int r = lane; r < kp; r += 32) {
+            rs.c[q] = (double)c;
+            rs.s[q] = (double)sn;
+            rs.act[q] = act;
+            rs.pi[q] = i;
+            rs.pj[q] = j;
+        }
+        __syncthreads();
+        // rotations: warp per pair, lane per row (no integer division in the inner loop)
+        for (int q = tid >> 5; q < np; q += nt >> 5) {
+            if (!rs.act[q]) continue;
+            const F c = (F)rs.c[q], sn = (F)rs.s[q];
+            F* ai = A + (long long)rs.pi[q] * ld;
+            F* aj = A + (long long)rs.pj[q] * ld;
+            F* vi = V + (long long)rs.pi[q] * ld;
+            F* vj = V + (long long)rs.pj[q] * ld;
+            for (int r = tid & 31; r < kp; r += 32) {
                 const F x = ai[r], y = aj[r];
                 ai[r] = c * x - sn * y;
                 aj[r] = sn * x + c * y;
@@ -205,13 +215,19 @@ __global__ void __launch_bounds__(kPsvdThreads)
     jacobi_svd_kernel(const double* __restrict__ B, int k, double* __restrict__ S,
                       double* __restrict__ U, double* __restrict__ W, int* info, double* Vg) {
     extern __shared__ double sm[];
-    const int kp = k + (k & 1), ld = kp + 1;
+    const int kp = k + (k & 1), ld = kp + 1, np = kp / 2;
     double* A = sm;                        // FP64 phase: column j at A + j ld
     double* V = Vg ? Vg : sm + kp * ld;    // W, column j at V + j ld (global above kPsvdSmemK)
     float* A32 = (float*)A;                // FP32 phase: both FP32 matrices inside A's space
     float* V32 = A32 + kp * ld;
     double* sig = sm + (Vg ? 1 : 2) * kp * ld;
-    int* rank = (int*)(sig + kp);
+    RoundScratch rs;
+    rs.c = sig + kp;
+    rs.s = rs.c + np;
+    int* rank = (int*)(rs.s + np);
+    rs.act = rank + kp;
+    rs.pi = rs.act + np;
+    rs.pj = rs.pi + np;
     __shared__ float s_max;
     __shared__ int s_exp;
     __shared__ double s_wmax[kPsvdThreads / 32];
@@ -246,7 +262,7 @@ __global__ void __launch_bounds__(kPsvdThreads)
     __syncthreads();
     const float tol32 = 4.0f * (float)kp * 5.9604645e-8f;
     for (int sw = 0; sw < kJacobiMaxSweeps32; ++sw)
-        if (jacobi_sweep<float>(A32, V32, kp, ld, tol32, &s_max) <= tol32) break;
+        if (jacobi_sweep<float>(A32, V32, kp, ld, tol32, rs, &s_max) <= tol32) break;
     // 2. W = V32 in FP64, re-orthonormalised: W <- W F^-1 with F^T F = W^T W
     for (int e = tid; e < kp * kp; e += nt) {
         const int r = e % kp, c = e / kp;
@@ -287,7 +303,7 @@ __global__ void __launch_bounds__(kPsvdThreads)
     {
         int sw = 0;
         for (; sw < kJacobiMaxSweeps64; ++sw) {
-            const float mx = jacobi_sweep<double>(A, V, kp, ld, tol64, &s_max);
+            const float mx = jacobi_sweep<double>(A, V, kp, ld, tol64, rs, &s_max);
             if (mx <= tol64 || mx < 1e-7f) break;
         }
         if (sw >= kJacobiMaxSweeps64) bad = 1;
@@ -353,9 +369,10 @@ void launch_refill(double* V, int n, int k, const double* S, unsigned long long 
 size_t chol_orth_smem(int k, bool global_x) {
     return (size_t)((global_x ? 1 : 2) * k * k + 2 * k) * sizeof(double);
 }
-size_t jacobi_svd_smem(int k, bool global_v) {  // A (and W), the singular values, the ranks
-    const int kp = k + (k & 1), ld = kp + 1;
-    return (size_t)((global_v ? 1 : 2) * kp * ld + kp) * sizeof(double) + (size_t)kp * sizeof(int);
+size_t jacobi_svd_smem(int k, bool global_v) {  // A (and W), S, the round scratch, the ranks
+    const int kp = k + (k & 1), ld = kp + 1, np = kp / 2;
+    return (size_t)((global_v ? 1 : 2) * kp * ld + kp + 2 * np) * sizeof(double) +
+           (size_t)(kp + 3 * np) * sizeof(int);
 }
 
 // The one-CTA kernels are bound by the FP64 throughput of their SM, which every warp resident on

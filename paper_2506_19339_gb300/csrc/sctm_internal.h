@@ -96,6 +96,9 @@ void launch_jacobi_svd(const double* B, int k, double* S, double* U, double* W, 
                        double* Vg, cudaStream_t s);
 void launch_vt_columns(const double* VT, double* Vout, int n, int k, cudaStream_t s);
 void launch_zero(double* p, long long n, cudaStream_t s);
+void launch_symmetrize(double* X, int n, cudaStream_t s);   // X <- (X + X^T) / 2, n x n
+// D4 group average of A[s, u, l, d, r] over its four virtual legs (out != in)
+void launch_d4_project(const double* in, double* out, int p, int D, cudaStream_t s);
 // flag[0] = 1 if any of p[0..n) is NaN or infinite, else 0
 void launch_check_finite(const double* p, long long n, int* flag, cudaStream_t s);
 // p[i] <- 0 where p[i] is not finite, and *flag <- 1 if any was (flag is never cleared here)

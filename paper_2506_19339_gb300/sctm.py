@@ -20,7 +20,8 @@ SCTM_PREC_FP64, SCTM_PREC_TF32, SCTM_PREC_TF32X3, SCTM_PREC_BF16, SCTM_PREC_BF16
 SCTM_GRAD_ENV, SCTM_GRAD_ADJOINT = 0, 1
 SCTM_SVD_QR, SCTM_SVD_POLAR, SCTM_SVD_PARTIAL, SCTM_SVD_PARTIAL_RANDOM = 0, 1, 2, 3
 SCTM_NET_NUM, SCTM_NET_DEN = 0, 1
-SCTM_METHOD_SPLIT, SCTM_METHOD_REDUCED = 0, 1
+SCTM_METHOD_SPLIT, SCTM_METHOD_REDUCED, SCTM_METHOD_SPLIT_D2 = 0, 1, 2
+SCTM_P4_FULL, SCTM_P4_HALF = 0, 1
 SCTM_MOVE_LEFT, SCTM_MOVE_RIGHT, SCTM_MOVE_UP, SCTM_MOVE_DOWN = range(4)
 
 
@@ -29,7 +30,7 @@ class SctmOpts(ctypes.Structure):
                 ('d', ctypes.c_int), ('precision', ctypes.c_int), ('grad_mode', ctypes.c_int),
                 ('svd_cutoff', ctypes.c_double), ('init_seed', ctypes.c_ulonglong),
                 ('batch', ctypes.c_int), ('cuda_stream', ctypes.c_void_p),
-                ('svd_mode', ctypes.c_int), ('method', ctypes.c_int)]
+                ('svd_mode', ctypes.c_int), ('method', ctypes.c_int), ('p4_mode', ctypes.c_int)]
 
 
 class SctmError(RuntimeError):
@@ -288,13 +289,14 @@ class SplitCTMRG:
     """Convenience owner of one context: create / iterate / f / g / destroy."""
 
     def __init__(self, peps, pepo, chi, T, precision=SCTM_PREC_FP64, cutoff=1e-12, seed=0,
-                 svd_mode=SCTM_SVD_QR, method=SCTM_METHOD_SPLIT):
+                 svd_mode=SCTM_SVD_QR, method=SCTM_METHOD_SPLIT, p4_mode=SCTM_P4_FULL):
         st, o = sctm_default_opts()
         p, D = peps.shape[0], peps.shape[1]
         o.T, o.D, o.p, o.d = float(T), D, p, pepo.shape[2]
         o.precision, o.svd_cutoff, o.init_seed = precision, cutoff, seed
         o.svd_mode = svd_mode
         o.method = method
+        o.p4_mode = p4_mode
         self.method = method
         self.chi, self.D, self.p, self.d = chi, D, p, pepo.shape[2]
         st, self.ctx = sctm_create(np.ascontiguousarray(peps, dtype=np.float64),

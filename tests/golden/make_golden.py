@@ -8,7 +8,7 @@ algorithm can be compared.  For each requested iteration count ("converged" = it
 the environment gradient g = -2T (E_num / Z11_num - E_den / Z11_den) (Sec. II, Eqs. "free energy
 expression" and "gradient expression"), both networks iterated from the SplitMix64 cold start.
 
-    python tests/golden/make_golden.py <case> [<case> ...]        (cases: see CASES)
+    python tests/golden/make_golden.py <case> [<case> ...]     (cases: see CASES, CASES_D2)
 
 Output: tests/golden/<case>.json.  Only oracle/ and the seeded input generators are imported.
 """
@@ -24,7 +24,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(os.path.dirname(HERE))
 sys.path.insert(0, ROOT)
 
-from oracle import ising, split_ctmrg as sc  # noqa: E402
+from oracle import ising, split_ctmrg as sc, split_ctmrg_d2 as sd  # noqa: E402
 from paper_2506_19339_gb300 import inputs  # noqa: E402
 
 # name: (D, chi, T, seed, eps, records, tol, max_iter); records are iteration counts and/or
@@ -36,6 +36,48 @@ CASES = {
     'cfg3_D4_chi64': (4, 64, 4.5, 2, 0.1, [2, 'converged'], 1e-11, 300),
     'cfg4_D5_chi100': (5, 100, 4.52, 3, 0.1, [2, 'converged'], 1e-11, 300),
 }
+
+# the D2-symmetric scheme (Sec. III.B; oracle/split_ctmrg_d2.py) on the D4 group average of the
+# same kind of input: name: (D, chi, T, seed, eps, tol, max_iter); converged record only
+CASES_D2 = {
+    'd2_D4_chi64': (4, 64, 4.5, 2, 0.1, 1e-11, 300),
+}
+
+
+def run_case_d2(name):
+    D, chi, T, seed, eps, tol, max_iter = CASES_D2[name]
+    A = sd.d4_project(inputs.perturbed_product_peps(D, seed, eps=eps))
+    nets = {'num': ising.ising_pepo(1.0 / T), 'den': ising.identity_pepo()}
+    out = {'case': name, 'D': D, 'chi': chi, 'T': T, 'seed': seed, 'eps': eps,
+           'peps': 'split_ctmrg_d2.d4_project(inputs.perturbed_product_peps(%d, %d, eps=%g))' % (
+               D, seed, eps),
+           'method': 'D2-symmetric split-CTMRG', 'cutoff': 1e-12, 'tol': tol, 'records': {},
+           'written_by': 'tests/golden/make_golden.py (oracle/split_ctmrg_d2.py, FP64 NumPy)',
+           'host': platform.machine()}
+    t0 = time.time()
+    res = {}
+    for k, O in nets.items():
+        env = sd.sym_init_env(chi, D, O.shape[2])
+        trace = []
+        env, it, dS, S = sd.sym_iterate(env, A, O, A, chi, max_iter, tol, 1e-12, trace)
+        loc = sc.local_contractions(env, A, O, A)
+        res[k] = {'lnk': sc.ln_kappa(loc), 'Z11': loc['Z11'], 'E': sc.bra_environment(env, loc),
+                  'it': it, 'dS': dS}
+        print('%s %s: %d iterations, dS %.3e (%.0f s)' % (name, k, it, dS, time.time() - t0),
+              flush=True)
+    f = -T * (res['num']['lnk'] - res['den']['lnk'])
+    g = sd.d4_project(-2.0 * T * (res['num']['E'] / res['num']['Z11'] -
+                                  res['den']['E'] / res['den']['Z11']))
+    out['records']['converged'] = {
+        'f': f, 'g': [float(x) for x in g.ravel()],
+        'iterations': {k: res[k]['it'] for k in nets},
+        'dS': {k: float(res[k]['dS']) for k in nets},
+        'lnk': {k: res[k]['lnk'] for k in nets}}
+    out['seconds'] = time.time() - t0
+    print('%s converged: f = %.15f' % (name, f), flush=True)
+    with open(os.path.join(HERE, name + '.json'), 'w') as fh:
+        json.dump(out, fh, indent=0)
+        fh.write('\n')
 
 
 def run_case(name):
@@ -96,5 +138,8 @@ def run_case(name):
 
 
 if __name__ == '__main__':
-    for case in sys.argv[1:] or list(CASES):
-        run_case(case)
+    for case in sys.argv[1:] or list(CASES) + list(CASES_D2):
+        if case in CASES_D2:
+            run_case_d2(case)
+        else:
+            run_case(case)

@@ -127,6 +127,51 @@ def test_reduced_plans_build_without_gpu(lib, D, chi, svd):
     assert out.stdout.strip() == '0', out.stdout + out.stderr
 
 
+@pytest.mark.parametrize('D,chi,svd,p4', [(2, 6, 0, 0), (4, 64, 3, 0), (3, 36, 2, 1), (5, 100, 3, 1),
+                                          (4, 64, 3, 1)])
+def test_symmetric_plans_build_without_gpu(lib, D, chi, svd, p4):
+    """SCTM_DRYRUN=1 with the D2-symmetric split method (Sec. III.B): the one-update iteration
+    (this boundary's stage-1 projectors, the opposite boundary's as their mirrored views, the
+    full or half projector 4, T4, and both corners from their enlarged forms), the spectrum and
+    the local contractions over the strided views of the derived environment slots build with
+    every label and dimension checked."""
+    import subprocess
+    import sys
+    code = ('import numpy as np\n'
+            'from paper_2506_19339_gb300 import sctm\n'
+            'st, o = sctm.sctm_default_opts()\n'
+            'o.D, o.d, o.svd_mode, o.method = %d, 2, %d, sctm.SCTM_METHOD_SPLIT_D2\n'
+            'o.p4_mode = %d\n'
+            'A = np.zeros((2,) + (%d,) * 4); O = np.zeros((2, 2) + (2,) * 4)\n'
+            'st, ctx = sctm.sctm_create(A, O, %d, o)\n'
+            'print(st)\n') % (D, svd, p4, D, chi)
+    env = dict(os.environ, SCTM_DRYRUN='1')
+    out = subprocess.run([sys.executable, '-c', code], cwd=ROOT, env=env, capture_output=True,
+                         text=True, timeout=300)
+    assert out.returncode == 0, out.stderr
+    assert out.stdout.strip() == '0', out.stdout + out.stderr
+
+
+def test_symmetric_method_option_checks(lib):
+    """The D2-symmetric method has the environment gradient only: the adjoint is rejected on
+    entry, before any device work."""
+    A = np.zeros((2, 2, 2, 2, 2))
+    O = np.zeros((2, 2, 2, 2, 2, 2))
+    st, o = sctm.sctm_default_opts()
+    o.method = sctm.SCTM_METHOD_SPLIT_D2
+    o.grad_mode = sctm.SCTM_GRAD_ADJOINT
+    assert sctm.sctm_create(A, O, 4, o)[0] == sctm.SCTM_EINVAL
+    o.grad_mode = sctm.SCTM_GRAD_ENV
+    o.method = 3
+    assert sctm.sctm_create(A, O, 4, o)[0] == sctm.SCTM_EINVAL
+    o.method = sctm.SCTM_METHOD_SPLIT          # the half projector 4 needs the symmetric scheme
+    o.p4_mode = sctm.SCTM_P4_HALF
+    assert sctm.sctm_create(A, O, 4, o)[0] == sctm.SCTM_EINVAL
+    o.method = sctm.SCTM_METHOD_SPLIT_D2
+    o.p4_mode = 2
+    assert sctm.sctm_create(A, O, 4, o)[0] == sctm.SCTM_EINVAL
+
+
 def test_reduced_method_option_checks(lib):
     """The reduced method is FP64 with the environment gradient only: other combinations are
     rejected on entry."""

@@ -1,0 +1,148 @@
+"""GPU parity of the D2-symmetric split-CTMRG (SCTM_METHOD_SPLIT_D2; arXiv:2506.19339 Sec. III.B,
+Eq. "Symmetry constraints" and the symmetric corner absorption) against the oracle's symmetric
+scheme (oracle/split_ctmrg_d2.py), and against the GPU's own directional scheme.
+
+The PEPS given to both sides is not symmetric: each side replaces it by its D4 group average, so
+the projection kernel is covered too.
+"""
+import json
+import os
+import time
+
+import numpy as np
+import pytest
+
+from oracle import ising, split_ctmrg_d2 as sd
+from paper_2506_19339_gb300 import inputs, sctm
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), 'golden')
+
+
+def _run(A, chi, T, max_it, tol, svd_mode=sctm.SCTM_SVD_QR, prec=sctm.SCTM_PREC_FP64,
+         method=sctm.SCTM_METHOD_SPLIT_D2, p4=sctm.SCTM_P4_FULL):
+    st, O = sctm.sctm_ising_pepo(T)
+    r = sctm.SplitCTMRG(A, O, chi, T, svd_mode=svd_mode, precision=prec, method=method,
+                        p4_mode=p4)
+    try:
+        t0 = time.time()
+        st, it, ds = r.iterate(max_it, tol)
+        f = r.free_energy()
+        g = r.grad()
+        secs = time.time() - t0
+        return {'f': f, 'g': g, 'st': st, 'it': it, 'dS': ds, 'env': (r.env(0), r.env(1)),
+                's': secs}
+    finally:
+        r.close()
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize('p4', [sctm.SCTM_P4_FULL, sctm.SCTM_P4_HALF])
+def test_d2_fixed_iterations_match_oracle(p4):
+    """Ten symmetric iterations at D=2, chi=8 (full SVD), with the full and the half projector 4:
+    f to 1e-10 and g to 1e-8 of the oracle's, and the exported environment obeys Eq. "Symmetry
+    constraints" exactly (the derived slots are strided views of C1, C4, T4; the corners are
+    symmetrised)."""
+    T, D, chi, n = 4.5, 2, 8, 10
+    A = inputs.perturbed_product_peps(D, 5, eps=0.2)
+    got = _run(A, chi, T, n, 0.0, p4=p4)
+    assert got['it'] == n
+    ref = sd.sym_evaluate(A, ising.ising_pepo(1 / T), ising.identity_pepo(), T, chi, n,
+                          p4='half' if p4 == sctm.SCTM_P4_HALF else 'full')
+    print('D2 scheme, %d iterations: |df|/|f| = %.1e, |dg|/|g| = %.1e' % (
+        n, abs(got['f'] - ref['f']) / abs(ref['f']), _rel(got['g'], ref['g'])))
+    assert abs(got['f'] - ref['f']) <= 1e-10 * abs(ref['f'])
+    assert _rel(got['g'], ref['g']) <= 1e-8
+    for env in got['env']:
+        assert sd.constraint_residual(env) == 0.0
+
+
+@pytest.mark.parametrize('svd_mode,prec,p4', [
+    (sctm.SCTM_SVD_QR, sctm.SCTM_PREC_FP64, sctm.SCTM_P4_FULL),
+    (sctm.SCTM_SVD_PARTIAL_RANDOM, sctm.SCTM_PREC_FP64, sctm.SCTM_P4_FULL),
+    (sctm.SCTM_SVD_PARTIAL_RANDOM, sctm.SCTM_PREC_F64EMU, sctm.SCTM_P4_FULL),
+    (sctm.SCTM_SVD_PARTIAL_RANDOM, sctm.SCTM_PREC_F64EMU, sctm.SCTM_P4_HALF)])
+def test_d2_converged_matches_oracle(svd_mode, prec, p4):
+    """Past convergence at D=3, chi=16 (both sides run 80 iterations; ||dS|| < 1e-11 is reached
+    after about 35): f to 1e-10, g to 1e-8.  A fixed count on both sides leaves no gap from
+    stopping at different iterations of the slowly decaying environment mode."""
+    T, D, chi, n = 4.5, 3, 16, 80
+    A = inputs.perturbed_product_peps(D, 2, eps=0.1)
+    got = _run(A, chi, T, n, 0.0, svd_mode, prec, p4=p4)
+    ref = sd.sym_evaluate(A, ising.ising_pepo(1 / T), ising.identity_pepo(), T, chi, n,
+                          p4='half' if p4 == sctm.SCTM_P4_HALF else 'full')
+    assert ref['num']['dS'] < 1e-11 and ref['den']['dS'] < 1e-11
+    print('D2 after %d iterations, svd %d prec %d p4 %d: last dS %.1e (oracle %.1e), '
+          '|df|/|f| = %.1e, |dg|/|g| = %.1e' % (
+              n, svd_mode, prec, p4, got['dS'], ref['num']['dS'],
+              abs(got['f'] - ref['f']) / abs(ref['f']), _rel(got['g'], ref['g'])))
+    assert abs(got['f'] - ref['f']) <= 1e-10 * abs(ref['f'])
+    assert _rel(got['g'], ref['g']) <= 1e-8
+
+
+def test_d2_matches_directional_scheme():
+    """Sec. III.B: for a symmetric PEPS the symmetric scheme and the four directional moves share
+    their fixed point.  D=4, chi=32, both on the GPU, each to ||dS|| < 1e-10: the same f (1e-9
+    relative) and the same projected gradient (1e-5), with the two schemes' iteration counts
+    and times reported."""
+    T, D, chi = 4.5, 4, 32
+    A = sd.d4_project(inputs.perturbed_product_peps(D, 2, eps=0.1))
+    sym = _run(A, chi, T, 800, 1e-10, sctm.SCTM_SVD_PARTIAL_RANDOM)
+    dirn = _run(A, chi, T, 800, 1e-10, sctm.SCTM_SVD_PARTIAL_RANDOM,
+                method=sctm.SCTM_METHOD_SPLIT)
+    assert sym['st'] == sctm.SCTM_OK and dirn['st'] == sctm.SCTM_OK
+    gd = sd.d4_project(dirn['g'])
+    print('D=4 chi=32: symmetric %d iterations %.2f s, directional %d iterations %.2f s; '
+          '|df|/|f| = %.1e, |dg|/|g| = %.1e' % (sym['it'], sym['s'], dirn['it'], dirn['s'],
+                                                abs(sym['f'] - dirn['f']) / abs(dirn['f']),
+                                                _rel(sym['g'], gd)))
+    assert abs(sym['f'] - dirn['f']) <= 1e-9 * abs(dirn['f'])
+    assert _rel(sym['g'], gd) <= 1e-5
+
+
+def test_d2_headline_size_against_stored_oracle_values():
+    """D=4, chi=64 (the benchmark's size), the randomized partial SVD in the FP64 emulation form,
+    converged, against the oracle's stored converged values of the symmetric scheme
+    (tests/golden/d2_D4_chi64.json, written by make_golden.py from oracle/ only)."""
+    path = os.path.join(GOLDEN, 'd2_D4_chi64.json')
+    if not os.path.exists(path):
+        pytest.skip('stored oracle values not written')
+    with open(path) as fh:
+        gold = json.load(fh)
+    ref = gold['records']['converged']
+    A = inputs.perturbed_product_peps(gold['D'], gold['seed'], eps=gold['eps'])
+    got = _run(A, gold['chi'], gold['T'], 400, 1e-11, sctm.SCTM_SVD_PARTIAL_RANDOM,
+               sctm.SCTM_PREC_F64EMU)
+    assert got['st'] == sctm.SCTM_OK, got['it']
+    g_ref = np.array(ref['g']).reshape(got['g'].shape)
+    print('D2 D=4 chi=64: %d iterations (oracle %s), %.2f s, |df|/|f| = %.1e, |dg|/|g| = %.1e' % (
+        got['it'], ref['iterations'], got['s'], abs(got['f'] - ref['f']) / abs(ref['f']),
+        _rel(got['g'], g_ref)))
+    assert abs(got['f'] - ref['f']) <= 1e-10 * abs(ref['f'])
+    assert _rel(got['g'], g_ref) <= 1e-8
+
+
+def test_d2_option_checks():
+    """A PEPO without the D2 symmetry is rejected at creation; single updates other than LEFT
+    and the adjoint gradient are rejected; a LEFT update is one symmetric iteration."""
+    T, D, chi = 4.5, 2, 4
+    A = inputs.perturbed_product_peps(D, 1)
+    st, O = sctm.sctm_ising_pepo(T)
+    st, o = sctm.sctm_default_opts()
+    o.T, o.D, o.method = T, D, sctm.SCTM_METHOD_SPLIT_D2
+    bad = np.array(O, dtype=np.float64).reshape(2, 2, 2, 2, 2, 2).copy()
+    bad[0, 0, 1, 0, 0, 0] += 0.1  # breaks u <-> l
+    st, ctx = sctm.sctm_create(A, bad, chi, o)
+    assert st == sctm.SCTM_EINVAL
+    st, ctx = sctm.sctm_create(A, np.asarray(O, dtype=np.float64), chi, o)
+    assert st == sctm.SCTM_OK
+    try:
+        assert sctm.sctm_move(ctx, sctm.SCTM_NET_NUM, sctm.SCTM_MOVE_UP) == sctm.SCTM_EINVAL
+        assert sctm.sctm_move(ctx, sctm.SCTM_NET_NUM, sctm.SCTM_MOVE_LEFT) == sctm.SCTM_OK
+        assert sctm.sctm_set_grad_mode(ctx, sctm.SCTM_GRAD_ADJOINT) == sctm.SCTM_EINVAL
+    finally:
+        sctm.sctm_destroy(ctx)
