@@ -69,6 +69,9 @@ def parse():
                          'the D2-symmetric scheme (one projector set per iteration) on the D4 '
                          'group average of the same PEPS, accepted against the oracle\'s stored '
                          'value of that scheme')
+    ap.add_argument('--p4', default=None, choices=['full', 'half'],
+                    help='projector 4 patch (Appendix): full (2x2 cells; the only one of the '
+                         'directional scheme) or half (2x1 cells; default of split-d2)')
     ap.add_argument('--gemm', default=None,
                     help='M,N,K: time one plain contraction O = X Y through sctm_gemm in the '
                          'headline precision instead (kernel isolation and profiler captures)')
@@ -295,7 +298,7 @@ def combine_ranks(ms, e2e_ms, dist, device):
 class Instance:
     """One context of the workload in one precision form, driven through the C ABI."""
 
-    def __init__(self, sctm, w, prec, svd, stream, dev, A_host, method='split'):
+    def __init__(self, sctm, w, prec, svd, stream, dev, A_host, method='split', p4='full'):
         import torch
         st, O = sctm.sctm_ising_pepo(w['T'])
         st, o = sctm.sctm_default_opts()
@@ -304,6 +307,7 @@ class Instance:
         o.svd_mode = SVD_MODES[svd]
         o.precision = PRECISIONS[prec]
         o.method = METHODS[method]
+        o.p4_mode = 1 if p4 == 'half' else 0
         self.sctm, self.w, self.prec = sctm, w, prec
         self.A_dev = torch.from_numpy(A_host).to(dev)
         st, self.ctx = sctm.sctm_create(self.A_dev, np.ascontiguousarray(O), w['chi'], o)
@@ -407,7 +411,8 @@ def run_ours(args):
     A_host = inputs.perturbed_product_peps(w['D'], w['seed'], eps=w['eps'])
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
-    head = Instance(sctm, w, args.precision, args.svd, stream, dev, A_host, args.method)
+    p4 = args.p4 or ('half' if args.method == 'split-d2' else 'full')
+    head = Instance(sctm, w, args.precision, args.svd, stream, dev, A_host, args.method, p4)
 
     # ---- headline: converged evaluations, inputs resident on the device, profiling off
     for _ in range(args.warmup):
@@ -547,6 +552,7 @@ def run_ours(args):
         'config': {'workload': workload_name(w, args.method), 'D': w['D'], 'chi': w['chi'],
                    'T': w['T'], 'seed': w['seed'], 'eps': w['eps'], 'tol': w['tol'],
                    'precision': args.precision, 'svd': args.svd, 'method': args.method,
+                   'projector4': p4,
                    'accept': '|f - f_oracle| <= %g, f_oracle from tests/golden/%s' % (
                        ACCEPT_DF, os.path.basename(GOLDENS[args.method])),
                    'parallelism': 'replicas',

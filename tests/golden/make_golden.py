@@ -37,21 +37,24 @@ CASES = {
     'cfg4_D5_chi100': (5, 100, 4.52, 3, 0.1, [2, 'converged'], 1e-11, 300),
 }
 
-# the D2-symmetric scheme (Sec. III.B; oracle/split_ctmrg_d2.py) on the D4 group average of the
-# same kind of input: name: (D, chi, T, seed, eps, tol, max_iter); converged record only
+# the D2-symmetric scheme (Sec. III.B; oracle/split_ctmrg_d2.py) with the half projector 4 and
+# the mirrored opposite-boundary projectors (the paper's main-text choices, Appendix) on the D4
+# group average of the same kind of input: name: (D, chi, T, seed, eps, tol, max_iter, p4);
+# converged record only
 CASES_D2 = {
-    'd2_D4_chi64': (4, 64, 4.5, 2, 0.1, 1e-11, 300),
+    'd2_D4_chi64': (4, 64, 4.5, 2, 0.1, 1e-11, 300, 'half'),
 }
 
 
 def run_case_d2(name):
-    D, chi, T, seed, eps, tol, max_iter = CASES_D2[name]
+    D, chi, T, seed, eps, tol, max_iter, p4 = CASES_D2[name]
     A = sd.d4_project(inputs.perturbed_product_peps(D, seed, eps=eps))
     nets = {'num': ising.ising_pepo(1.0 / T), 'den': ising.identity_pepo()}
     out = {'case': name, 'D': D, 'chi': chi, 'T': T, 'seed': seed, 'eps': eps,
            'peps': 'split_ctmrg_d2.d4_project(inputs.perturbed_product_peps(%d, %d, eps=%g))' % (
                D, seed, eps),
-           'method': 'D2-symmetric split-CTMRG', 'cutoff': 1e-12, 'tol': tol, 'records': {},
+           'method': 'D2-symmetric split-CTMRG', 'p4': p4, 'pr': 'mirror', 'cutoff': 1e-12,
+           'tol': tol, 'records': {},
            'written_by': 'tests/golden/make_golden.py (oracle/split_ctmrg_d2.py, FP64 NumPy)',
            'host': platform.machine()}
     t0 = time.time()
@@ -59,7 +62,7 @@ def run_case_d2(name):
     for k, O in nets.items():
         env = sd.sym_init_env(chi, D, O.shape[2])
         trace = []
-        env, it, dS, S = sd.sym_iterate(env, A, O, A, chi, max_iter, tol, 1e-12, trace)
+        env, it, dS, S = sd.sym_iterate(env, A, O, A, chi, max_iter, tol, 1e-12, trace, p4=p4)
         loc = sc.local_contractions(env, A, O, A)
         res[k] = {'lnk': sc.ln_kappa(loc), 'Z11': loc['Z11'], 'E': sc.bra_environment(env, loc),
                   'it': it, 'dS': dS}

@@ -105,9 +105,9 @@ def test_d2_matches_directional_scheme():
 
 
 def test_d2_headline_size_against_stored_oracle_values():
-    """D=4, chi=64 (the benchmark's size), the randomized partial SVD in the FP64 emulation form,
-    converged, against the oracle's stored converged values of the symmetric scheme
-    (tests/golden/d2_D4_chi64.json, written by make_golden.py from oracle/ only)."""
+    """D=4, chi=64 (the benchmark's size), the half projector 4, the randomized partial SVD in the
+    FP64 emulation form, converged, against the oracle's stored converged values of the same
+    scheme (tests/golden/d2_D4_chi64.json, written by make_golden.py from oracle/ only)."""
     path = os.path.join(GOLDEN, 'd2_D4_chi64.json')
     if not os.path.exists(path):
         pytest.skip('stored oracle values not written')
@@ -115,8 +115,9 @@ def test_d2_headline_size_against_stored_oracle_values():
         gold = json.load(fh)
     ref = gold['records']['converged']
     A = inputs.perturbed_product_peps(gold['D'], gold['seed'], eps=gold['eps'])
+    assert gold['p4'] == 'half'
     got = _run(A, gold['chi'], gold['T'], 400, 1e-11, sctm.SCTM_SVD_PARTIAL_RANDOM,
-               sctm.SCTM_PREC_F64EMU)
+               sctm.SCTM_PREC_F64EMU, p4=sctm.SCTM_P4_HALF)
     assert got['st'] == sctm.SCTM_OK, got['it']
     g_ref = np.array(ref['g']).reshape(got['g'].shape)
     print('D2 D=4 chi=64: %d iterations (oracle %s), %.2f s, |df|/|f| = %.1e, |dg|/|g| = %.1e' % (
