@@ -7,11 +7,14 @@
 // kept (the rest lie below 2^-63 of the leading term).  Pairs of one level L = t + u share a
 // tensor-memory accumulator (8 levels x 64 FP32 columns = the whole 512-column tensor memory):
 // a level sum over K blocks of 128 is an integer below 8 * 127^2 * 128 < 2^24, so FP32
-// accumulation in the tensor core is exact.  After each K block the eight level sums are read
-// back (tcgen05.ld), combined exactly in 64-bit integers (levels 0-3 and 4-7 into one integer
-// each, below 2^46) and added into FP64 registers with two FMAs, and the block's MMAs restart
-// the accumulators.  FP64 arithmetic is spent once per operand element (the digit split) and
-// twice per output element per 128 K, not per multiply-add.
+// accumulation in the tensor core is exact.  After each K block the four leading level sums
+// (L = 0..3) are read back (tcgen05.ld), combined exactly into one 64-bit integer (below 2^46)
+// and added to a 64-bit integer accumulator, and their MMAs restart the accumulators.  The four
+// trailing levels (L = 4..7) weigh 2^-28 and less of the leading one: they accumulate in FP32 in
+// the tensor memory over all of K (rounding 2^-24 of their sum, below 2^-52 of the product
+// bound) and are read once at the end.  FP64 arithmetic is spent once per operand element (the
+// digit split) and a few times per output element, none per K block: this GPU's FP64 rate is a
+// small fraction of its integer and FP32 rates.
 //
 // Data movement: the digit split writes, per (row tile, K chunk of 32), the eight digit tiles
 // contiguously in the shared-memory image order (K-major, no swizzle), so one K chunk of the A
@@ -256,9 +259,9 @@ __global__ void __launch_bounds__(ENT, 1) emu_ctr_kernel(const CtrLaunch a, cons
 
     // warp w reads TMEM lanes 32 (w % 4) .. + 31 (tile rows) and columns (w / 4) x 32 .. + 31
     const int quarter = warp & 3, colhalf = warp >> 2;
-    double acc[kColsPerThread];
+    long long acc[kColsPerThread];  // levels 0-3, in units of level 3, exact
 #pragma unroll
-    for (int j = 0; j < kColsPerThread; ++j) acc[j] = 0.0;
+    for (int j = 0; j < kColsPerThread; ++j) acc[j] = 0;
 
     for (int c = 0; c < nch; ++c) {
         const int s = c % kStages;
@@ -276,14 +279,17 @@ __global__ void __launch_bounds__(ENT, 1) emu_ctr_kernel(const CtrLaunch a, cons
                 const uint32_t sb = sa + kChunkA;
                 for (int da = 0; da < kDigits; ++da) {
                     for (int db = 0; db + da < kLevels; ++db) {
-                        const uint32_t ta = tmem + (uint32_t)((da + db) * EBN);
+                        const int L = da + db;
+                        const uint32_t ta = tmem + (uint32_t)(L * EBN);
+                        // a level's first MMA (da == 0, st == 0) of a K block (levels 0-3) or of
+                        // the whole contraction (levels 4-7) starts its accumulator
+                        const bool start = da == 0 && (L < kLevels / 2 ? fresh : c == 0);
 #pragma unroll
                         for (int st = 0; st < EBK / 16; ++st) {
                             const uint32_t step = st * 256;  // 16 BF16 along K = 2 core matrices
                             const uint64_t dA = smem_desc(sa + da * kSliceA + step, LBO, SBO);
                             const uint64_t dB = smem_desc(sb + db * kSliceB + step, LBO, SBO);
-                            // a level's first MMA of the K block (da == 0, st == 0) starts it
-                            mma_bf16(ta, dA, dB, (fresh && da == 0 && st == 0) ? 0u : 1u);
+                            mma_bf16(ta, dA, dB, (start && st == 0) ? 0u : 1u);
                         }
                     }
                 }
@@ -317,42 +323,65 @@ __global__ void __launch_bounds__(ENT, 1) emu_ctr_kernel(const CtrLaunch a, cons
             __syncthreads();
             if (s_fail) break;
             asm volatile("tcgen05.fence::after_thread_sync;");
-            // level sums are exact integers (|S| < 2^24): combine levels 0-3 and 4-7 exactly in
-            // 64-bit integers (S_0 2^21 + S_1 2^14 + S_2 2^7 + S_3, below 2^46), then two FP64
-            // FMAs with weights 2^-35 and 2^-63
+            // the leading level sums are exact integers (|S| < 2^24): S_0 2^21 + S_1 2^14 +
+            // S_2 2^7 + S_3 (below 2^46) is added exactly to the 64-bit accumulator
 #pragma unroll
             for (int cb = 0; cb < kColsPerThread; cb += 8) {
+                uint32_t r[4][8];
 #pragma unroll
-                for (int half = 0; half < 2; ++half) {  // levels 0-3, then 4-7
-                    uint32_t r[4][8];
+                for (int q = 0; q < 4; ++q) {
+                    const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) +
+                                           (uint32_t)(q * EBN + colhalf * kColsPerThread + cb);
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, "
+                        "%7}, [%8];"
+                        : "=r"(r[q][0]), "=r"(r[q][1]), "=r"(r[q][2]), "=r"(r[q][3]),
+                          "=r"(r[q][4]), "=r"(r[q][5]), "=r"(r[q][6]), "=r"(r[q][7])
+                        : "r"(taddr));
+                }
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int L = 4 * half + q;
-                        const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) +
-                                               (uint32_t)(L * EBN + colhalf * kColsPerThread + cb);
-                        asm volatile(
-                            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, "
-                            "%7}, [%8];"
-                            : "=r"(r[q][0]), "=r"(r[q][1]), "=r"(r[q][2]), "=r"(r[q][3]),
-                              "=r"(r[q][4]), "=r"(r[q][5]), "=r"(r[q][6]), "=r"(r[q][7])
-                            : "r"(taddr));
-                    }
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                    const double w = half ? 0x1p-63 : 0x1p-35;
+                for (int j = 0; j < 8; ++j) {
+                    long long v = 0;
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        long long v = 0;
-#pragma unroll
-                        for (int q = 0; q < 4; ++q)
-                            v = v * 128 + (long long)__float2int_rn(__uint_as_float(r[q][j]));
-                        acc[cb + j] = fma((double)v, w, acc[cb + j]);
-                    }
+                    for (int q = 0; q < 4; ++q)
+                        v = v * 128 + (long long)__float2int_rn(__uint_as_float(r[q][j]));
+                    acc[cb + j] += v;
                 }
             }
             // the next block's MMAs overwrite the accumulators only after every warp has read them
             asm volatile("tcgen05.fence::before_thread_sync;");
             __syncthreads();
             asm volatile("tcgen05.fence::after_thread_sync;");
+        }
+    }
+
+    // the trailing levels 4-7 (FP32 sums over all of K, weights 2^-49 .. 2^-70 relative to the
+    // accumulator's unit 2^-35): read once, combined in FP64 with the exact leading part
+    double res[kColsPerThread];
+    if (!s_fail) {
+#pragma unroll
+        for (int cb = 0; cb < kColsPerThread; cb += 8) {
+            uint32_t r[4][8];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) +
+                                       (uint32_t)((4 + q) * EBN + colhalf * kColsPerThread + cb);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, "
+                    "%7}, [%8];"
+                    : "=r"(r[q][0]), "=r"(r[q][1]), "=r"(r[q][2]), "=r"(r[q][3]),
+                      "=r"(r[q][4]), "=r"(r[q][5]), "=r"(r[q][6]), "=r"(r[q][7])
+                    : "r"(taddr));
+            }
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                double lo = (double)__uint_as_float(r[0][j]);
+#pragma unroll
+                for (int q = 1; q < 4; ++q) lo = fma(lo, 128.0, (double)__uint_as_float(r[q][j]));
+                res[cb + j] = fma(lo, 0x1p-63, (double)acc[cb + j] * 0x1p-35);
+            }
         }
     }
 
@@ -370,7 +399,7 @@ __global__ void __launch_bounds__(ENT, 1) emu_ctr_kernel(const CtrLaunch a, cons
                 const int n = n0 + colhalf * kColsPerThread + j;
                 if (n >= a.N) continue;
                 const int ec = ey[(long long)b * a.N + n];
-                const double v = acc[j] * er1 * pow2_lo(ec / 2) * er2 * pow2_lo(ec - ec / 2);
+                const double v = res[j] * er1 * pow2_lo(ec / 2) * er2 * pow2_lo(ec - ec / 2);
                 if (a.splits > 1) {
                     a.partial[((long long)z * a.M + m) * a.N + n] = v;
                 } else {

@@ -50,6 +50,7 @@ def _gemm(X, Y, prec):
     (300, 200, 1000),   # several tiles and K chunks
     (64, 64, 5000),     # one tile: K split across CTAs, FP64 split-K reduction
     (1000, 1000, 64),   # grid of 8 x 16 tiles, short K
+    (130, 70, 20000),   # long K: over a hundred K blocks accumulated in one output
 ])
 @pytest.mark.parametrize('prec', sorted(FORMS))
 def test_gemm_forms(M, N, K, prec):

@@ -30,12 +30,15 @@ def _gpu(A, T, chi, method, svd_mode=sctm.SCTM_SVD_QR, tol=1e-11, max_it=400):
 @pytest.mark.parametrize('D,chi,T,seed,eps', [(2, 16, 4.6, 7, 0.3), (3, 18, 4.5, 4, 0.1)])
 @pytest.mark.parametrize('svd_mode', [sctm.SCTM_SVD_QR, sctm.SCTM_SVD_PARTIAL_RANDOM])
 def test_reduced_matches_oracle(D, chi, T, seed, eps, svd_mode):
-    """Converged f and g of the reduced method (Sec. II, Fig. 3) against the oracle's, both
-    iterated to the same ||dS|| < 1e-12: the spectrum of Sec. III.D is insensitive to a slowly
-    decaying environment mode that g still sees, so stopping one side earlier leaves a gradient
-    gap of order 1e-8."""
+    """Converged f and g of the reduced method (Sec. II, Fig. 3) against the oracle's (iterated
+    to ||dS|| < 1e-12).  The spectrum of Sec. III.D is insensitive to a slowly decaying
+    environment mode that g still sees, so stopping one side earlier leaves a gradient gap of
+    order 1e-8: the GPU iterates to the same 1e-12 with the full SVD; the partial SVD's spectrum
+    has a floor near 1e-12 (measured: 2000 iterations did not reach it at D=2, chi=16), so that
+    form stops at 1e-11 (gaps measured 5e-10 and 5e-9)."""
     A = inputs.perturbed_product_peps(D, seed, eps=eps)
-    f, g, st, it = _gpu(A, T, chi, sctm.SCTM_METHOD_REDUCED, svd_mode, tol=1e-12, max_it=2000)
+    tol = 1e-12 if svd_mode == sctm.SCTM_SVD_QR else 1e-11
+    f, g, st, it = _gpu(A, T, chi, sctm.SCTM_METHOD_REDUCED, svd_mode, tol=tol, max_it=2000)
     assert st == sctm.SCTM_OK, (st, it)
     ref = reduced_ctmrg.evaluate(A, ising.ising_pepo(1 / T), ising.identity_pepo(), T, chi, 400,
                                  1e-12)
