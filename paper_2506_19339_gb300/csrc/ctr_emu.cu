@@ -76,6 +76,17 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
     return false;
 }
 
+// The integer value of an FP32 number that holds an exact integer of magnitude below 2^24 (a
+// level sum), decoded from its IEEE-754 fields with integer operations only: on this GPU the
+// float-to-integer conversion instruction shares the slow FP64 pipe, and the level read-back
+// converts 128 values per thread per K block.
+__device__ __forceinline__ int level_to_int(float f) {
+    const unsigned u = __float_as_uint(f);
+    const int e = (int)((u >> 23) & 0xFFu);  // biased exponent: 0 for zero, 127..150 otherwise
+    const int mag = e == 0 ? 0 : (int)((0x800000u | (u & 0x7FFFFFu)) >> (150 - e));
+    return (u >> 31) ? -mag : mag;
+}
+
 // 2^e as a double for a frexp exponent of a finite double (e in [-1073, 1024]): built from its
 // bits in one or two normal factors, so that a product by it is the exact scaling ldexp would do
 // (up to the rounding of a subnormal result)
@@ -345,7 +356,7 @@ __global__ void __launch_bounds__(ENT, 1) emu_ctr_kernel(const CtrLaunch a, cons
                     long long v = 0;
 #pragma unroll
                     for (int q = 0; q < 4; ++q)
-                        v = v * 128 + (long long)__float2int_rn(__uint_as_float(r[q][j]));
+                        v = v * 128 + (long long)level_to_int(__uint_as_float(r[q][j]));
                     acc[cb + j] += v;
                 }
             }
@@ -377,10 +388,12 @@ __global__ void __launch_bounds__(ENT, 1) emu_ctr_kernel(const CtrLaunch a, cons
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-                double lo = (double)__uint_as_float(r[0][j]);
+                // S_4 2^21 + S_5 2^14 + S_6 2^7 + S_7 in FP32: its relative rounding (3 x 2^-24)
+                // is below 2^-50 of the product bound, since this part weighs 2^-28 of it
+                float lo = __uint_as_float(r[0][j]);
 #pragma unroll
-                for (int q = 1; q < 4; ++q) lo = fma(lo, 128.0, (double)__uint_as_float(r[q][j]));
-                res[cb + j] = fma(lo, 0x1p-63, (double)acc[cb + j] * 0x1p-35);
+                for (int q = 1; q < 4; ++q) lo = fmaf(lo, 128.0f, __uint_as_float(r[q][j]));
+                res[cb + j] = fma((double)lo, 0x1p-63, (double)acc[cb + j] * 0x1p-35);
             }
         }
     }
@@ -398,8 +411,11 @@ __global__ void __launch_bounds__(ENT, 1) emu_ctr_kernel(const CtrLaunch a, cons
             for (int j = 0; j < kColsPerThread; ++j) {
                 const int n = n0 + colhalf * kColsPerThread + j;
                 if (n >= a.N) continue;
-                const int ec = ey[(long long)b * a.N + n];
-                const double v = res[j] * er1 * pow2_lo(ec / 2) * er2 * pow2_lo(ec - ec / 2);
+                const int ec = ey[(long long)b * a.N + n], et = erow + ec;
+                // one multiplication by 2^(erow + ec) when that is a normal power of two
+                const double v = (et >= -1022 && et <= 1023)
+                                     ? res[j] * pow2_lo(et)
+                                     : res[j] * er1 * pow2_lo(ec / 2) * er2 * pow2_lo(ec - ec / 2);
                 if (a.splits > 1) {
                     a.partial[((long long)z * a.M + m) * a.N + n] = v;
                 } else {

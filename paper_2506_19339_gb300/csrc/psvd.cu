@@ -160,8 +160,16 @@ __device__ float jacobi_sweep(F* A, F* V, int kp, int ld, F tol, RoundScratch rs
 }  // namespace
 
 // G (k x k, column-major G[i + j k]) -> T (k x k, column-major, upper triangular) with Y T
-// orthonormal (up to the shift) for the Y that gave G = Y^T Y.  Shared memory: 2 k^2 + 2 k
-// doubles.
+// orthonormal (up to the shift) for the Y that gave G = Y^T Y.  Shared memory: chol_orth_smem(k).
+//
+// This SM retires two FP64 lane-operations per cycle, so the kernel is organised around few
+// FP64 instructions and few block barriers: a blocked right-looking Cholesky (warp 0 factors a
+// block of kCholNB rows -- pivots, the block's own rows, its scaled pivot rows -- under warp
+// synchronisation only; then every warp applies the block's kCholNB rank-one terms to the
+// trailing rows at once: two barriers per block instead of two per row), the factor's rows
+// scaled once, and the inverse factor by column back substitution with a warp per column.
+constexpr int kCholNB = 16;
+
 __global__ void __launch_bounds__(kPsvdThreads)
     chol_orth_kernel(const double* __restrict__ G, int k, double shift, double* __restrict__ T,
                      double* Xg) {
@@ -169,8 +177,10 @@ __global__ void __launch_bounds__(kPsvdThreads)
     double* R = sm;                        // row-major k x k: scaled Gram, then the factor rows
     double* X = Xg ? Xg : sm + k * k;      // row-major k x k: F^-1 (global above kPsvdSmemK)
     double* d = sm + (Xg ? 1 : 2) * k * k; // reciprocal column norms
-    double* rinv = d + k;        // reciprocal pivots
-    const int tid = threadIdx.x, nt = blockDim.x;
+    double* rinv = d + k;                  // reciprocal pivots
+    double* P = X;                         // kCholNB x k scaled pivot rows (X is free until then)
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5,
+              nw = nt >> 5;
     for (int i = tid; i < k; i += nt) {  // d = 1 / column norm (0 for a zero column)
         const double g = G[i + (long long)i * k];
         d[i] = g > 0.0 ? 1.0 / sqrt(g) : 0.0;
@@ -183,19 +193,63 @@ __global__ void __launch_bounds__(kPsvdThreads)
         R[e] = G[e] * d[i] * d[j] + ((i == j && d[i] > 0.0) ? shift : 0.0);
     }
     __syncthreads();
-    block_cholesky(R, rinv, k);
-    // X = F^-1 by back substitution, one column per thread.  With F[r][l] = R[r][l] rinv[r] and
-    // F[r][r] = 1 / rinv[r]:  x_r = rinv[r] (delta_rc - rinv[r] sum_{l > r} R[r][l] x_l)
-    for (int c = tid; c < k; c += nt) {
-        for (int r = k - 1; r >= 0; --r) {
-            double x = 0.0;
-            const double ri = rinv[r];
-            if (r <= c && ri > 0.0) {
-                double acc = 0.0;
-                for (int l = r + 1; l <= c; ++l) acc = fma(R[r * k + l], X[l * k + c], acc);
-                x = ri * ((r == c ? 1.0 : 0.0) - ri * acc);
+    // Cholesky R = F^T F of the upper triangle, rows left unscaled: F[j][c] = R[j][c] rinv[j]
+    // (c >= j).  A pivot at or below kPivotFloor gives rinv = 0 (a zero row).
+    for (int j0 = 0; j0 < k; j0 += kCholNB) {
+        const int j1 = min(j0 + kCholNB, k);
+        if (warp == 0) {
+            for (int j = j0; j < j1; ++j) {
+                double ri = 0.0;
+                if (lane == 0) {
+                    const double piv = R[j * k + j];
+                    ri = piv > kPivotFloor ? 1.0 / sqrt(piv) : 0.0;
+                    rinv[j] = ri;
+                }
+                ri = __shfl_sync(0xffffffffu, ri, 0);
+                const double r2 = ri * ri;
+                for (int a = j + 1; a < j1; ++a) {  // the block's own later rows, all columns
+                    const double fa = R[j * k + a] * r2;
+                    for (int b = a + lane; b < k; b += 32) R[a * k + b] -= fa * R[j * k + b];
+                }
+                for (int b = j1 + lane; b < k; b += 32) P[(j - j0) * k + b] = R[j * k + b] * r2;
+                __syncwarp();
             }
-            X[r * k + c] = x;
+        }
+        __syncthreads();
+        // trailing rows a >= j1: R[a][b] -= sum_j P[j][a] R[j][b], the same terms in the same
+        // order as one rank-one update per pivot
+        const int nb = j1 - j0;
+        for (int a = j1 + warp; a < k; a += nw) {
+            double pa[kCholNB];
+#pragma unroll
+            for (int q = 0; q < kCholNB; ++q) pa[q] = q < nb ? P[q * k + a] : 0.0;
+            for (int b = a + lane; b < k; b += 32) {
+                double acc = R[a * k + b];
+#pragma unroll
+                for (int q = 0; q < kCholNB; ++q)
+                    if (q < nb) acc -= pa[q] * R[(j0 + q) * k + b];
+                R[a * k + b] = acc;
+            }
+        }
+        __syncthreads();
+    }
+    // F's off-diagonal part in place: R[r][l] <- R[r][l] rinv[r] (l > r)
+    for (int e = tid; e < k * k; e += nt) {
+        const int r = e / k, l = e % k;
+        if (l > r) R[e] *= rinv[r];
+    }
+    __syncthreads();
+    // X = F^-1, column c by back substitution (F[l][l] = 1 / rinv[l]): x = e_c, then for l = c
+    // down to 0: x_l <- x_l rinv[l] and x_r -= F[r][l] x_l for r < l.  A warp per column.
+    for (int c = warp; c < k; c += nw) {
+        for (int r = lane; r < k; r += 32) X[r * k + c] = r == c ? 1.0 : 0.0;
+        __syncwarp();
+        for (int l = c; l >= 0; --l) {
+            const double xl = X[l * k + c] * rinv[l];
+            __syncwarp();
+            if (lane == 0) X[l * k + c] = xl;
+            for (int r = lane; r < l; r += 32) X[r * k + c] -= R[r * k + l] * xl;
+            __syncwarp();
         }
     }
     __syncthreads();

@@ -39,10 +39,12 @@ CASES = {
 
 # the D2-symmetric scheme (Sec. III.B; oracle/split_ctmrg_d2.py) with the half projector 4 and
 # the mirrored opposite-boundary projectors (the paper's main-text choices, Appendix) on the D4
-# group average of the same kind of input: name: (D, chi, T, seed, eps, tol, max_iter, p4);
-# converged record only
+# group average of the same kind of input: name: (D, chi, T, seed, eps, tol, max_iter, p4).
+# tol None: exactly max_iter iterations, well past convergence (the norm network at D=4, chi=64
+# converges after an unstable excursion near iteration 58, so two runs stop at slightly
+# different iterations; a fixed count past convergence compares the fixed point itself)
 CASES_D2 = {
-    'd2_D4_chi64': (4, 64, 4.5, 2, 0.1, 1e-11, 300, 'half'),
+    'd2_D4_chi64': (4, 64, 4.5, 2, 0.1, None, 200, 'half'),
 }
 
 
@@ -71,7 +73,7 @@ def run_case_d2(name):
     f = -T * (res['num']['lnk'] - res['den']['lnk'])
     g = sd.d4_project(-2.0 * T * (res['num']['E'] / res['num']['Z11'] -
                                   res['den']['E'] / res['den']['Z11']))
-    out['records']['converged'] = {
+    out['records']['converged' if tol is not None else 'fixed'] = {
         'f': f, 'g': [float(x) for x in g.ravel()],
         'iterations': {k: res[k]['it'] for k in nets},
         'dS': {k: float(res[k]['dS']) for k in nets},

@@ -106,19 +106,21 @@ def test_d2_matches_directional_scheme():
 
 def test_d2_headline_size_against_stored_oracle_values():
     """D=4, chi=64 (the benchmark's size), the half projector 4, the randomized partial SVD in the
-    FP64 emulation form, converged, against the oracle's stored converged values of the same
-    scheme (tests/golden/d2_D4_chi64.json, written by make_golden.py from oracle/ only)."""
+    FP64 emulation form, 200 iterations (both networks converge before 130), against the
+    oracle's stored values of the same scheme after the same count
+    (tests/golden/d2_D4_chi64.json, written by make_golden.py from oracle/ only)."""
     path = os.path.join(GOLDEN, 'd2_D4_chi64.json')
     if not os.path.exists(path):
         pytest.skip('stored oracle values not written')
     with open(path) as fh:
         gold = json.load(fh)
-    ref = gold['records']['converged']
+    ref = gold['records']['fixed']
+    n = ref['iterations']['num']
     A = inputs.perturbed_product_peps(gold['D'], gold['seed'], eps=gold['eps'])
     assert gold['p4'] == 'half'
-    got = _run(A, gold['chi'], gold['T'], 400, 1e-11, sctm.SCTM_SVD_PARTIAL_RANDOM,
+    got = _run(A, gold['chi'], gold['T'], n, 0.0, sctm.SCTM_SVD_PARTIAL_RANDOM,
                sctm.SCTM_PREC_F64EMU, p4=sctm.SCTM_P4_HALF)
-    assert got['st'] == sctm.SCTM_OK, got['it']
+    assert got['it'] == n and got['dS'] < 1e-10, got['dS']
     g_ref = np.array(ref['g']).reshape(got['g'].shape)
     print('D2 D=4 chi=64: %d iterations (oracle %s), %.2f s, |df|/|f| = %.1e, |dg|/|g| = %.1e' % (
         got['it'], ref['iterations'], got['s'], abs(got['f'] - ref['f']) / abs(ref['f']),

