@@ -145,18 +145,25 @@ __global__ void __launch_bounds__(256) emu_rowexp_kernel(const CtrLaunch a, int*
         const long long q = isY ? w - rx : w;
         const int R = isY ? a.N : a.M;
         const int b = (int)(q / R), r = (int)(q - (long long)b * R);
-        double m = 0.0;
+        // max |x| as the largest bit pattern of |x| (non-negative doubles order as integers):
+        // integer operations only, the FP64 pipe of this GPU being slow
+        unsigned long long m = 0;
         if (isY) {
             const long long base = (a.yb ? a.yb[b] : 0) + a.yn[r];
-            for (int k = lane; k < a.K; k += 32) m = fmax(m, fabs(a.Y[base + a.yk[k]]));
+            for (int k = lane; k < a.K; k += 32)
+                m = max(m, (unsigned long long)__double_as_longlong(a.Y[base + a.yk[k]]) &
+                               0x7FFFFFFFFFFFFFFFull);
         } else {
             const long long base = (a.xb ? a.xb[b] : 0) + a.xm[r];
-            for (int k = lane; k < a.K; k += 32) m = fmax(m, fabs(a.X[base + a.xk[k]]));
+            for (int k = lane; k < a.K; k += 32)
+                m = max(m, (unsigned long long)__double_as_longlong(a.X[base + a.xk[k]]) &
+                               0x7FFFFFFFFFFFFFFFull);
         }
-        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
         if (lane == 0) {
             int e = 0;
-            if (m > 0.0 && isfinite(m)) frexp(m, &e);
+            const double md = __longlong_as_double((long long)m);
+            if (md > 0.0 && isfinite(md)) frexp(md, &e);
             (isY ? ey : ex)[q] = e;
         }
     }
@@ -198,15 +205,28 @@ __global__ void __launch_bounds__(256) emu_pack_kernel(const CtrLaunch a, const 
                     er = ex[(long long)b * a.M + row];
                 }
             }
-            // |v| < 2^er, so |N| < 2^56 and the truncation is exact to 2^-56 of the row maximum
-            const long long N = __double2ll_rz(ldexp(v, 56 - er));
-            const unsigned long long mag = (unsigned long long)(N < 0 ? -N : N);
-            const float sgn = N < 0 ? -1.0f : 1.0f;
+            // |v| < 2^er, so N = trunc(|v| 2^(56 - er)) < 2^56 (exact to 2^-56 of the row
+            // maximum), taken from the IEEE-754 fields of v: |v| = mant 2^(E' - 1075)
+            const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+            const unsigned neg = (unsigned)(bits >> 63);
+            const int E = (int)((bits >> 52) & 0x7FFull);
+            const unsigned long long mant =
+                (bits & 0xFFFFFFFFFFFFFull) | (E ? 0x10000000000000ull : 0ull);
+            const int sh = (E ? E : 1) - 1075 + 56 - er;
+            const unsigned long long mag =
+                sh >= 0 ? (mant << sh) : (sh > -64 ? (mant >> (-sh)) : 0ull);
 #pragma unroll
             for (int d = 0; d < kDigits; ++d) {
-                const int chunk = (int)((mag >> (7 * (kDigits - 1 - d))) & 127ull);
-                const __nv_bfloat16 h = __float2bfloat16_rn(sgn * (float)chunk);  // exact
-                dst[d * slice + e] = *reinterpret_cast<const unsigned short*>(&h);
+                // the 7-bit digit as a BF16 bit pattern (exact): sign, exponent 127 + p with
+                // p = floor(log2 digit), the digit's bits below its leading one as mantissa
+                const unsigned chunk = (unsigned)((mag >> (7 * (kDigits - 1 - d))) & 127ull);
+                unsigned short h = 0;
+                if (chunk) {
+                    const int p = 31 - __clz(chunk);
+                    h = (unsigned short)((neg << 15) | ((127u + p) << 7) |
+                                         ((chunk << (7 - p)) & 0x7Fu));
+                }
+                dst[d * slice + e] = h;
             }
         }
     }

@@ -75,8 +75,8 @@ __device__ void block_cholesky(double* R, double* rinv, int k) {
 
 // Scratch of one Jacobi round, one entry per column pair.
 struct RoundScratch {
-    double* c;   // cosine of each pair's rotation
-    double* s;   // sine
+    double* c;   // cosine of each pair's rotation (as the sweep's type)
+    double* s;   // sine (as the sweep's type)
     int* act;    // 1 if the pair rotates
     int* pi;     // the pair's columns i, j (this round)
     int* pj;
@@ -122,8 +122,10 @@ __device__ float jacobi_sweep(F* A, F* V, int kp, int ld, F tol, RoundScratch rs
                     act = 1;
                 }
             }
-            rs.c[q] = (double)c;
-            rs.s[q] = (double)sn;
+            // stored in the sweep's own type (np doubles of room hold np values of either):
+            // a float <-> double conversion runs on the FP64 pipe of this GPU
+            reinterpret_cast<F*>(rs.c)[q] = c;
+            reinterpret_cast<F*>(rs.s)[q] = sn;
             rs.act[q] = act;
             rs.pi[q] = i;
             rs.pj[q] = j;
@@ -132,7 +134,7 @@ __device__ float jacobi_sweep(F* A, F* V, int kp, int ld, F tol, RoundScratch rs
         // rotations: warp per pair, lane per row (no integer division in the inner loop)
         for (int q = tid >> 5; q < np; q += nt >> 5) {
             if (!rs.act[q]) continue;
-            const F c = (F)rs.c[q], sn = (F)rs.s[q];
+            const F c = reinterpret_cast<const F*>(rs.c)[q], sn = reinterpret_cast<const F*>(rs.s)[q];
             F* ai = A + (long long)rs.pi[q] * ld;
             F* aj = A + (long long)rs.pj[q] * ld;
             F* vi = V + (long long)rs.pi[q] * ld;
