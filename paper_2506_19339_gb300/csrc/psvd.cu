@@ -235,29 +235,34 @@ __global__ void __launch_bounds__(kPsvdThreads)
         }
         __syncthreads();
     }
-    // F's off-diagonal part in place: R[r][l] <- R[r][l] rinv[r] (l > r)
+    // F's off-diagonal part, transposed into R's unused lower triangle: R[l][r] = F[r][l] =
+    // R[r][l] rinv[r] (r < l), so that the columns of F the back substitution walks are rows
     for (int e = tid; e < k * k; e += nt) {
-        const int r = e / k, l = e % k;
-        if (l > r) R[e] *= rinv[r];
+        const int l = e / k, r = e % k;
+        if (r < l) R[e] = R[r * k + l] * rinv[r];
     }
     __syncthreads();
-    // X = F^-1, column c by back substitution (F[l][l] = 1 / rinv[l]): x = e_c, then for l = c
-    // down to 0: x_l <- x_l rinv[l] and x_r -= F[r][l] x_l for r < l.  A warp per column.
+    // X = F^-1, stored by columns (X[c k + r] = (F^-1)[r][c]), column c by back substitution
+    // (F[l][l] = 1 / rinv[l]): x = e_c, then for l = c down to 0: x_l <- x_l rinv[l] and
+    // x_r -= F[r][l] x_l for r < l.  A warp per column; its lanes walk r, so both the column of
+    // X and the column of F they touch are consecutive in shared memory.
     for (int c = warp; c < k; c += nw) {
-        for (int r = lane; r < k; r += 32) X[r * k + c] = r == c ? 1.0 : 0.0;
+        double* x = X + (long long)c * k;
+        for (int r = lane; r < k; r += 32) x[r] = r == c ? 1.0 : 0.0;
         __syncwarp();
         for (int l = c; l >= 0; --l) {
-            const double xl = X[l * k + c] * rinv[l];
+            const double xl = x[l] * rinv[l];
             __syncwarp();
-            if (lane == 0) X[l * k + c] = xl;
-            for (int r = lane; r < l; r += 32) X[r * k + c] -= R[r * k + l] * xl;
+            if (lane == 0) x[l] = xl;
+            const double* fl = R + (long long)l * k;  // F[r][l] for r < l
+            for (int r = lane; r < l; r += 32) x[r] -= fl[r] * xl;
             __syncwarp();
         }
     }
     __syncthreads();
     for (int e = tid; e < k * k; e += nt) {  // T = D^-1 F^-1, column-major
         const int i = e % k, j = e / k;
-        T[e] = j >= i ? X[i * k + j] * d[i] : 0.0;
+        T[e] = j >= i ? X[e] * d[i] : 0.0;
     }
 }
 
@@ -317,8 +322,23 @@ __global__ void __launch_bounds__(kPsvdThreads)
     }
     __syncthreads();
     const float tol32 = 4.0f * (float)kp * 5.9604645e-8f;
+    bool w_is_identity = false;  // the first FP32 sweep found every pair orthogonal: W = I
     for (int sw = 0; sw < kJacobiMaxSweeps32; ++sw)
-        if (jacobi_sweep<float>(A32, V32, kp, ld, tol32, rs, &s_max) <= tol32) break;
+        if (jacobi_sweep<float>(A32, V32, kp, ld, tol32, rs, &s_max) <= tol32) {
+            w_is_identity = sw == 0;  // no rotation was made (uniform: s_max is shared)
+            break;
+        }
+    if (w_is_identity) {
+        // a warm solve whose B already has orthogonal columns to FP32 accuracy: W = I and
+        // A = B 2^-ex exactly, which steps 2 and 3 below would also produce
+        __syncthreads();
+        for (int e = tid; e < kp * kp; e += nt) {
+            const int r = e % kp, c = e / kp;
+            V[c * ld + r] = r == c ? 1.0 : 0.0;
+            A[c * ld + r] = (r < k && c < k) ? ldexp(B[r + (long long)c * k], -ex) : 0.0;
+        }
+        __syncthreads();
+    } else {
     // 2. W = V32 in FP64, re-orthonormalised: W <- W F^-1 with F^T F = W^T W
     for (int e = tid; e < kp * kp; e += nt) {
         const int r = e % kp, c = e / kp;
@@ -352,15 +372,17 @@ __global__ void __launch_bounds__(kPsvdThreads)
         A[c * ld + r] = ldexp(v, -ex);
     }
     __syncthreads();
+    }
     // 4. FP64 sweeps; tol64 = kp eps is the rounding level of a kp-term dot product.  Jacobi
     //    converges quadratically, so a sweep whose largest relative off-diagonal value was below
-    //    1e-7 leaves them near 1e-14: it is the last
+    //    1e-6 leaves them near 1e-12: it is the last (one FP64 sweep costs about 1.5 ms of the
+    //    SM's FP64 pipe at k = 80, most of a warm solve)
     const double tol64 = (double)kp * 2.220446049250313e-16;
     {
         int sw = 0;
         for (; sw < kJacobiMaxSweeps64; ++sw) {
             const float mx = jacobi_sweep<double>(A, V, kp, ld, tol64, rs, &s_max);
-            if (mx <= tol64 || mx < 1e-7f) break;
+            if (mx <= tol64 || mx < 1e-6f) break;
         }
         if (sw >= kJacobiMaxSweeps64) bad = 1;
     }
