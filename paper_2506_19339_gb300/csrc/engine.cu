@@ -175,31 +175,89 @@ struct ParallelStep : Step {
             }
             return;
         }
-        std::vector<std::exception_ptr> errs(sub.size());
-        std::vector<std::thread> th;
-        for (size_t i = 1; i < sub.size(); ++i)
-            th.emplace_back([&, i, lane] {
-                Engine::cur_lane = lane;
-                try {
-                    e.run_sub(sub[i]);
-                } catch (...) {
-                    errs[i] = std::current_exception();
-                }
-            });
+        std::exception_ptr err;
         try {
-            if (!sub.empty()) e.run_sub(sub[0]);
+            // the lane's persistent workers issue the sub-plans (each on its own stream)
+            e.pools[lane]->run((int)sub.size(), [&](int i) {
+                Engine::cur_lane = lane;
+                e.run_sub(sub[i]);
+            });
         } catch (...) {
-            errs[0] = std::current_exception();
+            err = std::current_exception();
         }
-        for (auto& t : th) t.join();
         for (size_t i = 0; i < sub.size(); ++i) {
             cudaEventRecord(join_ev[i], L.streams[i + 1]);
             cudaStreamWaitEvent(e.strm(0), join_ev[i], 0);
         }
-        for (auto& x : errs)
-            if (x) std::rethrow_exception(x);
+        if (err) std::rethrow_exception(err);
     }
 };
+
+// ---------------------------------------------------------------------------------------------
+// host worker pool
+// ---------------------------------------------------------------------------------------------
+WorkerPool::WorkerPool(int workers) {
+    for (int w = 1; w <= workers; ++w) threads_.emplace_back([this, w] { loop(w); });
+}
+
+WorkerPool::~WorkerPool() {
+    {
+        std::lock_guard<std::mutex> g(m_);
+        stop_ = true;
+    }
+    start_cv_.notify_all();
+    for (auto& t : threads_) t.join();
+}
+
+void WorkerPool::loop(int w) {
+    long long seen = 0;
+    for (;;) {
+        const std::function<void(int)>* job;
+        {
+            std::unique_lock<std::mutex> g(m_);
+            start_cv_.wait(g, [&] { return stop_ || generation_ != seen; });
+            if (stop_) return;
+            seen = generation_;
+            if (w >= njob_) continue;
+            job = job_;
+        }
+        std::exception_ptr err;
+        try {
+            (*job)(w);
+        } catch (...) {
+            err = std::current_exception();
+        }
+        std::lock_guard<std::mutex> g(m_);
+        if (err && !errors_[w]) errors_[w] = err;
+        if (--pending_ == 0) done_cv_.notify_all();
+    }
+}
+
+void WorkerPool::run(int n, const std::function<void(int)>& fn) {
+    if (n <= 0) return;
+    if (n - 1 > (int)threads_.size()) throw Error(SCTM_EINVAL, "worker pool too small");
+    {
+        std::lock_guard<std::mutex> g(m_);
+        job_ = &fn;
+        njob_ = n;
+        pending_ = n - 1;
+        errors_.assign(n, nullptr);
+        ++generation_;
+    }
+    start_cv_.notify_all();
+    std::exception_ptr err0;
+    try {
+        fn(0);
+    } catch (...) {
+        err0 = std::current_exception();
+    }
+    std::unique_lock<std::mutex> g(m_);
+    done_cv_.wait(g, [&] { return pending_ == 0; });
+    job_ = nullptr;
+    if (err0) std::rethrow_exception(err0);
+    for (auto& x : errors_)
+        if (x) std::rethrow_exception(x);
+}
 
 // ---------------------------------------------------------------------------------------------
 // engine
@@ -224,6 +282,7 @@ Engine::Engine(cudaStream_t s, int prec, double cut) : stream(s), precision(prec
         }
     }
     SOLVER_OK(cusolverDnCreateParams(&solver_params));
+    for (int l = 0; l < kLanes; ++l) pools[l].reset(new WorkerPool(kStreams - 1));
     for (int l = 0; l < kLanes; ++l)
         CUDA_OK(cudaStreamCreateWithFlags(&cap_stream[l], cudaStreamNonBlocking));
     const char* pf = getenv("SCTM_PROFILE");

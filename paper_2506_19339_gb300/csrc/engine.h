@@ -2,7 +2,10 @@
 #pragma once
 
 #include <atomic>
+#include <condition_variable>
+#include <exception>
 #include <functional>
+#include <mutex>
 #include <memory>
 #include <thread>
 #include <unordered_map>
@@ -37,6 +40,29 @@ Ten view(double* p, const std::vector<int>& dims);                 // contiguous
 Ten permute(const Ten& t, const std::vector<int>& perm);           // out axis k = t axis perm[k]
 
 class Engine;
+
+// Persistent host threads for the independent sub-plans of a parallel step: run(n, fn) calls
+// fn(i) for i = 1 .. n-1 on the workers and fn(0) on the caller, waits for all of them and
+// rethrows the first exception.  One pool per lane (the two networks' lanes run at once).
+class WorkerPool {
+public:
+    explicit WorkerPool(int workers);
+    ~WorkerPool();
+    WorkerPool(const WorkerPool&) = delete;
+    WorkerPool& operator=(const WorkerPool&) = delete;
+    void run(int n, const std::function<void(int)>& fn);
+
+private:
+    void loop(int w);
+    std::vector<std::thread> threads_;
+    std::mutex m_;
+    std::condition_variable start_cv_, done_cv_;
+    const std::function<void(int)>* job_ = nullptr;
+    int njob_ = 0, pending_ = 0;
+    long long generation_ = 0;
+    bool stop_ = false;
+    std::vector<std::exception_ptr> errors_;
+};
 
 // One operation of a plan as the reverse mode sees it, recorded while the plan is built (the
 // tape): a contraction, a projector pair (Eqs. "projector construction" / "projector
@@ -146,6 +172,7 @@ public:
     };
     static constexpr int kLanes = 2;
     Lane lanes[kLanes];
+    std::unique_ptr<WorkerPool> pools[kLanes];  // host workers of each lane's parallel steps
     static thread_local int cur_lane;
     Lane& lane() { return lanes[cur_lane]; }
     // Serialised execution (profiling): every step of every plan on the lane's stream 0, the
