@@ -127,14 +127,24 @@ __device__ float jacobi_sweep(F* A, F* V, int kp, int ld, F tol, RoundScratch rs
             int act = 0;
             F c = 1, sn = 0;
             if (al > F(0) && be > F(0)) {
+                // FP32 holds the norms unless a column is tiny (below 1e-30 in squared norm: a
+                // padding or rank-deficient column); those pairs take the type F throughout
+                const bool in_range = al > F(1e-30) && be > F(1e-30);
                 const float g32 = (float)ga;
-                const float rel = fabsf(g32) / (sqrtf((float)al) * sqrtf((float)be));
+                const float rel = in_range ? fabsf(g32) / (sqrtf((float)al) * sqrtf((float)be))
+                                           : (float)(fabs(ga) / (sqrt(al) * sqrt(be)));
                 wmax = fmaxf(wmax, rel);
                 if (rel > tolf) {
-                    const float z = (float)(be - al) / (2.0f * g32);
-                    float t32 = (z >= 0.0f ? 1.0f : -1.0f) / (fabsf(z) + sqrtf(1.0f + z * z));
-                    if (fabsf(z) > 1e18f) t32 = 0.5f / z;  // 1 + z^2 would overflow
-                    const F t = (F)t32;
+                    F t;
+                    if (in_range) {
+                        const float z = (float)(be - al) / (2.0f * g32);
+                        float t32 = (z >= 0.0f ? 1.0f : -1.0f) / (fabsf(z) + sqrtf(1.0f + z * z));
+                        if (fabsf(z) > 1e18f) t32 = 0.5f / z;  // 1 + z^2 would overflow
+                        t = (F)t32;
+                    } else {
+                        const F zeta = (be - al) / (F(2) * ga);
+                        t = (zeta >= F(0) ? F(1) : F(-1)) / (fabs(zeta) + sqrt(F(1) + zeta * zeta));
+                    }
                     c = F(1) / sqrt(F(1) + t * t);
                     sn = c * t;
                     nrm[i] = c * c * (al - F(2) * t * ga + t * t * be);
@@ -192,7 +202,7 @@ __device__ float jacobi_sweep(F* A, F* V, int kp, int ld, F tol, RoundScratch rs
 // scaled once, and the inverse factor by column back substitution with a warp per column.
 constexpr int kCholNB = 16;
 
-__global__ void __launch_bounds__(kPsvdThreads)
+__global__ void __launch_bounds__(kPsvdThreads, 1)
     chol_orth_kernel(const double* __restrict__ G, int k, double shift, double* __restrict__ T,
                      double* Xg) {
     extern __shared__ double sm[];
@@ -292,7 +302,7 @@ __global__ void __launch_bounds__(kPsvdThreads)
 // zero column that is never rotated); columns are stored with the odd leading dimension
 // ld = kp + 1 so that the threads of the dot-product phase, which read different columns, hit
 // different shared-memory banks.  Shared memory: jacobi_svd_smem(k).
-__global__ void __launch_bounds__(kPsvdThreads)
+__global__ void __launch_bounds__(kPsvdThreads, 1)
     jacobi_svd_kernel(const double* __restrict__ B, int k, double* __restrict__ S,
                       double* __restrict__ U, double* __restrict__ W, int* info, double* Vg) {
     extern __shared__ double sm[];
