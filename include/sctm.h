@@ -158,7 +158,8 @@ typedef struct {
 } sctm_opts;
 
 /* Fill *o with the defaults: T=1, D=2, p=2, d=2, FP64, env gradient, cutoff 1e-12, seed 0,
- * batch 1, default stream, QR SVD.  Returns SCTM_EINVAL for NULL. */
+ * batch 1, default stream, QR SVD, the directional split method, full projector 4.  Returns
+ * SCTM_EINVAL for NULL. */
 sctm_status sctm_default_opts(sctm_opts* o);
 
 /* sctm_create -- the problem statement of Sec. II: a PEPS tensor A, a PEPO tensor O and the
