@@ -362,24 +362,31 @@ def form_summary(sctm, ms, fs, its, sts, ref_f, ref_g, g_last):
                              all(s == sctm.SCTM_OK for s in sts))}
 
 
-def dgemm_tflops(dev):
-    """FP64 matrix-multiply rate of this GPU (cuBLAS through torch), the FP64 roofline peak."""
+def dgemm_tflops(dev, dtype=None):
+    """Matrix-multiply rate of this GPU (cuBLAS through torch, 8192^3, best of 3): FP64 by default,
+    the FP64 roofline peak; dtype=float32 with TF32 allowed gives the TF32 tensor-core rate."""
     import torch
     n = 8192
-    a = torch.randn(n, n, dtype=torch.float64, device=dev)
-    b = torch.randn(n, n, dtype=torch.float64, device=dev)
-    torch.matmul(a, b)
-    torch.cuda.synchronize(dev)
-    best = 1e30
-    for _ in range(3):
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
+    dtype = dtype or torch.float64
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = dtype == torch.float32
+    try:
+        a = torch.randn(n, n, dtype=dtype, device=dev)
+        b = torch.randn(n, n, dtype=dtype, device=dev)
         torch.matmul(a, b)
-        e1.record()
-        e1.synchronize()
-        best = min(best, e0.elapsed_time(e1))
-    del a, b
+        torch.cuda.synchronize(dev)
+        best = 1e30
+        for _ in range(3):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b)
+            e1.record()
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        del a, b
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
     return 2.0 * n ** 3 / (best * 1e-3) / 1e12
 
 
@@ -497,6 +504,7 @@ def run_ours(args):
             inst.close()
 
     fp64_peak = dgemm_tflops(dev)
+    tf32_peak = dgemm_tflops(dev, torch.float32)
 
     # max over ranks
     total_ms, e2e_total = combine_ranks(total_ms, float(np.sum(e2e_ms)), dist, dev)
@@ -540,6 +548,8 @@ def run_ours(args):
         'step_contraction_frac': f64_flops / (step_ms * 1e-3) / 1e12 / fp64_peak,
         'svd_steps_ms_serial': sprof['svd_ms'],
         'bf16_peak_measured_tflops': peaks.get('bf16_tflops'),
+        'tf32_peak_measured_tflops': tf32_peak,
+        'fp64_peak_measured_tflops': fp64_peak,
     }
     head_form = forms[args.precision]
     n_steps = args.steps * world
