@@ -84,35 +84,16 @@ struct RoundScratch {
 
 // One sweep of one-sided Jacobi rotations over all column pairs (circle-method rounds) of the
 // kp x kp column-major matrix A (leading dimension ld), accumulating into V (same layout).  Per
-// round: thread q < kp/2 forms pair q's rotation (one pair per thread, so the square roots and
-// divisions are not repeated across a warp), then every warp applies the rotations, one (pair,
-// row) element per lane.  Pairs with |a_i . a_j| <= tol |a_i| |a_j| are left alone.  Returns (to
-// every thread) the largest |a_i . a_j| / (|a_i| |a_j|) seen.
-//
-// FP64 lane-operations are scarce on this GPU (two per cycle per SM), so the FP64 sweeps spend
-// them only where the accuracy needs them:
-//   * the squared column norms are carried in nrm (recomputed at the start of each sweep and
-//     updated with each rotation: a' = c^2 (a - 2 t g + t^2 b), b' = c^2 (b + 2 t g + t^2 a)),
-//     so a pair costs one dot product instead of three;
-//   * the relative off-diagonal value and the tangent t of the angle are formed in FP32 (they
-//     set only the convergence rate); c = 1 / sqrt(1 + t^2) and s = c t are formed in F from
-//     that t, so the rotation is orthogonal to F's rounding whatever t is.
+// round: thread q < kp/2 forms pair q's three dot products and its rotation (one pair per
+// thread, so the FP64 square roots and divisions are not repeated across a warp), then every
+// thread applies the rotations, one (pair, row) element at a time.  Pairs with
+// |a_i . a_j| <= tol |a_i| |a_j| are left alone.  Returns (to every thread) the largest
+// |a_i . a_j| / (|a_i| |a_j|) seen.
 template <typename F>
-__device__ float jacobi_sweep(F* A, F* V, int kp, int ld, F tol, RoundScratch rs, float* s_max,
-                              F* nrm) {
-    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5,
-              nw = nt >> 5;
+__device__ float jacobi_sweep(F* A, F* V, int kp, int ld, F tol, RoundScratch rs, float* s_max) {
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
     const int np = kp / 2;
     if (tid == 0) *s_max = 0.0f;
-    for (int c = warp; c < kp; c += nw) {
-        F v = 0;
-        for (int r = lane; r < kp; r += 32) v = fma(A[c * ld + r], A[c * ld + r], v);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) nrm[c] = v;
-    }
-    __syncthreads();
-    const float tolf = (float)tol;
     float wmax = 0.0f;
     for (int round = 0; round < kp - 1; ++round) {
         for (int q = tid; q < np; q += nt) {
@@ -121,34 +102,23 @@ __device__ float jacobi_sweep(F* A, F* V, int kp, int ld, F tol, RoundScratch rs
             const int j = 1 + (p1 - 1 + round) % (kp - 1);
             const F* ai = A + (long long)i * ld;
             const F* aj = A + (long long)j * ld;
-            const F al = nrm[i], be = nrm[j];
-            F ga = 0;
-            for (int r = 0; r < kp; ++r) ga = fma(ai[r], aj[r], ga);
+            F al = 0, be = 0, ga = 0;
+            for (int r = 0; r < kp; ++r) {
+                const F x = ai[r], y = aj[r];
+                al = fma(x, x, al);
+                be = fma(y, y, be);
+                ga = fma(x, y, ga);
+            }
             int act = 0;
             F c = 1, sn = 0;
             if (al > F(0) && be > F(0)) {
-                // FP32 holds the norms unless a column is tiny (below 1e-30 in squared norm: a
-                // padding or rank-deficient column); those pairs take the type F throughout
-                const bool in_range = al > F(1e-30) && be > F(1e-30);
-                const float g32 = (float)ga;
-                const float rel = in_range ? fabsf(g32) / (sqrtf((float)al) * sqrtf((float)be))
-                                           : (float)(fabs(ga) / (sqrt(al) * sqrt(be)));
-                wmax = fmaxf(wmax, rel);
-                if (rel > tolf) {
-                    F t;
-                    if (in_range) {
-                        const float z = (float)(be - al) / (2.0f * g32);
-                        float t32 = (z >= 0.0f ? 1.0f : -1.0f) / (fabsf(z) + sqrtf(1.0f + z * z));
-                        if (fabsf(z) > 1e18f) t32 = 0.5f / z;  // 1 + z^2 would overflow
-                        t = (F)t32;
-                    } else {
-                        const F zeta = (be - al) / (F(2) * ga);
-                        t = (zeta >= F(0) ? F(1) : F(-1)) / (fabs(zeta) + sqrt(F(1) + zeta * zeta));
-                    }
+                const F rel = fabs(ga) / (sqrt(al) * sqrt(be));
+                wmax = fmaxf(wmax, (float)rel);
+                if (rel > tol) {
+                    const F zeta = (be - al) / (F(2) * ga);
+                    const F t = (zeta >= F(0) ? F(1) : F(-1)) / (fabs(zeta) + sqrt(F(1) + zeta * zeta));
                     c = F(1) / sqrt(F(1) + t * t);
                     sn = c * t;
-                    nrm[i] = c * c * (al - F(2) * t * ga + t * t * be);
-                    nrm[j] = c * c * (be + F(2) * t * ga + t * t * al);
                     act = 1;
                 }
             }
@@ -162,14 +132,14 @@ __device__ float jacobi_sweep(F* A, F* V, int kp, int ld, F tol, RoundScratch rs
         }
         __syncthreads();
         // rotations: warp per pair, lane per row (no integer division in the inner loop)
-        for (int q = warp; q < np; q += nw) {
+        for (int q = tid >> 5; q < np; q += nt >> 5) {
             if (!rs.act[q]) continue;
             const F c = reinterpret_cast<const F*>(rs.c)[q], sn = reinterpret_cast<const F*>(rs.s)[q];
             F* ai = A + (long long)rs.pi[q] * ld;
             F* aj = A + (long long)rs.pj[q] * ld;
             F* vi = V + (long long)rs.pi[q] * ld;
             F* vj = V + (long long)rs.pj[q] * ld;
-            for (int r = lane; r < kp; r += 32) {
+            for (int r = tid & 31; r < kp; r += 32) {
                 const F x = ai[r], y = aj[r];
                 ai[r] = c * x - sn * y;
                 aj[r] = sn * x + c * y;
@@ -202,7 +172,7 @@ __device__ float jacobi_sweep(F* A, F* V, int kp, int ld, F tol, RoundScratch rs
 // scaled once, and the inverse factor by column back substitution with a warp per column.
 constexpr int kCholNB = 16;
 
-__global__ void __launch_bounds__(kPsvdThreads, 1)
+__global__ void __launch_bounds__(kPsvdThreads)
     chol_orth_kernel(const double* __restrict__ G, int k, double shift, double* __restrict__ T,
                      double* Xg) {
     extern __shared__ double sm[];
@@ -302,7 +272,7 @@ __global__ void __launch_bounds__(kPsvdThreads, 1)
 // zero column that is never rotated); columns are stored with the odd leading dimension
 // ld = kp + 1 so that the threads of the dot-product phase, which read different columns, hit
 // different shared-memory banks.  Shared memory: jacobi_svd_smem(k).
-__global__ void __launch_bounds__(kPsvdThreads, 1)
+__global__ void __launch_bounds__(kPsvdThreads)
     jacobi_svd_kernel(const double* __restrict__ B, int k, double* __restrict__ S,
                       double* __restrict__ U, double* __restrict__ W, int* info, double* Vg) {
     extern __shared__ double sm[];
@@ -315,8 +285,7 @@ __global__ void __launch_bounds__(kPsvdThreads, 1)
     RoundScratch rs;
     rs.c = sig + kp;
     rs.s = rs.c + np;
-    double* nrm64 = rs.s + np;  // squared column norms of the sweep in progress
-    int* rank = (int*)(nrm64 + kp);
+    int* rank = (int*)(rs.s + np);
     rs.act = rank + kp;
     rs.pi = rs.act + np;
     rs.pj = rs.pi + np;
@@ -355,7 +324,7 @@ __global__ void __launch_bounds__(kPsvdThreads, 1)
     const float tol32 = 4.0f * (float)kp * 5.9604645e-8f;
     bool w_is_identity = false;  // the first FP32 sweep found every pair orthogonal: W = I
     for (int sw = 0; sw < kJacobiMaxSweeps32; ++sw)
-        if (jacobi_sweep<float>(A32, V32, kp, ld, tol32, rs, &s_max, (float*)nrm64) <= tol32) {
+        if (jacobi_sweep<float>(A32, V32, kp, ld, tol32, rs, &s_max) <= tol32) {
             w_is_identity = sw == 0;  // no rotation was made (uniform: s_max is shared)
             break;
         }
@@ -412,7 +381,7 @@ __global__ void __launch_bounds__(kPsvdThreads, 1)
     {
         int sw = 0;
         for (; sw < kJacobiMaxSweeps64; ++sw) {
-            const float mx = jacobi_sweep<double>(A, V, kp, ld, tol64, rs, &s_max, nrm64);
+            const float mx = jacobi_sweep<double>(A, V, kp, ld, tol64, rs, &s_max);
             if (mx <= tol64 || mx < 1e-6f) break;
         }
         if (sw >= kJacobiMaxSweeps64) bad = 1;
@@ -478,9 +447,9 @@ void launch_refill(double* V, int n, int k, const double* S, unsigned long long 
 size_t chol_orth_smem(int k, bool global_x) {
     return (size_t)((global_x ? 1 : 2) * k * k + 2 * k) * sizeof(double);
 }
-size_t jacobi_svd_smem(int k, bool global_v) {  // A (and W), S, round scratch, norms, ranks
+size_t jacobi_svd_smem(int k, bool global_v) {  // A (and W), S, the round scratch, the ranks
     const int kp = k + (k & 1), ld = kp + 1, np = kp / 2;
-    return (size_t)((global_v ? 1 : 2) * kp * ld + kp + 2 * np + kp) * sizeof(double) +
+    return (size_t)((global_v ? 1 : 2) * kp * ld + kp + 2 * np) * sizeof(double) +
            (size_t)(kp + 3 * np) * sizeof(int);
 }
 
