@@ -11,7 +11,7 @@ tests/golden/cfg3_D4_chi64.json (written by tests/golden/make_golden.py).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|f64emu|tf32x3]
                     [--impl ours|reference] [--batch B] [--method split|split-d2]
-                    [--gemm M,N,K]
+                    [--gemm M,N,K] [--jacobi-kernel cluster|cta] [--jacobi-timing k]
 
 Prints one JSON line (rank 0).  Under torchrun with N > 1 every rank runs an independent replica
 (the single-instance path does not shard) and `value` is the sum over ranks.
@@ -38,8 +38,9 @@ ACCEPT_DF = 1e-8
 PRECISIONS = {'fp64': 0, 'tf32': 1, 'tf32x3': 2, 'bf16': 3, 'bf16x3': 4, 'f64emu': 5}
 FORMS = ('fp64', 'f64emu', 'tf32x3')   # the forms every run compares
 SVD_MODES = {'qr': 0, 'polar': 1, 'partial': 2, 'partial-random': 3}
+JACOBI_KERNELS = {'cta': 0, 'cluster': 1}
 KERNELS = (('ctr_f64_kernel', 0), ('ctr_skinny_kernel', 1), ('ctr_tc_kernel', 2),
-           ('emu_ctr_kernel', 3), ('jacobi_svd_kernel', 4), ('chol_orth_kernel', 5))
+           ('emu_ctr_kernel', 3), ('jacobi_svd', 4), ('chol_orth_kernel', 5))
 NOMINAL_FP64_TFLOPS = 1.25
 
 
@@ -75,9 +76,25 @@ def parse():
     ap.add_argument('--gemm', default=None,
                     help='M,N,K: time one plain contraction O = X Y through sctm_gemm in the '
                          'headline precision instead (kernel isolation and profiler captures)')
+    ap.add_argument('--jacobi-kernel', default=None, choices=list(JACOBI_KERNELS),
+                    help='kernel of the partial SVD\'s k x k Jacobi SVD: cluster (rows split over '
+                         'a cluster of 8 CTAs) or cta (one CTA, the library default); default: '
+                         'the faster per evaluation as measured, cluster for split, cta for '
+                         'split-d2 (whose iteration count to the tolerance rose with the '
+                         'cluster kernel\'s rounding from 102 to 232)')
+    ap.add_argument('--jacobi-timing', type=int, default=0,
+                    help='k: time the partial SVD\'s k x k Jacobi SVD through sctm_jacobi_svd, '
+                         'one-CTA kernel against the cluster kernel, on a dense Gaussian matrix '
+                         '(cold solve) and a nearly diagonal graded one (warm solve)')
     ap.add_argument('--D', type=int, default=None, help='PEPS bond dimension (small captures)')
     ap.add_argument('--chi', type=int, default=None, help='chi (small captures)')
     return ap.parse_args()
+
+
+def jacobi_kernel(args):
+    if args.jacobi_kernel:
+        return args.jacobi_kernel
+    return 'cta' if args.method == 'split-d2' else 'cluster'
 
 
 def workload(args):
@@ -298,7 +315,8 @@ def combine_ranks(ms, e2e_ms, dist, device):
 class Instance:
     """One context of the workload in one precision form, driven through the C ABI."""
 
-    def __init__(self, sctm, w, prec, svd, stream, dev, A_host, method='split', p4='full'):
+    def __init__(self, sctm, w, prec, svd, stream, dev, A_host, method='split', p4='full',
+                 jacobi='cluster'):
         import torch
         st, O = sctm.sctm_ising_pepo(w['T'])
         st, o = sctm.sctm_default_opts()
@@ -308,6 +326,7 @@ class Instance:
         o.precision = PRECISIONS[prec]
         o.method = METHODS[method]
         o.p4_mode = 1 if p4 == 'half' else 0
+        o.jacobi = JACOBI_KERNELS[jacobi]
         self.sctm, self.w, self.prec = sctm, w, prec
         self.A_dev = torch.from_numpy(A_host).to(dev)
         st, self.ctx = sctm.sctm_create(self.A_dev, np.ascontiguousarray(O), w['chi'], o)
@@ -420,7 +439,8 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
     p4 = args.p4 or ('half' if args.method == 'split-d2' else 'full')
-    head = Instance(sctm, w, args.precision, args.svd, stream, dev, A_host, args.method, p4)
+    head = Instance(sctm, w, args.precision, args.svd, stream, dev, A_host, args.method, p4,
+                    jacobi_kernel(args))
 
     # ---- headline: converged evaluations, inputs resident on the device, profiling off
     for _ in range(args.warmup):
@@ -496,7 +516,8 @@ def run_ours(args):
         for form in FORMS:
             if form == args.precision:
                 continue
-            inst = Instance(sctm, w, form, args.svd, stream, dev, A_host)
+            inst = Instance(sctm, w, form, args.svd, stream, dev, A_host,
+                            jacobi=jacobi_kernel(args))
             inst.evaluate()
             torch.cuda.synchronize(dev)
             m2, f2, i2, s2 = timed(inst, stream, flush, min(args.steps, 2))
@@ -563,6 +584,7 @@ def run_ours(args):
         'config': {'workload': workload_name(w, args.method), 'D': w['D'], 'chi': w['chi'],
                    'T': w['T'], 'seed': w['seed'], 'eps': w['eps'], 'tol': w['tol'],
                    'precision': args.precision, 'svd': args.svd, 'method': args.method,
+                   'jacobi_kernel': jacobi_kernel(args),
                    'projector4': p4,
                    'accept': '|f - f_oracle| <= %g, f_oracle from tests/golden/%s' % (
                        ACCEPT_DF, os.path.basename(GOLDENS[args.method])),
@@ -606,6 +628,7 @@ def run_batch(args):
         o.cuda_stream = streams[i].cuda_stream
         o.svd_mode = SVD_MODES[args.svd]
         o.precision = PRECISIONS[args.precision]
+        o.jacobi = JACOBI_KERNELS[jacobi_kernel(args)]
         st, ctx = sctm.sctm_create(A, np.ascontiguousarray(O), w['chi'], o)
         if st != sctm.SCTM_OK:
             raise RuntimeError('sctm_create failed for batch member %d: %s' % (i, sctm.STATUS_NAMES[st]))
@@ -698,8 +721,53 @@ def run_gemm(args):
                               'the contraction kernel'}), flush=True)
 
 
+def run_jacobi(args):
+    """The k x k Jacobi SVD of the partial SVD in isolation: both kernels, CUDA events around each
+    call (which includes the entry point's status-word allocation and stream synchronisation)."""
+    import torch
+    from paper_2506_19339_gb300 import build, sctm
+    k = args.jacobi_timing
+    dev = torch.device('cuda', 0)
+    build.build()
+    sctm.load()
+    rng = np.random.default_rng(k)
+    s = np.logspace(0, -12, k)
+    mats = {'gaussian (cold)': rng.standard_normal((k, k)),
+            'near-diagonal graded (warm)': np.diag(s) + 1e-7 * np.triu(rng.standard_normal((k, k)), 1) * s}
+    stream = torch.cuda.current_stream(dev)
+    out = {'jacobi_k': k}
+    for name, B in mats.items():
+        Bd = torch.from_numpy(B.ravel(order='F').copy()).to(dev)
+        S = torch.zeros(k, dtype=torch.float64, device=dev)
+        U = torch.zeros(k * k, dtype=torch.float64, device=dev)
+        W = torch.zeros(k * k, dtype=torch.float64, device=dev)
+        row = {}
+        for vname, v in (('cta', sctm.SCTM_JACOBI_CTA), ('cluster', sctm.SCTM_JACOBI_CLUSTER)):
+            for _ in range(args.warmup):
+                assert sctm.sctm_jacobi_svd(Bd, k, S, U, W, v, stream.cuda_stream) == sctm.SCTM_OK
+            ms = []
+            for _ in range(args.steps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                st = sctm.sctm_jacobi_svd(Bd, k, S, U, W, v, stream.cuda_stream)
+                e1.record(stream)
+                e1.synchronize()
+                assert st == sctm.SCTM_OK, st
+                ms.append(e0.elapsed_time(e1))
+            ref = np.linalg.svd(B, compute_uv=False)
+            row[vname] = {'ms_median': float(np.median(ms)),
+                          'max_abs_dS_vs_lapack': float(np.max(np.abs(S.cpu().numpy() - ref)))}
+        row['speedup'] = row['cta']['ms_median'] / row['cluster']['ms_median']
+        out[name] = row
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
+    if args.jacobi_timing:
+        run_jacobi(args)
+        return
     if args.gemm:
         run_gemm(args)
         return

@@ -192,7 +192,8 @@ sctm_status sctm_create(const double* peps, const double* pepo, int chi, const s
          (opts.precision != SCTM_PREC_FP64 || opts.grad_mode != SCTM_GRAD_ENV)) ||
         (opts.method == SCTM_METHOD_SPLIT_D2 && opts.grad_mode != SCTM_GRAD_ENV) ||
         (opts.p4_mode != SCTM_P4_FULL && opts.p4_mode != SCTM_P4_HALF) ||
-        (opts.p4_mode == SCTM_P4_HALF && opts.method != SCTM_METHOD_SPLIT_D2))
+        (opts.p4_mode == SCTM_P4_HALF && opts.method != SCTM_METHOD_SPLIT_D2) ||
+        (opts.jacobi != SCTM_JACOBI_CTA && opts.jacobi != SCTM_JACOBI_CLUSTER))
         return SCTM_EINVAL;
     std::unique_ptr<sctm_ctx> c(new sctm_ctx());
     c->opts = opts;
@@ -202,6 +203,7 @@ sctm_status sctm_create(const double* peps, const double* pepo, int chi, const s
         cudaStream_t s = (cudaStream_t)opts.cuda_stream;
         c->eng.reset(new Engine(s, opts.precision, opts.svd_cutoff));
         c->eng->svd_mode = opts.svd_mode;
+        c->eng->jacobi_cluster = opts.jacobi == SCTM_JACOBI_CLUSTER;
         Engine& e = *c->eng;
         const long long na = peps_size(opts), no = pepo_size(opts);
         c->A_dev = e.dalloc(na);
@@ -758,6 +760,45 @@ static bool stream_on(cudaStream_t s, int dev) {
         return false;
     }
     return sd == dev;
+}
+
+// sctm_jacobi_svd: the partial SVD's k x k Jacobi SVD on device buffers, either kernel
+sctm_status sctm_jacobi_svd(const double* B, int k, double* S, double* U, double* W, int variant,
+                            void* cuda_stream) {
+    if (!B || !S || !U || !W || k < 1 || k > kPsvdMaxK) return SCTM_EINVAL;
+    if (variant != SCTM_JACOBI_CTA && variant != SCTM_JACOBI_CLUSTER) return SCTM_EINVAL;
+    if (variant == SCTM_JACOBI_CLUSTER && !jacobi_cluster_fits(k)) return SCTM_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SCTM_ECUDA;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (!on_device(B, dev) || !on_device(S, dev) || !on_device(U, dev) || !on_device(W, dev) ||
+        !stream_on(s, dev))
+        return SCTM_EINVAL;
+    const int kp = k + (k & 1);
+    int* info = nullptr;
+    double* Vg = nullptr;
+    if (cudaMalloc((void**)&info, sizeof(int)) != cudaSuccess) return SCTM_ENOMEM;
+    sctm_status st = SCTM_OK;
+    if (variant == SCTM_JACOBI_CTA && k > kPsvdSmemK &&
+        cudaMalloc((void**)&Vg, (size_t)kp * (kp + 1) * sizeof(double)) != cudaSuccess)
+        st = SCTM_ENOMEM;
+    int info_host = 0;
+    if (st == SCTM_OK && cudaMemsetAsync(info, 0, sizeof(int), s) != cudaSuccess) st = SCTM_ECUDA;
+    if (st == SCTM_OK) {
+        if (variant == SCTM_JACOBI_CLUSTER)
+            launch_jacobi_svd_cluster(B, k, S, U, W, info, s);
+        else
+            launch_jacobi_svd_cta(B, k, S, U, W, info, Vg, s);
+        if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+            st = SCTM_ECUDA;
+        else if (cudaMemcpy(&info_host, info, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+            st = SCTM_ECUDA;
+        else if (info_host)
+            st = SCTM_ECUSOLVER;
+    }
+    cudaFree(info);
+    if (Vg) cudaFree(Vg);
+    return st;
 }
 
 sctm_status sctm_gemm(const double* X, const double* Y, double* O, int M, int N, int K,

@@ -756,8 +756,9 @@ Engine::PPair Engine::projector(Network& net, Plan& P, const Ten& U, const Ten& 
             ctr(net, W, "ba,bc->ac", Mv, Qyt, &Zbt);  // Z = M^T Q_y
             cholqr3(Zb, Yb, Q1, Qz);                  // Q_z
             ctr(net, W, "ac,ad->cd", Zbt, Qzt, &Bt);  // B = Z^T Q_z = Q_y^T M Q_z
+            const bool jc = jacobi_cluster;
             push(W, std::make_unique<FnStep>([=](cudaStream_t s) {
-                launch_jacobi_svd(R1, k, S, Ur, Wr, np->svd_info + info_idx, Vg, s);
+                launch_jacobi_svd(R1, k, S, Ur, Wr, np->svd_info + info_idx, Vg, jc, s);
             }, SCTM_KERNEL_JACOBI));
             ctr(net, W, "ac,cd->ad", Qyt, Urt, &Ut);  // U = Q_y U_B
             ctr(net, W, "ac,cd->ad", Qzt, Wt, &Vb);   // V = Q_z V_B
@@ -1186,8 +1187,9 @@ void build_spectrum(Engine& e, Network& net) {
         double* Vg = chi > kPsvdSmemK ? e.dalloc((long long)kp * (kp + 1)) : nullptr;
         const int info_idx = net.n_svd++;
         const Network* np = &net;
+        const bool jc = e.jacobi_cluster;
         e.push(P, std::make_unique<FnStep>([=](cudaStream_t s) {
-            launch_jacobi_svd(rho_p, chi, Sraw, Ub, Wb, np->svd_info + info_idx, Vg, s);
+            launch_jacobi_svd(rho_p, chi, Sraw, Ub, Wb, np->svd_info + info_idx, Vg, jc, s);
         }, SCTM_KERNEL_JACOBI));
         e.push(P, std::make_unique<FnStep>(
             [=](cudaStream_t s) { launch_spectrum_update(Sraw, rho_p, chi, S_old, dS, s); }));

@@ -215,6 +215,7 @@ public:
     // ||dS|| at which sctm_iterate leaves a mixed form for the FP64 polish
     static double switch_level(int prec);
     int svd_mode = SCTM_SVD_QR;
+    bool jacobi_cluster = false;  // SCTM_JACOBI_CLUSTER: the Jacobi SVD on a cluster of CTAs
     bool dry = false;  // SCTM_DRYRUN=1: build plans with placeholder pointers, no CUDA calls
     int cur_stream = 0;  // stream index given to steps while a plan is being built
 

@@ -28,6 +28,8 @@
 //     converges quadratically, so one or two FP64 sweeps reach rounding level.  B's columns are
 //     the rows of the triangular factor of Z, graded by the singular values, which is the
 //     ordering under which one-sided Jacobi converges fastest.
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <cstdlib>
 #include <mutex>
@@ -412,6 +414,342 @@ __global__ void __launch_bounds__(kPsvdThreads)
     if (tid == 0 && info) *info = bad;
 }
 
+// ---------------------------------------------------------------------------------------------
+// The same one-sided Jacobi SVD spread over a thread-block cluster of kJcCluster CTAs.
+//
+// One SM retires two FP64 lane-operations per cycle, so the one-CTA kernel above is bound by its
+// SM's FP64 pipe (about 1.5 ms per FP64 sweep at k = 80).  Here the rows of A (= B W) and of W
+// are split across the cluster: CTA c keeps rows [c rows_per, (c + 1) rows_per) of both in its
+// shared memory.  A round of the circle method then costs, per CTA, the dot products and the
+// rotations of its own rows only:
+//   1. every CTA forms, for each of the kp/2 pairs of the round, the three partial dot products
+//      a_i.a_i, a_j.a_j, a_i.a_j over its rows (one buffer of 3 kp/2 values, two alternating
+//      buffers so that a round's writes never meet the previous round's reads);
+//   2. one cluster barrier; every CTA reads the partial sums of all CTAs through distributed
+//      shared memory and adds them in cluster-rank order, so every CTA holds bit-identical sums
+//      and computes bit-identical rotations (FP64 angles, the formulas of jacobi_sweep) and
+//      bit-identical convergence decisions: the loops stay in step without further exchange;
+//   3. every CTA rotates its own rows of A and W.
+// W's re-orthonormalisation after the FP32 sweeps is two Newton-Schulz steps
+// W <- W (3 I - W^T W) / 2 (the Gram matrix reduced over the cluster: a reduce-scatter and an
+// all-gather through distributed shared memory), A = B W reads the rows of W from their owners,
+// and the singular values are column norms summed over the cluster.  Results agree with the
+// one-CTA kernel to rounding (the dot products are summed in another order).
+// ---------------------------------------------------------------------------------------------
+namespace cg = cooperative_groups;
+
+constexpr int kJcCluster = 8;                      // CTAs per cluster (the portable maximum)
+constexpr int kJcThreads = 256;
+constexpr int kJcMaxKp = 128;                      // the k x k Gram matrix fits in shared memory
+constexpr int kJcMaxRows = kJcMaxKp / kJcCluster;  // rows of A and W per CTA, at most
+constexpr int kJcMinKp = 32;                       // smaller orders stay on the one-CTA kernel
+constexpr int kJcNsSteps = 2;                      // Newton-Schulz steps (1e-5 -> 1e-10 -> eps)
+
+namespace {
+
+struct JcLayout {  // shared-memory carve-up of one CTA, in doubles from the base
+    int kp, np, rows_per, un, slice_n;
+    long long al, vl, un_off, slice, part, cpart, sig, rc, rsn, ints;
+    long long doubles;
+    __host__ __device__ explicit JcLayout(int k) {
+        kp = k + (k & 1);
+        np = kp / 2;
+        rows_per = (kp + kJcCluster - 1) / kJcCluster;
+        un = kp * kp > rows_per * kp ? kp * kp : rows_per * kp;
+        slice_n = (kp * kp + kJcCluster - 1) / kJcCluster;
+        al = 0;
+        vl = al + (long long)rows_per * kp;
+        un_off = vl + (long long)rows_per * kp;
+        slice = un_off + un;
+        part = slice + slice_n;  // 2 buffers x 3 values x np pairs
+        cpart = part + 3LL * kp;
+        sig = cpart + kp;
+        rc = sig + kp;
+        rsn = rc + np;
+        ints = rsn + np;         // rank[kp], act[np], pi[np], pj[np]
+        doubles = ints;
+    }
+    __host__ __device__ size_t bytes() const {
+        return (size_t)doubles * sizeof(double) + (size_t)(kp + 3 * np) * sizeof(int);
+    }
+};
+
+// One sweep over all column pairs of the kp x kp matrix whose rows [row0, row0 + nr) this CTA
+// holds (Al, Vl: row-major, row stride kp).  part: two alternating buffers of 3 np values of F;
+// buf selects the one the next round writes.  Returns to every thread of every CTA the largest
+// relative off-diagonal value |a_i . a_j| / (|a_i| |a_j|) of the sweep (identical in all CTAs).
+template <typename F>
+__device__ float cluster_sweep(cg::cluster_group& cluster, F* Al, F* Vl, int nr, int kp, F tol,
+                               F* part, int& buf, RoundScratch rs, float* s_max) {
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
+    const int np = kp / 2;
+    if (tid == 0) *s_max = 0.0f;
+    float wmax = 0.0f;
+    for (int round = 0; round < kp - 1; ++round) {
+        F* pb = part + (long long)buf * 3 * np;
+        // 1. partial dot products of this CTA's rows
+        for (int q = tid; q < np; q += nt) {
+            const int p0 = q, p1 = kp - 1 - q;
+            const int i = p0 == 0 ? 0 : 1 + (p0 - 1 + round) % (kp - 1);
+            const int j = 1 + (p1 - 1 + round) % (kp - 1);
+            F al = 0, be = 0, ga = 0;
+            for (int r = 0; r < nr; ++r) {
+                const F x = Al[r * kp + i], y = Al[r * kp + j];
+                al = fma(x, x, al);
+                be = fma(y, y, be);
+                ga = fma(x, y, ga);
+            }
+            pb[3 * q] = al;
+            pb[3 * q + 1] = be;
+            pb[3 * q + 2] = ga;
+            rs.pi[q] = i;
+            rs.pj[q] = j;
+        }
+        cluster.sync();
+        // 2. the cluster's sums in rank order, then the rotation of every pair (in every CTA)
+        for (int q = tid; q < np; q += nt) {
+            F al = 0, be = 0, ga = 0;
+            for (int src = 0; src < kJcCluster; ++src) {
+                const F* rp = cluster.map_shared_rank(pb, src);
+                al += rp[3 * q];
+                be += rp[3 * q + 1];
+                ga += rp[3 * q + 2];
+            }
+            int act = 0;
+            F c = 1, sn = 0;
+            if (al > F(0) && be > F(0)) {
+                const F rel = fabs(ga) / (sqrt(al) * sqrt(be));
+                wmax = fmaxf(wmax, (float)rel);
+                if (rel > tol) {
+                    const F zeta = (be - al) / (F(2) * ga);
+                    const F t = (zeta >= F(0) ? F(1) : F(-1)) / (fabs(zeta) + sqrt(F(1) + zeta * zeta));
+                    c = F(1) / sqrt(F(1) + t * t);
+                    sn = c * t;
+                    act = 1;
+                }
+            }
+            reinterpret_cast<F*>(rs.c)[q] = c;
+            reinterpret_cast<F*>(rs.s)[q] = sn;
+            rs.act[q] = act;
+        }
+        __syncthreads();
+        // 3. rotations of this CTA's rows of A and W, one (pair, row) element per thread
+        for (int e = tid; e < np * nr; e += nt) {
+            const int q = e % np, r = e / np;
+            if (!rs.act[q]) continue;
+            const F c = reinterpret_cast<const F*>(rs.c)[q], sn = reinterpret_cast<const F*>(rs.s)[q];
+            F* a = Al + r * kp;
+            F* v = Vl + r * kp;
+            const int i = rs.pi[q], j = rs.pj[q];
+            const F x = a[i], y = a[j];
+            a[i] = c * x - sn * y;
+            a[j] = sn * x + c * y;
+            const F u = v[i], w = v[j];
+            v[i] = c * u - sn * w;
+            v[j] = sn * u + c * w;
+        }
+        __syncthreads();
+        buf ^= 1;
+    }
+    for (int o = 16; o > 0; o >>= 1) wmax = fmaxf(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+    if (lane == 0) atomicMax((int*)s_max, __float_as_int(wmax));
+    __syncthreads();
+    const float r = *s_max;
+    __syncthreads();
+    return r;
+}
+
+}  // namespace
+
+// B (k x k, column-major) -> S (k, decreasing), U, W (k x k, column-major, columns in the order
+// of S) with B = U diag(S) W^T; info: 0, or 1 if the FP64 sweep limit was reached.  Launched as
+// one cluster of kJcCluster CTAs; kJcMinKp <= k + (k & 1) <= kJcMaxKp.  Shared memory:
+// JcLayout(k).bytes().  Every loop that contains a cluster barrier runs the same number of times
+// in every CTA (its trip count depends only on k and on values every CTA computes identically).
+__global__ void __cluster_dims__(kJcCluster, 1, 1) __launch_bounds__(kJcThreads)
+    jacobi_svd_cluster_kernel(const double* __restrict__ B, int k, double* __restrict__ S,
+                              double* __restrict__ U, double* __restrict__ W, int* info) {
+    cg::cluster_group cluster = cg::this_cluster();
+    const JcLayout L(k);
+    const int kp = L.kp, np = L.np, rows_per = L.rows_per;
+    if (kp < 2 || kp > kJcMaxKp) return;  // uniform over the cluster (the launcher checks)
+    extern __shared__ double sm[];
+    const int crank = (int)cluster.block_rank();
+    const int row0 = min(kp, crank * rows_per);
+    const int nr = min(kp, row0 + rows_per) - row0;  // rows of this CTA (0 for trailing CTAs)
+    double* Al = sm + L.al;
+    double* Vl = sm + L.vl;
+    double* Un = sm + L.un_off;  // FP32 rows, then the Gram matrix, then B's rows
+    double* slice = sm + L.slice;
+    double* part = sm + L.part;
+    double* cpart = sm + L.cpart;
+    double* sig = sm + L.sig;
+    RoundScratch rs;
+    rs.c = sm + L.rc;
+    rs.s = sm + L.rsn;
+    int* rank = (int*)(sm + L.ints);
+    rs.act = rank + kp;
+    rs.pi = rs.act + np;
+    rs.pj = rs.pi + np;
+    float* A32 = (float*)Un;
+    float* V32 = A32 + rows_per * kp;
+    __shared__ float s_max;
+    __shared__ int s_exp;
+    __shared__ double s_wmax[kJcThreads / 32];
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5,
+              nw = nt >> 5;
+    int bad = 0, buf = 0;
+
+    // 0. scale: B 2^-ex has entries below 1 in magnitude (every CTA reads all of B)
+    {
+        double m = 0.0;
+        for (int e = tid; e < k * k; e += nt) m = fmax(m, fabs(B[e]));
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) s_wmax[warp] = m;
+        __syncthreads();
+        if (tid == 0) {
+            double mm = 0.0;
+            for (int w = 0; w < nw; ++w) mm = fmax(mm, s_wmax[w]);
+            int e2 = 0;
+            if (mm > 0.0 && isfinite(mm)) frexp(mm, &e2);
+            s_exp = e2;
+        }
+        __syncthreads();
+    }
+    const int ex = s_exp;
+    // 1. FP32 sweeps on this CTA's rows of B 2^-ex
+    for (int e = tid; e < nr * kp; e += nt) {
+        const int r = e / kp, c = e % kp, rg = row0 + r;
+        A32[e] = (rg < k && c < k) ? (float)ldexp(B[rg + (long long)c * k], -ex) : 0.0f;
+        V32[e] = rg == c ? 1.0f : 0.0f;
+    }
+    __syncthreads();
+    const float tol32 = 4.0f * (float)kp * 5.9604645e-8f;
+    bool w_is_identity = false;
+    for (int sw = 0; sw < kJacobiMaxSweeps32; ++sw)
+        if (cluster_sweep<float>(cluster, A32, V32, nr, kp, tol32, (float*)part, buf, rs, &s_max) <=
+            tol32) {
+            w_is_identity = sw == 0;
+            break;
+        }
+    // every CTA is past its last read of the FP32 partial sums before any buffer is reused
+    cluster.sync();
+    buf = 0;
+    if (w_is_identity) {
+        for (int e = tid; e < nr * kp; e += nt) {
+            const int r = e / kp, c = e % kp, rg = row0 + r;
+            Vl[e] = rg == c ? 1.0 : 0.0;
+            Al[e] = (rg < k && c < k) ? ldexp(B[rg + (long long)c * k], -ex) : 0.0;
+        }
+        __syncthreads();
+    } else {
+        // 2. W in FP64, re-orthonormalised by Newton-Schulz steps W <- W (3 I - X) / 2,
+        //    X = W^T W summed over the cluster
+        for (int e = tid; e < nr * kp; e += nt) Vl[e] = (double)V32[e];
+        __syncthreads();
+        const int kk = kp * kp;
+        const int e0 = min(kk, crank * L.slice_n), e1 = min(kk, e0 + L.slice_n);
+        for (int step = 0; step < kJcNsSteps; ++step) {
+            for (int e = tid; e < kk; e += nt) {  // this CTA's rows' share of X (row-major)
+                const int a = e / kp, b = e % kp;
+                double v = 0.0;
+                for (int r = 0; r < nr; ++r) v = fma(Vl[r * kp + a], Vl[r * kp + b], v);
+                Un[e] = v;
+            }
+            cluster.sync();
+            for (int e = e0 + tid; e < e1; e += nt) {  // reduce-scatter, rank order
+                double v = 0.0;
+                for (int src = 0; src < kJcCluster; ++src) v += cluster.map_shared_rank(Un, src)[e];
+                slice[e - e0] = v;
+            }
+            cluster.sync();
+            for (int e = tid; e < kk; e += nt) {  // all-gather of the summed slices
+                const int o = e / L.slice_n;
+                Un[e] = cluster.map_shared_rank(slice, o)[e - o * L.slice_n];
+            }
+            __syncthreads();
+            for (int e = tid; e < nr * kp; e += nt) {
+                const int r = e / kp, c = e % kp;
+                double v = 0.0;
+                for (int m = 0; m < kp; ++m) v = fma(Vl[r * kp + m], Un[m * kp + c], v);
+                Al[e] = 1.5 * Vl[e] - 0.5 * v;
+            }
+            __syncthreads();
+            for (int e = tid; e < nr * kp; e += nt) Vl[e] = Al[e];
+            __syncthreads();
+        }
+        // 3. A = B W 2^-ex on this CTA's rows; W's rows are read from the CTAs that hold them
+        cluster.sync();  // every CTA's W is final
+        double* Bl = Un;
+        for (int e = tid; e < nr * kp; e += nt) {
+            const int r = e / kp, m = e % kp, rg = row0 + r;
+            Bl[e] = (rg < k && m < k) ? B[rg + (long long)m * k] : 0.0;
+        }
+        __syncthreads();
+        for (int c = tid; c < kp; c += nt) {
+            double acc[kJcMaxRows];
+#pragma unroll
+            for (int r = 0; r < kJcMaxRows; ++r) acc[r] = 0.0;
+            for (int m = 0; m < kp; ++m) {
+                const int o = m / rows_per;
+                const double w = cluster.map_shared_rank(Vl, o)[(m - o * rows_per) * kp + c];
+#pragma unroll
+                for (int r = 0; r < kJcMaxRows; ++r)
+                    if (r < nr) acc[r] = fma(Bl[r * kp + m], w, acc[r]);
+            }
+#pragma unroll
+            for (int r = 0; r < kJcMaxRows; ++r)
+                if (r < nr) Al[r * kp + c] = ldexp(acc[r], -ex);
+        }
+        __syncthreads();
+    }
+    cluster.sync();  // no CTA rotates its W before every CTA has read it
+    // 4. FP64 sweeps (stopping rule of the one-CTA kernel)
+    const double tol64 = (double)kp * 2.220446049250313e-16;
+    {
+        int sw = 0;
+        for (; sw < kJacobiMaxSweeps64; ++sw) {
+            const float mx = cluster_sweep<double>(cluster, Al, Vl, nr, kp, tol64, part, buf, rs,
+                                                   &s_max);
+            if (mx <= tol64 || mx < 1e-6f) break;
+        }
+        if (sw >= kJacobiMaxSweeps64) bad = 1;
+    }
+    // 5. singular values = column norms summed over the cluster; ranks by decreasing value
+    for (int c = tid; c < kp; c += nt) {
+        double v = 0.0;
+        for (int r = 0; r < nr; ++r) v = fma(Al[r * kp + c], Al[r * kp + c], v);
+        cpart[c] = v;
+    }
+    cluster.sync();
+    for (int c = tid; c < k; c += nt) {
+        double v = 0.0;
+        for (int src = 0; src < kJcCluster; ++src) v += cluster.map_shared_rank(cpart, src)[c];
+        sig[c] = sqrt(v);  // of B 2^-ex
+    }
+    __syncthreads();
+    for (int c = tid; c < k; c += nt) {
+        int rk = 0;
+        for (int o = 0; o < k; ++o)
+            if (sig[o] > sig[c] || (sig[o] == sig[c] && o < c)) ++rk;
+        rank[c] = rk;
+    }
+    __syncthreads();
+    for (int e = tid; e < nr * k; e += nt) {
+        const int r = e / k, c = e % k, rg = row0 + r;
+        if (rg >= k) continue;
+        const int dst = rg + rank[c] * k;
+        const double sc = sig[c];
+        U[dst] = sc > 0.0 ? Al[r * kp + c] / sc : 0.0;
+        W[dst] = Vl[r * kp + c];
+    }
+    if (crank == 0) {
+        for (int c = tid; c < k; c += nt) S[rank[c]] = ldexp(sig[c], ex);
+        if (tid == 0 && info) *info = bad;
+    }
+    cluster.sync();  // no CTA exits while another may still read its shared memory
+}
+
 // Vout[r + c n] = VT[c + r n] for c < k: the first k right singular vectors of gesvd's V^T as
 // columns.
 __global__ void vt_columns_kernel(const double* __restrict__ VT, double* __restrict__ Vout, int n,
@@ -481,8 +819,34 @@ void launch_chol_orth(const double* G, int k, double shift, double* T, double* X
     chol_orth_kernel<<<1, kPsvdThreads, smem, s>>>(G, k, shift, T, Xg);
 }
 
+bool jacobi_cluster_fits(int k) {
+    const int kp = k + (k & 1);
+    return kp >= kJcMinKp && kp <= kJcMaxKp;
+}
+
+void launch_jacobi_svd_cluster(const double* B, int k, double* S, double* U, double* W, int* info,
+                               cudaStream_t s) {
+    const size_t smem = one_cta_smem(JcLayout(k).bytes());
+    static std::once_flag once;
+    std::call_once(once, [] {
+        const size_t mx = std::max(JcLayout(kJcMaxKp).bytes(), kExclusiveSmem);
+        cudaFuncSetAttribute(jacobi_svd_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)mx);
+    });
+    jacobi_svd_cluster_kernel<<<kJcCluster, kJcThreads, smem, s>>>(B, k, S, U, W, info);
+}
+
 void launch_jacobi_svd(const double* B, int k, double* S, double* U, double* W, int* info,
-                       double* Vg, cudaStream_t s) {
+                       double* Vg, bool cluster, cudaStream_t s) {
+    if (cluster && jacobi_cluster_fits(k)) {
+        launch_jacobi_svd_cluster(B, k, S, U, W, info, s);
+        return;
+    }
+    launch_jacobi_svd_cta(B, k, S, U, W, info, Vg, s);
+}
+
+void launch_jacobi_svd_cta(const double* B, int k, double* S, double* U, double* W, int* info,
+                           double* Vg, cudaStream_t s) {
     const size_t smem = one_cta_smem(jacobi_svd_smem(k, Vg != nullptr));
     static std::once_flag once;
     std::call_once(once, [] {

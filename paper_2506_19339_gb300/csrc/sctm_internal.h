@@ -92,8 +92,16 @@ void launch_chol_orth(const double* G, int k, double shift, double* T, double* X
                       cudaStream_t s);
 void launch_refill(double* V, int n, int k, const double* S, unsigned long long seed,
                    cudaStream_t s);
+// Jacobi SVD of the k x k matrix B: the cluster kernel if `cluster` and jacobi_cluster_fits(k),
+// the one-CTA kernel otherwise; Vg: global scratch of the one-CTA kernel above kPsvdSmemK
+// (kp (kp + 1) doubles), else null
 void launch_jacobi_svd(const double* B, int k, double* S, double* U, double* W, int* info,
-                       double* Vg, cudaStream_t s);
+                       double* Vg, bool cluster, cudaStream_t s);
+void launch_jacobi_svd_cta(const double* B, int k, double* S, double* U, double* W, int* info,
+                           double* Vg, cudaStream_t s);
+bool jacobi_cluster_fits(int k);  // 32 <= k + (k & 1) <= 128
+void launch_jacobi_svd_cluster(const double* B, int k, double* S, double* U, double* W, int* info,
+                               cudaStream_t s);
 void launch_vt_columns(const double* VT, double* Vout, int n, int k, cudaStream_t s);
 void launch_zero(double* p, long long n, cudaStream_t s);
 void launch_symmetrize(double* X, int n, cudaStream_t s);   // X <- (X + X^T) / 2, n x n

@@ -22,6 +22,7 @@ SCTM_SVD_QR, SCTM_SVD_POLAR, SCTM_SVD_PARTIAL, SCTM_SVD_PARTIAL_RANDOM = 0, 1, 2
 SCTM_NET_NUM, SCTM_NET_DEN = 0, 1
 SCTM_METHOD_SPLIT, SCTM_METHOD_REDUCED, SCTM_METHOD_SPLIT_D2 = 0, 1, 2
 SCTM_P4_FULL, SCTM_P4_HALF = 0, 1
+SCTM_JACOBI_CTA, SCTM_JACOBI_CLUSTER = 0, 1
 SCTM_MOVE_LEFT, SCTM_MOVE_RIGHT, SCTM_MOVE_UP, SCTM_MOVE_DOWN = range(4)
 
 
@@ -30,7 +31,8 @@ class SctmOpts(ctypes.Structure):
                 ('d', ctypes.c_int), ('precision', ctypes.c_int), ('grad_mode', ctypes.c_int),
                 ('svd_cutoff', ctypes.c_double), ('init_seed', ctypes.c_ulonglong),
                 ('batch', ctypes.c_int), ('cuda_stream', ctypes.c_void_p),
-                ('svd_mode', ctypes.c_int), ('method', ctypes.c_int), ('p4_mode', ctypes.c_int)]
+                ('svd_mode', ctypes.c_int), ('method', ctypes.c_int), ('p4_mode', ctypes.c_int),
+                ('jacobi', ctypes.c_int)]
 
 
 class SctmError(RuntimeError):
@@ -73,6 +75,7 @@ def load():
         'sctm_local_values': (I, [P, I, P]),
         'sctm_gemm_noalloc': (I, [P, P, P, I, I, I, P]),
         'sctm_gemm': (I, [P, P, P, I, I, I, I, P]),
+        'sctm_jacobi_svd': (I, [P, I, P, P, P, I, P]),
         'sctm_profile_kernel': (I, [P, I, P, P, P, P]),
         'sctm_iterate_batch': (I, [ctypes.POINTER(P), I, I, D, ctypes.POINTER(I),
                                    ctypes.POINTER(I), ctypes.POINTER(D)]),
@@ -192,6 +195,13 @@ def sctm_gemm_noalloc(X, Y, O, M, N, K, stream=None):
                                     ctypes.c_void_p(stream))
 
 
+def sctm_jacobi_svd(B, k, S, U, W, variant, stream=None):
+    """Jacobi SVD of the k x k column-major device matrix B (SCTM_JACOBI_CTA or _CLUSTER kernel);
+    returns the status."""
+    return load().sctm_jacobi_svd(_ptr(B), int(k), _ptr(S), _ptr(U), _ptr(W), int(variant),
+                                  ctypes.c_void_p(stream))
+
+
 def sctm_gemm(X, Y, O, M, N, K, precision, stream=None):
     """O = X Y (row-major device matrices) in the given SCTM_PREC_* form; returns the status."""
     return load().sctm_gemm(_ptr(X), _ptr(Y), _ptr(O), int(M), int(N), int(K), int(precision),
@@ -289,7 +299,8 @@ class SplitCTMRG:
     """Convenience owner of one context: create / iterate / f / g / destroy."""
 
     def __init__(self, peps, pepo, chi, T, precision=SCTM_PREC_FP64, cutoff=1e-12, seed=0,
-                 svd_mode=SCTM_SVD_QR, method=SCTM_METHOD_SPLIT, p4_mode=SCTM_P4_FULL):
+                 svd_mode=SCTM_SVD_QR, method=SCTM_METHOD_SPLIT, p4_mode=SCTM_P4_FULL,
+                 jacobi=SCTM_JACOBI_CTA):
         st, o = sctm_default_opts()
         p, D = peps.shape[0], peps.shape[1]
         o.T, o.D, o.p, o.d = float(T), D, p, pepo.shape[2]
@@ -297,6 +308,7 @@ class SplitCTMRG:
         o.svd_mode = svd_mode
         o.method = method
         o.p4_mode = p4_mode
+        o.jacobi = jacobi
         self.method = method
         self.chi, self.D, self.p, self.d = chi, D, p, pepo.shape[2]
         st, self.ctx = sctm_create(np.ascontiguousarray(peps, dtype=np.float64),

@@ -1,5 +1,6 @@
 """The C ABI without a GPU: the library builds for sm_103a, loads, exports every entry point that
 include/sctm.h declares, and its host-only entry points behave as documented."""
+import ctypes
 import os
 import re
 
@@ -62,6 +63,11 @@ def test_host_side_error_paths(lib):
     bad = sctm.SctmOpts.from_buffer_copy(o)
     bad.batch = 2
     assert sctm.sctm_create(A, O, 4, bad)[0] == sctm.SCTM_EINVAL
+    assert o.jacobi == sctm.SCTM_JACOBI_CTA
+    bad = sctm.SctmOpts.from_buffer_copy(o)
+    bad.jacobi = 2
+    assert sctm.sctm_create(A, O, 4, bad)[0] == sctm.SCTM_EINVAL
+    assert ctypes.sizeof(sctm.SctmOpts) == 80  # the header's struct: 13 fields + jacobi, padded
     assert lib.sctm_iterate(None, 1, 0.0, None, None) == sctm.SCTM_EINVAL
     assert lib.sctm_free_energy(None, None) == sctm.SCTM_EINVAL
 

@@ -42,11 +42,12 @@ def gpu_tol(g):
     return max(g['tol'], 1e-11)
 
 
-def run(g, precision, svd_mode, max_it, tol, profile=False):
+def run(g, precision, svd_mode, max_it, tol, profile=False, jacobi=sctm.SCTM_JACOBI_CTA):
     """Cold start, iterate, f and g; returns (f, g, status, iterations, emulation launches)."""
     A = peps(g)
     st, O = sctm.sctm_ising_pepo(g['T'])
-    r = sctm.SplitCTMRG(A, O, g['chi'], g['T'], precision=precision, svd_mode=svd_mode)
+    r = sctm.SplitCTMRG(A, O, g['chi'], g['T'], precision=precision, svd_mode=svd_mode,
+                        jacobi=jacobi)
     try:
         if profile:
             assert sctm.sctm_set_profiling(r.ctx, 1) == sctm.SCTM_OK
@@ -113,6 +114,37 @@ def test_converged_mixed_forms(case, prec, kind, tol):
         case, prec, it, abs(f - ref['f']), rel(gr, ref['g'])))
     assert st == sctm.SCTM_OK, (st, it)
     assert abs(f - ref['f']) <= bound, (f, ref['f'])
+
+
+@pytest.mark.parametrize('case', ['cfg2_D3_chi36', 'cfg3_D4_chi64'])
+@pytest.mark.parametrize('prec', [sctm.SCTM_PREC_FP64, sctm.SCTM_PREC_F64EMU])
+def test_converged_cluster_jacobi(case, prec):
+    """The bench's forms with the partial SVD's Jacobi SVD on a cluster of 8 CTAs
+    (SCTM_JACOBI_CLUSTER, the bench's kernel for the directional scheme; the subspaces are k = 45
+    and 80 columns, the spectra chi = 36 and 64): the same fixed point as the oracle's, f to 1e-10
+    and g to 1e-8."""
+    g = golden(case)
+    ref = g['records']['converged']
+    f, gr, st, it, _ = run(g, prec, sctm.SCTM_SVD_PARTIAL_RANDOM, 400, gpu_tol(g),
+                           jacobi=sctm.SCTM_JACOBI_CLUSTER)
+    print('%s precision %d, cluster Jacobi: %d iterations, |df|/|f| = %.2e, |dg|/|g| = %.2e' % (
+        case, prec, it, abs(f - ref['f']) / abs(ref['f']), rel(gr, ref['g'])))
+    assert st == sctm.SCTM_OK, (st, it)
+    assert abs(f - ref['f']) <= 1e-10 * abs(ref['f']), (f, ref['f'])
+    assert rel(gr, ref['g']) <= 1e-8
+
+
+def test_converged_mixed_form_cluster_jacobi():
+    """The bench's mixed form (TF32 hi/lo + FP64 polish) at D=4, chi=64 with the cluster Jacobi
+    kernel: |df| <= 1e-8, the headline metric's acceptance bound."""
+    g = golden('cfg3_D4_chi64')
+    ref = g['records']['converged']
+    f, gr, st, it, _ = run(g, sctm.SCTM_PREC_TF32X3, sctm.SCTM_SVD_PARTIAL_RANDOM, 400, gpu_tol(g),
+                           jacobi=sctm.SCTM_JACOBI_CLUSTER)
+    print('cfg3 TF32 hi/lo, cluster Jacobi: %d iterations, |df| = %.2e, |dg|/|g| = %.2e' % (
+        it, abs(f - ref['f']), rel(gr, ref['g'])))
+    assert st == sctm.SCTM_OK, (st, it)
+    assert abs(f - ref['f']) <= 1e-8, (f, ref['f'])
 
 
 @pytest.mark.parametrize('network', [sctm.SCTM_NET_NUM, sctm.SCTM_NET_DEN])
