@@ -278,15 +278,23 @@ def run_reference(args):
     for _ in range(args.warmup):
         oracle_iteration_sample(w, golden, moves='L')
     secs = []
+    spent = []
     desc = ''
     for _ in range(args.steps):
-        s, desc, _ = oracle_iteration_sample(w, golden, moves='L')
+        s, desc, t = oracle_iteration_sample(w, golden, moves='L')
         secs.append(s)
+        spent.append(t)
     value = 1.0 / float(np.mean(secs))
     line = {
         'impl': 'reference', 'metric': METRIC, 'value': value, 'unit': 'evals/s',
         'n_gpus': args.gpus, 'steps': args.steps, 'warmup': args.warmup,
-        'ms_per_step': 1000.0 / value, 'higher_is_better': True, 'scaling': 'weak',
+        # a step is the bounded sample (one left move of each network), timed as run; the value
+        # scales the sample to a converged evaluation
+        'ms_per_step': 1000.0 * float(np.mean(spent)),
+        'step': 'one left move of each network of the oracle at the workload size (a bounded '
+                'sample of one evaluation)',
+        'sec_per_eval_extrapolated': float(np.mean(secs)),
+        'higher_is_better': True, 'scaling': 'weak',
         'vs_baseline': None, 'dtype': 'f64', 'data': 'synthetic',
         'config': {'workload': workload_name(w), 'D': w['D'], 'chi': w['chi'], 'T': w['T']},
         'cpu_baseline': {'value': value, 'unit': 'evals/s', 'cores': cpu_cores(), 'kind': 'oracle',
@@ -502,13 +510,17 @@ def run_ours(args):
     # ---- the N(0,1) PEPS of the headline configuration (seed 2): it does not converge, so it is
     #      timed as split-CTMRG iterations per second over a fixed 10 iterations
     A_gauss = torch.from_numpy(inputs.random_peps(w['D'], w['seed'])).to(dev)
-    head.evaluate(A_gauss, None, max_it=2, tol=0.0)
-    torch.cuda.synchronize(dev)
-    e0.record(stream)
-    head.evaluate(A_gauss, None, max_it=10, tol=0.0)
-    e1.record(stream)
-    e1.synchronize()
-    gauss_its = 10.0 / (e0.elapsed_time(e1) * 1e-3)
+    try:
+        head.evaluate(A_gauss, None, max_it=2, tol=0.0)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        head.evaluate(A_gauss, None, max_it=10, tol=0.0)
+        e1.record(stream)
+        e1.synchronize()
+        gauss_its = 10.0 / (e0.elapsed_time(e1) * 1e-3)
+    except AssertionError as exc:  # context only: a failed status is reported, not fatal
+        torch.cuda.synchronize(dev)
+        gauss_its = {'error': str(exc)[:200]}
     head.close()
 
     # ---- the other precision forms, same workload and stopping rule
