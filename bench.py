@@ -83,7 +83,8 @@ def parse():
                          'split-d2 (whose iteration count to the tolerance rose with the '
                          'cluster kernel\'s rounding from 102 to 232)')
     ap.add_argument('--jacobi-timing', type=int, default=0,
-                    help='k: time the partial SVD\'s k x k Jacobi SVD through sctm_jacobi_svd, '
+                    help='k: time the partial SVD\'s k x k kernels (Jacobi SVD through '
+                         'sctm_jacobi_svd, a Cholesky-QR pass through sctm_chol_orth), '
                          'one-CTA kernel against the cluster kernel, on a dense Gaussian matrix '
                          '(cold solve) and a nearly diagonal graded one (warm solve)')
     ap.add_argument('--D', type=int, default=None, help='PEPS bond dimension (small captures)')
@@ -772,6 +773,29 @@ def run_jacobi(args):
                           'max_abs_dS_vs_lapack': float(np.max(np.abs(S.cpu().numpy() - ref)))}
         row['speedup'] = row['cta']['ms_median'] / row['cluster']['ms_median']
         out[name] = row
+    # one Cholesky-QR pass on the Gram matrix of a 512 x k Gaussian basis, both kernels
+    Y = rng.standard_normal((512, k))
+    G = Y.T @ Y
+    Gd = torch.from_numpy((0.5 * (G + G.T)).ravel(order='F').copy()).to(dev)
+    T = torch.zeros(k * k, dtype=torch.float64, device=dev)
+    row = {}
+    if k <= 128:
+        for vname, v in (('cta', sctm.SCTM_CHOL_CTA), ('cluster', sctm.SCTM_CHOL_CLUSTER)):
+            for _ in range(args.warmup):
+                assert sctm.sctm_chol_orth(Gd, k, 0.0, T, v, stream.cuda_stream) == sctm.SCTM_OK
+            ms = []
+            for _ in range(args.steps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                st = sctm.sctm_chol_orth(Gd, k, 0.0, T, v, stream.cuda_stream)
+                e1.record(stream)
+                e1.synchronize()
+                assert st == sctm.SCTM_OK, st
+                ms.append(e0.elapsed_time(e1))
+            row[vname] = {'ms_median': float(np.median(ms))}
+        row['speedup'] = row['cta']['ms_median'] / row['cluster']['ms_median']
+        out['cholesky_qr_pass'] = row
     print(json.dumps(out), flush=True)
 
 

@@ -368,6 +368,23 @@ sctm_status sctm_profile_kernel(sctm_ctx* ctx, int kernel, double* ms, long long
 sctm_status sctm_jacobi_svd(const double* B, int k, double* S, double* U, double* W, int variant,
                             void* cuda_stream);
 
+/* sctm_chol_orth -- one pass of the column-scaled, shifted Cholesky QR that orthonormalises the
+ * partial SVD's subspace bases (Sec. III, partial SVD by an iterative solver): for the k x k
+ * Gram matrix G = Y^T Y (column-major, symmetric), D = diag(G)^1/2, D^-1 G D^-1 + shift I = F^T F
+ * (upper F; pivots <= 1e-20 give a zero row), T = D^-1 F^-1 (upper triangular, column-major), so
+ * that Y T has orthonormal columns up to the shift and rounding.  variant SCTM_CHOL_CTA runs it
+ * in one CTA; SCTM_CHOL_CLUSTER on a cluster of 8 CTAs (the engine's choice for 32 <= k <= 128),
+ * with bit-identical results.  Diagnostic entry point: the engine calls the kernels itself.
+ *   G      device, k x k, FP64 (read only);  T  device, k x k (written)
+ *   k      1 <= k <= 160 (SCTM_CHOL_CTA); 32 <= k <= 128 (SCTM_CHOL_CLUSTER);  shift >= 0
+ *   cuda_stream  stream of the current device (NULL = legacy default); synchronised on return
+ * Pointers of the host or of another device, or sizes out of range: SCTM_EINVAL.  Returns
+ * SCTM_OK, SCTM_ENOMEM (SCTM_CHOL_CTA above k = 112 allocates one k x k scratch matrix) or
+ * SCTM_ECUDA. */
+enum { SCTM_CHOL_CTA = 0, SCTM_CHOL_CLUSTER = 1 };
+sctm_status sctm_chol_orth(const double* G, int k, double shift, double* T, int variant,
+                           void* cuda_stream);
+
 /* sctm_gemm -- O = X Y for row-major device matrices X (M x K), Y (K x N), O (M x N), run by the
  * library's contraction kernels in the arithmetic `precision` (SCTM_PREC_*): the FP64 kernel, or
  * the tensor-core kernel with TF32 / BF16 operands (optionally hi/lo split) and FP32

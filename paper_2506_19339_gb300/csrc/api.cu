@@ -762,6 +762,31 @@ static bool stream_on(cudaStream_t s, int dev) {
     return sd == dev;
 }
 
+// sctm_chol_orth: one Cholesky-QR pass of the partial SVD on device buffers, either kernel
+sctm_status sctm_chol_orth(const double* G, int k, double shift, double* T, int variant,
+                           void* cuda_stream) {
+    if (!G || !T || k < 1 || k > kPsvdMaxK || !(shift >= 0.0)) return SCTM_EINVAL;
+    if (variant != SCTM_CHOL_CTA && variant != SCTM_CHOL_CLUSTER) return SCTM_EINVAL;
+    if (variant == SCTM_CHOL_CLUSTER && !chol_cluster_fits(k)) return SCTM_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SCTM_ECUDA;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (!on_device(G, dev) || !on_device(T, dev) || !stream_on(s, dev)) return SCTM_EINVAL;
+    double* Xg = nullptr;
+    if (variant == SCTM_CHOL_CTA && k > kPsvdSmemK &&
+        cudaMalloc((void**)&Xg, (size_t)k * k * sizeof(double)) != cudaSuccess)
+        return SCTM_ENOMEM;
+    if (variant == SCTM_CHOL_CLUSTER)
+        launch_chol_orth_cluster(G, k, shift, T, s);
+    else
+        launch_chol_orth_cta(G, k, shift, T, Xg, s);
+    sctm_status st = SCTM_OK;
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+        st = SCTM_ECUDA;
+    if (Xg) cudaFree(Xg);
+    return st;
+}
+
 // sctm_jacobi_svd: the partial SVD's k x k Jacobi SVD on device buffers, either kernel
 sctm_status sctm_jacobi_svd(const double* B, int k, double* S, double* U, double* W, int variant,
                             void* cuda_stream) {

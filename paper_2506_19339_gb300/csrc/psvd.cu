@@ -38,6 +38,8 @@
 
 namespace sctm {
 
+namespace cg = cooperative_groups;
+
 namespace {
 
 constexpr int kPsvdThreads = 512;
@@ -271,6 +273,153 @@ __global__ void __launch_bounds__(kPsvdThreads)
     }
 }
 
+// ---------------------------------------------------------------------------------------------
+// The same Cholesky-QR pass spread over a thread-block cluster of kCcCluster CTAs.
+//
+// CTA c holds rows [c rp, (c + 1) rp) of the scaled Gram matrix R (rp = ceil(k / 8)).  The
+// factorisation goes panel by panel, a panel being one CTA's rows: the owner factors its rows
+// (each pivot's rank-one update applied to the panel's later rows), one cluster barrier, and
+// every later CTA applies the panel's rank-one updates to its own rows, reading the panel's rows
+// from the owner's shared memory.  Each element R[a][b] receives the updates of the pivots
+// j < a in pivot order, each as one fused multiply-add with the factor R[j][a] rinv[j]^2 -- the
+// operations of chol_orth_kernel in the same order -- so the factor is bit-identical.  Then every
+// CTA gathers F (upper triangle, transposed) and the reciprocal pivots, and computes the columns
+// c = rank, rank + 8, ... of F^-1 by the same back substitution (a warp per column), writing its
+// columns of T = D^-1 F^-1.
+// ---------------------------------------------------------------------------------------------
+constexpr int kCcCluster = 8;
+constexpr int kCcThreads = 256;
+constexpr int kCcMinK = 32;
+constexpr int kCcMaxK = 128;
+
+namespace {
+struct CcLayout {  // shared-memory carve-up of one CTA, in doubles from the base
+    int k, rp;
+    long long rl, ft, d, rinv, xcol, pl, prinv, doubles;
+    __host__ __device__ explicit CcLayout(int k_) : k(k_) {
+        rp = (k + kCcCluster - 1) / kCcCluster;
+        rl = 0;                             // own rows of R, row-major (stride k)
+        ft = rl + (long long)rp * k;        // F transposed: ft[l k + r] = F[r][l], r < l
+        d = ft + (long long)k * k;          // reciprocal column norms
+        rinv = d + k;                       // reciprocal pivots (all rows after the gather)
+        xcol = rinv + k;                    // one column of F^-1 per warp
+        pl = xcol + (long long)(kCcThreads / 32) * k;  // a copy of the current panel's rows
+        prinv = pl + (long long)rp * k;     //   and of their reciprocal pivots
+        doubles = prinv + rp;
+    }
+    __host__ __device__ size_t bytes() const { return (size_t)doubles * sizeof(double); }
+};
+}  // namespace
+
+__global__ void __cluster_dims__(kCcCluster, 1, 1) __launch_bounds__(kCcThreads)
+    chol_orth_cluster_kernel(const double* __restrict__ G, int k, double shift,
+                             double* __restrict__ T) {
+    cg::cluster_group cluster = cg::this_cluster();
+    const CcLayout L(k);
+    if (k < 1 || k > kCcMaxK) return;  // uniform over the cluster (the launcher checks)
+    extern __shared__ double sm[];
+    const int crank = (int)cluster.block_rank();
+    const int rp = L.rp;
+    const int row0 = min(k, crank * rp);
+    const int nr = min(k, row0 + rp) - row0;
+    double* Rl = sm + L.rl;
+    double* Ft = sm + L.ft;
+    double* d = sm + L.d;
+    double* rinv = sm + L.rinv;
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5,
+              nw = nt >> 5;
+    for (int i = tid; i < k; i += nt) {  // d = 1 / column norm (0 for a zero column)
+        const double g = G[i + (long long)i * k];
+        d[i] = g > 0.0 ? 1.0 / sqrt(g) : 0.0;
+    }
+    __syncthreads();
+    // own rows of the scaled Gram matrix plus the shift (G symmetric bit for bit: row a is read
+    // as G's column a)
+    for (int e = tid; e < nr * k; e += nt) {
+        const int a = row0 + e / k, b = e % k;
+        Rl[e] = G[b + (long long)a * k] * d[a] * d[b] + ((a == b && d[a] > 0.0) ? shift : 0.0);
+    }
+    __syncthreads();
+    for (int p = 0; p < kCcCluster; ++p) {
+        const int p0 = min(k, p * rp), p1 = min(k, p0 + rp);
+        if (crank == p) {  // factor this CTA's rows: pivot j, then its update of rows j+1 .. p1-1
+            for (int j = p0; j < p1; ++j) {
+                const int lj = j - row0;
+                if (tid == 0) {
+                    const double piv = Rl[lj * k + j];
+                    rinv[j] = piv > kPivotFloor ? 1.0 / sqrt(piv) : 0.0;
+                }
+                __syncthreads();
+                const double ri = rinv[j];
+                const double r2 = ri * ri;
+                for (int e = tid; e < (p1 - j - 1) * k; e += nt) {
+                    const int a = j + 1 + e / k, b = e % k;
+                    if (b < a) continue;
+                    const double fa = Rl[lj * k + a] * r2;
+                    Rl[(a - row0) * k + b] -= fa * Rl[lj * k + b];
+                }
+                __syncthreads();
+            }
+        }
+        cluster.sync();  // panel p is final (its rows are never written again)
+        if (crank > p && p1 > p0) {
+            // the panel's rows and pivots, copied from the owner's shared memory
+            double* Pl = sm + L.pl;
+            double* Pr = sm + L.prinv;
+            const double* Rp = cluster.map_shared_rank(Rl, p);
+            const double* rinvp = cluster.map_shared_rank(rinv, p);
+            for (int e = tid; e < (p1 - p0) * k; e += nt) Pl[e] = Rp[e];
+            for (int j = tid; j < p1 - p0; j += nt) Pr[j] = rinvp[p0 + j];
+            __syncthreads();
+            for (int e = tid; e < nr * k; e += nt) {
+                const int a = row0 + e / k, b = e % k;
+                if (b < a) continue;
+                double acc = Rl[e];
+                for (int j = 0; j < p1 - p0; ++j) {
+                    const double ri = Pr[j];
+                    const double pa = Pl[j * k + a] * (ri * ri);
+                    acc -= pa * Pl[j * k + b];
+                }
+                Rl[e] = acc;
+            }
+            __syncthreads();
+        }
+    }
+    // gather every reciprocal pivot and F's off-diagonal part, transposed:
+    // Ft[l k + r] = F[r][l] = R[r][l] rinv[r] (r < l)
+    for (int j = tid; j < k; j += nt) {
+        const int o = j / rp;
+        if (o != crank) rinv[j] = cluster.map_shared_rank(rinv, o)[j];
+    }
+    __syncthreads();
+    for (int e = tid; e < k * k; e += nt) {
+        const int l = e / k, r = e % k;
+        if (r < l) {
+            const int o = r / rp;
+            Ft[e] = cluster.map_shared_rank(Rl, o)[(r - o * rp) * k + l] * rinv[r];
+        }
+    }
+    __syncthreads();
+    // columns c = crank, crank + 8, ... of X = F^-1 by back substitution (the one-CTA kernel's
+    // order), then T = D^-1 X
+    double* x = sm + L.xcol + (long long)warp * k;
+    for (int c = crank + kCcCluster * warp; c < k; c += kCcCluster * nw) {
+        for (int r = lane; r < k; r += 32) x[r] = r == c ? 1.0 : 0.0;
+        __syncwarp();
+        for (int l = c; l >= 0; --l) {
+            const double xl = x[l] * rinv[l];
+            __syncwarp();
+            if (lane == 0) x[l] = xl;
+            const double* fl = Ft + (long long)l * k;
+            for (int r = lane; r < l; r += 32) x[r] -= fl[r] * xl;
+            __syncwarp();
+        }
+        for (int i = lane; i < k; i += 32) T[i + (long long)c * k] = c >= i ? x[i] * d[i] : 0.0;
+        __syncwarp();
+    }
+    cluster.sync();  // no CTA exits while another may still read its shared memory
+}
+
 // SVD of B (k x k, column-major): B W = A with orthogonal columns, B = U S W^T, U = A S^-1.
 // Writes S (k, decreasing), U and W (k x k, column-major, columns in the order of S).
 // info: 0, or 1 if the FP64 sweep limit was reached.  kp = k rounded up to even (an odd k gets a
@@ -439,8 +588,6 @@ __global__ void __launch_bounds__(kPsvdThreads)
 // and the singular values are column norms summed over the cluster.  Results agree with the
 // one-CTA kernel to rounding (the dot products are summed in another order).
 // ---------------------------------------------------------------------------------------------
-namespace cg = cooperative_groups;
-
 constexpr int kJcCluster = 8;                      // CTAs per cluster (the portable maximum)
 constexpr int kJcThreads = 256;
 constexpr int kJcMaxKp = 128;                      // the k x k Gram matrix fits in shared memory
@@ -809,8 +956,40 @@ static size_t one_cta_smem(size_t need) {
     return shared ? need : std::max(need, kExclusiveSmem);
 }
 
+bool chol_cluster_fits(int k) { return k >= kCcMinK && k <= kCcMaxK; }
+
+void launch_chol_orth_cluster(const double* G, int k, double shift, double* T, cudaStream_t s) {
+    const size_t smem = one_cta_smem(CcLayout(k).bytes());
+    static std::once_flag once;
+    std::call_once(once, [] {
+        const size_t mx = std::max(CcLayout(kCcMaxK).bytes(), kExclusiveSmem);
+        cudaFuncSetAttribute(chol_orth_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)mx);
+    });
+    chol_orth_cluster_kernel<<<kCcCluster, kCcThreads, smem, s>>>(G, k, shift, T);
+}
+
+// The engine's Cholesky-QR pass: the cluster kernel where the order fits it (bit-identical
+// results), unless SCTM_CHOL=cta selects the one-CTA kernel everywhere (for comparison).
+static bool cluster_chol_enabled() {
+    static const bool on = [] {
+        const char* v = getenv("SCTM_CHOL");
+        return !(v && v[0] == 'c' && v[1] == 't' && v[2] == 'a');
+    }();
+    return on;
+}
+
 void launch_chol_orth(const double* G, int k, double shift, double* T, double* Xg,
                       cudaStream_t s) {
+    if (cluster_chol_enabled() && chol_cluster_fits(k)) {
+        launch_chol_orth_cluster(G, k, shift, T, s);
+        return;
+    }
+    launch_chol_orth_cta(G, k, shift, T, Xg, s);
+}
+
+void launch_chol_orth_cta(const double* G, int k, double shift, double* T, double* Xg,
+                          cudaStream_t s) {
     const size_t smem = one_cta_smem(chol_orth_smem(k, Xg != nullptr));
     static std::once_flag once;
     std::call_once(once, [] {

@@ -88,8 +88,15 @@ void launch_copy(const double* src, double* dst, long long n, cudaStream_t s);
 constexpr int kPsvdSmemK = 112;  // subspaces up to this size keep all k x k work in shared memory
 constexpr int kPsvdMaxK = 160;   // largest subspace: above kPsvdSmemK one k x k matrix of each
                                  // one-CTA kernel lives in a global scratch buffer
+// Cholesky-QR pass on the k x k Gram matrix G: the cluster kernel where chol_cluster_fits(k)
+// (bit-identical to the one-CTA kernel; SCTM_CHOL=cta in the environment forces the one-CTA
+// kernel), the one-CTA kernel otherwise (Xg: its global scratch above kPsvdSmemK, else null)
 void launch_chol_orth(const double* G, int k, double shift, double* T, double* Xg,
                       cudaStream_t s);
+void launch_chol_orth_cta(const double* G, int k, double shift, double* T, double* Xg,
+                          cudaStream_t s);
+bool chol_cluster_fits(int k);  // 32 <= k <= 128
+void launch_chol_orth_cluster(const double* G, int k, double shift, double* T, cudaStream_t s);
 void launch_refill(double* V, int n, int k, const double* S, unsigned long long seed,
                    cudaStream_t s);
 // Jacobi SVD of the k x k matrix B: the cluster kernel if `cluster` and jacobi_cluster_fits(k),

@@ -23,6 +23,7 @@ SCTM_NET_NUM, SCTM_NET_DEN = 0, 1
 SCTM_METHOD_SPLIT, SCTM_METHOD_REDUCED, SCTM_METHOD_SPLIT_D2 = 0, 1, 2
 SCTM_P4_FULL, SCTM_P4_HALF = 0, 1
 SCTM_JACOBI_CTA, SCTM_JACOBI_CLUSTER = 0, 1
+SCTM_CHOL_CTA, SCTM_CHOL_CLUSTER = 0, 1
 SCTM_MOVE_LEFT, SCTM_MOVE_RIGHT, SCTM_MOVE_UP, SCTM_MOVE_DOWN = range(4)
 
 
@@ -76,6 +77,7 @@ def load():
         'sctm_gemm_noalloc': (I, [P, P, P, I, I, I, P]),
         'sctm_gemm': (I, [P, P, P, I, I, I, I, P]),
         'sctm_jacobi_svd': (I, [P, I, P, P, P, I, P]),
+        'sctm_chol_orth': (I, [P, I, D, P, I, P]),
         'sctm_profile_kernel': (I, [P, I, P, P, P, P]),
         'sctm_iterate_batch': (I, [ctypes.POINTER(P), I, I, D, ctypes.POINTER(I),
                                    ctypes.POINTER(I), ctypes.POINTER(D)]),
@@ -193,6 +195,13 @@ def sctm_gemm_noalloc(X, Y, O, M, N, K, stream=None):
     """O = X Y (row-major device tensors, FP64) without any device allocation in the library."""
     return load().sctm_gemm_noalloc(_ptr(X), _ptr(Y), _ptr(O), int(M), int(N), int(K),
                                     ctypes.c_void_p(stream))
+
+
+def sctm_chol_orth(G, k, shift, T, variant, stream=None):
+    """One Cholesky-QR pass on the k x k column-major device Gram matrix G (SCTM_CHOL_CTA or
+    _CLUSTER kernel) into T; returns the status."""
+    return load().sctm_chol_orth(_ptr(G), int(k), float(shift), _ptr(T), int(variant),
+                                 ctypes.c_void_p(stream))
 
 
 def sctm_jacobi_svd(B, k, S, U, W, variant, stream=None):
