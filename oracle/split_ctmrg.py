@@ -484,7 +484,37 @@ def renormalise(env, A, O, B, P):
 # the left move (Sec. III.B, Fig. 5): insertion, absorption, six-projector truncation
 # ----------------------------------------------------------------------------------------------
 
-def left_move(env, A, O, B, chi, cutoff=1e-12, info=None, normalise=True):
+def opposite_stage1(left):
+    """The opposite boundary's stage-1 pairs as the images of this boundary's under the rotation
+    by 180 degrees with ket <-> bra, the relabelling that turns the left move into the right move
+    (``frame_rotate``; likewise the up move into the down move).  The Appendix's captions of
+    projectors 4-6 take the right column's stage-1 pairs from the right move; in the D2-symmetric
+    scheme that move is this one's image, so P^R_1T = P_1B, P^R_1B = P_1T, P^R_2T = P_3B,
+    P^R_2B = P_3T, P^R_3T = P_2B, P^R_3B = P_2T.  The rotation puts the right column's alpha cut
+    onto the left column's alpha cut, its kappa cut (ket | int) onto the left iota cut
+    (int | bra) and its iota cut onto the left kappa cut, with the right environment bond onto
+    the left one, the ket lines onto the bra lines and the physical line A-O onto O-A-bar.  Leg
+    orders:
+        right alpha (xr, A_v)      <- left alpha (xl, B_v)
+        right kappa (xr, A.d, s)   <- left iota  (xl, s', B.u)
+        right iota  (xr, A.d, s')  <- left kappa (xl, s, B.u)"""
+    PBa, PTa, Sa = left['alpha']
+    PBk, PTk, Sk = left['kappa']
+    PBi, PTi, Si = left['iota']
+    return {
+        'alpha': (PTa.transpose(1, 2, 0), PBa.transpose(2, 0, 1), Sa),
+        'kappa': (PTi.transpose(1, 3, 2, 0), PBi.transpose(3, 0, 2, 1), Si),
+        'iota': (PTk.transpose(1, 3, 2, 0), PBk.transpose(3, 0, 2, 1), Sk),
+    }
+
+
+def stage1_left(env, A, O, B, chi, cutoff=1e-12):
+    """This move's own stage-1 pairs (P1, P2, P3 on the bra-related legs of its column)."""
+    halves = one_column_halves(env, A, O, B)
+    return {cut: projector_pair(U, L, T_AXES_LEFT[cut], chi, cutoff) for cut, (U, L) in halves.items()}
+
+
+def left_move(env, A, O, B, chi, cutoff=1e-12, info=None, normalise=True, right=None):
     """One left move.  Returns the renormalised, Frobenius-normalised (C1', [T4'^k, T4'^i, T4'^b],
     C4').
 
@@ -494,9 +524,15 @@ def left_move(env, A, O, B, chi, cutoff=1e-12, info=None, normalise=True):
     left column is already renormalised by the stage-1 pair and whose right column is
     renormalised by the mirror-image stage-1 pair of the opposite boundary (paper: "full"
     projector 4 and the 1x2 cells of projectors 5 and 6, with P^R computed in the same move).
+    right: the opposite boundary's stage-1 pairs to use instead (``opposite_stage1`` of the
+    opposite move's pairs: the paper's reading, P^R from the right move); None computes them here.
     """
     halves = one_column_halves(env, A, O, B)
-    left, right = stage1_projectors(halves, chi, cutoff)
+    if right is None:
+        left, right = stage1_projectors(halves, chi, cutoff)
+    else:
+        left = {cut: projector_pair(U, L, T_AXES_LEFT[cut], chi, cutoff)
+                for cut, (U, L) in halves.items()}
     halves2 = two_column_halves(env, A, O, B, left, right)
     stage2 = {cut: projector_pair(U2, L2, (0, 1, 2), chi, cutoff) for cut, (U2, L2) in halves2.items()}
     P = composite_projectors(left, stage2)
@@ -512,16 +548,50 @@ def left_move(env, A, O, B, chi, cutoff=1e-12, info=None, normalise=True):
         info['projectors'] = P
         info['halves'] = halves
         info['halves2'] = halves2
+        info['left'], info['right'] = left, right
     return C1n, T4n, C4n
 
 
-def move(env, A, O, B, which, chi, cutoff=1e-12):
-    """One directional move ('L', 'R', 'U' or 'D') on the stored environment."""
+def move(env, A, O, B, which, chi, cutoff=1e-12, right=None, info=None):
+    """One directional move ('L', 'R', 'U' or 'D') on the stored environment (right, info: as
+    ``left_move``, in the move's own frame)."""
     e, a, o, b = to_frame(which, env, A, O, B)
-    C1n, T4n, C4n = left_move(e, a, o, b, chi, cutoff)
+    C1n, T4n, C4n = left_move(e, a, o, b, chi, cutoff, info=info, right=right)
     e = dict(e)
     e['C1'], e['T4'], e['C4'] = C1n, T4n, C4n
     return from_frame(which, e)
+
+
+OPPOSITE_MOVE = {'L': 'R', 'R': 'L', 'U': 'D', 'D': 'U'}
+UPDATED = {'L': ('C1', 'C4', 'T4'), 'R': ('C2', 'C3', 'T2'), 'U': ('C1', 'C2', 'T1'),
+           'D': ('C3', 'C4', 'T3')}  # the stored tensors each move renormalises
+
+
+def paired_move(env, A, O, B, pair, chi, cutoff=1e-12, svd_count=None):
+    """Two opposite moves ('LR' or 'UD') on one environment: each move's stage-1 pairs are computed
+    once and serve both as its own (P1-P3) and, mapped by ``opposite_stage1``, as the other move's
+    P^R (the Appendix takes P^R from the right move); each move's stage-2 pairs and its
+    renormalisation use the environment both started from.  The moves renormalise disjoint
+    tensors (UPDATED), so the results are merged.  Twelve SVDs per pair, where two sequential
+    moves with P^R in the move take eighteen."""
+    w1, w2 = pair
+    frames = {w: to_frame(w, env, A, O, B) for w in pair}
+    left = {w: stage1_left(*frames[w], chi, cutoff) for w in pair}
+    out = dict(env)
+    for w, other in ((w1, w2), (w2, w1)):
+        e, a, o, b = frames[w]
+        inf = {}
+        # left_move recomputes this move's stage-1 pairs from the same halves (same values)
+        C1n, T4n, C4n = left_move(e, a, o, b, chi, cutoff, info=inf,
+                                  right=opposite_stage1(left[other]))
+        e2 = dict(e)
+        e2['C1'], e2['T4'], e2['C4'] = C1n, T4n, C4n
+        new = from_frame(w, e2)
+        for key in UPDATED[w]:
+            out[key] = new[key]
+    if svd_count is not None:
+        svd_count[0] += 12
+    return out
 
 
 def ctm_spectrum(env):
@@ -532,16 +602,37 @@ def ctm_spectrum(env):
     return np.linalg.svd(rho, compute_uv=False)
 
 
-def iterate(env, A, O, B, chi, max_iter, tol=None, cutoff=1e-12, S_prev=None, trace=None):
+def iterate(env, A, O, B, chi, max_iter, tol=None, cutoff=1e-12, S_prev=None, trace=None,
+            pr='in-move', svd_count=None):
     """Power iteration of the environment: each iteration is the left, right, up and down moves in
     that order (Sec. III.B); stop once ||S[i+1] - S[i]||_2 < tol (Sec. III.D).  Spectra shorter
-    than chi are padded with zeros.  Returns (env, iterations done, last dS, spectrum)."""
+    than chi are padded with zeros.  Returns (env, iterations done, last dS, spectrum).
+    pr: where each move's opposite-boundary stage-1 pairs (P^R) come from -- 'in-move' (their
+    own SVDs in the move, nine SVDs per move) or 'opposite-move' (the Appendix's reading: the
+    pairs of the latest opposite move, left <-> right and up <-> down, mapped by
+    ``opposite_stage1``; six SVDs per move once the opposite move has run) or 'paired' (left and
+    right, then up and down, as ``paired_move`` on one environment each: P^R is the opposite
+    move's pair of the same environment, twelve SVDs per pair).  svd_count: a list whose first
+    entry is increased by the number of SVDs made."""
     S_old = np.zeros(chi) if S_prev is None else S_prev
     dS = np.inf
     it = 0
+    last = {}
     for it in range(1, max_iter + 1):
-        for w in 'LRUD':
-            env = move(env, A, O, B, w, chi, cutoff)
+        if pr == 'paired':
+            for pair in ('LR', 'UD'):
+                env = paired_move(env, A, O, B, pair, chi, cutoff, svd_count)
+        for w in ('LRUD' if pr != 'paired' else ''):
+            right = None
+            if pr == 'opposite-move' and OPPOSITE_MOVE[w] in last:
+                right = opposite_stage1(last[OPPOSITE_MOVE[w]])
+            elif pr not in ('in-move', 'opposite-move', 'paired'):
+                raise ValueError(pr)
+            inf = {}
+            env = move(env, A, O, B, w, chi, cutoff, right=right, info=inf)
+            last[w] = inf['left']
+            if svd_count is not None:
+                svd_count[0] += 6 if right is not None else 9
         S = np.zeros(chi)
         s = ctm_spectrum(env)
         S[:len(s)] = s[:chi]
@@ -601,13 +692,15 @@ def ket_environment(env, loc):
     return _c2('awlesy,wyr->saler', X, T2[KET])
 
 
-def evaluate(A, O_num, O_den, T, chi, max_iter, tol=None, cutoff=1e-12, env_num=None, env_den=None):
+def evaluate(A, O_num, O_den, T, chi, max_iter, tol=None, cutoff=1e-12, env_num=None, env_den=None,
+             pr='in-move'):
     """f and g for PEPS A at temperature T (Eqs. "free energy expression" and "gradient
     expression"):
         f = -T (ln kappa_num - ln kappa_den),
         g = 2 d f / d A-bar = -2T (E_num / Z11_num - E_den / Z11_den).
     The numerator <psi|T|psi> uses the Ising PEPO, the denominator <psi|psi> the identity PEPO.
-    Each network is iterated from the cold start (or from the given environment)."""
+    Each network is iterated from the cold start (or from the given environment); pr as
+    ``iterate``."""
     A = np.asarray(A, dtype=np.float64)
     B = A
     p, D = A.shape[0], A.shape[1]
@@ -615,11 +708,12 @@ def evaluate(A, O_num, O_den, T, chi, max_iter, tol=None, cutoff=1e-12, env_num=
     for name, O, e0 in (('num', O_num, env_num), ('den', O_den, env_den)):
         d = O.shape[2]
         env = init_env(chi, D, d) if e0 is None else copy_env(e0)
-        env, it, dS, S = iterate(env, A, O, B, chi, max_iter, tol, cutoff)
+        svds = [0]
+        env, it, dS, S = iterate(env, A, O, B, chi, max_iter, tol, cutoff, pr=pr, svd_count=svds)
         loc = local_contractions(env, A, O, B)
         E = bra_environment(env, loc)
         res[name] = {'env': env, 'iters': it, 'dS': dS, 'S': S, 'lnk': ln_kappa(loc),
-                     'Z11': loc['Z11'], 'E': E, 'loc': loc}
+                     'Z11': loc['Z11'], 'E': E, 'loc': loc, 'svds': svds[0]}
     beta_f = -(res['num']['lnk'] - res['den']['lnk'])
     f = T * beta_f if np.isfinite(T) else np.nan
     g = -2.0 * (res['num']['E'] / res['num']['Z11'] - res['den']['E'] / res['den']['Z11'])

@@ -147,25 +147,10 @@ def enlarged_c4(env, A, O, B):
     return X.transpose(5, 6, 3, 1, 0, 7, 4, 2)
 
 
-def mirror_stage1(left):
-    """The opposite boundary's stage-1 pairs as the images of this boundary's under the rotation
-    by 180 degrees with ket <-> bra (Appendix, captions of projectors 4-6: in the D2-symmetric
-    scheme P^R_1T = P_1B, P^R_1B = P_1T, P^R_2T = P_3B, P^R_2B = P_3T, P^R_3T = P_2B,
-    P^R_3B = P_2T).  The rotation puts the right column's alpha cut onto the left column's alpha
-    cut, its kappa cut (ket | int) onto the left iota cut (int | bra) and its iota cut onto the
-    left kappa cut, with the right environment bond onto the left one, the ket lines onto the
-    bra lines and the physical line A-O onto O-A-bar.  Leg orders as ``split_ctmrg``:
-        right alpha (xr, A_v)      <- left alpha (xl, B_v)
-        right kappa (xr, A.d, s)   <- left iota  (xl, s', B.u)
-        right iota  (xr, A.d, s')  <- left kappa (xl, s, B.u)"""
-    PBa, PTa, Sa = left['alpha']
-    PBk, PTk, Sk = left['kappa']
-    PBi, PTi, Si = left['iota']
-    return {
-        'alpha': (PTa.transpose(1, 2, 0), PBa.transpose(2, 0, 1), Sa),
-        'kappa': (PTi.transpose(1, 3, 2, 0), PBi.transpose(3, 0, 2, 1), Si),
-        'iota': (PTk.transpose(1, 3, 2, 0), PBk.transpose(3, 0, 2, 1), Sk),
-    }
+# the opposite boundary's stage-1 pairs as the 180-degree-rotation images of this boundary's (the
+# geometry is the directional scheme's; the D2 symmetry makes them the opposite boundary's pairs
+# of the same environment)
+mirror_stage1 = sc.opposite_stage1
 
 
 def half_p4_halves(env, A, O, B, left):

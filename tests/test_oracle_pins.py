@@ -427,6 +427,72 @@ def test_ctm_spectrum_is_a_gauge_invariant_plaquette_product():
         assert moved > 1e-6
 
 
+def _composite(pair):
+    PB, PT = pair[0], pair[1]
+    return np.tensordot(PB, PT, axes=([PB.ndim - 1], [0]))
+
+
+def test_opposite_move_pairs_are_the_in_move_pairs():
+    """Appendix, captions of projectors 4-6: the left move's P^R is the right move's stage-1 pair.
+    On one environment of a PEPS without the D2 symmetry (D=2, chi=6, three iterations from the
+    cold start) the right move's own stage-1 pairs, mapped by ``opposite_stage1`` (180-degree
+    rotation with ket <-> bra: alpha -> alpha, kappa -> iota, iota -> kappa), equal the pairs the
+    left move computes for the right column: singular values to 1e-13 of the largest, oblique
+    projectors P_B P_T to 1e-10 (the pseudo-inverse square roots amplify rounding).  Mapping the
+    kappa pair onto kappa instead fails."""
+    T, D, chi = 4.5, 2, 6
+    A = inputs.perturbed_product_peps(D, 3, eps=0.3)
+    O = ising.ising_pepo(1.0 / T)
+    env, *_ = sc.iterate(sc.init_env(chi, D, 2), A, O, A, chi, 3)
+    inf_l, inf_r = {}, {}
+    sc.move(env, A, O, A, 'L', chi, info=inf_l)
+    sc.move(env, A, O, A, 'R', chi, info=inf_r)
+    mapped = sc.opposite_stage1(inf_r['left'])
+    for cut in ('alpha', 'kappa', 'iota'):
+        want = inf_l['right'][cut]
+        S, Sm = want[2], mapped[cut][2]
+        assert np.max(np.abs(S - Sm)) <= 1e-13 * S[0], cut
+        P, Pm = _composite(want), _composite(mapped[cut])
+        assert np.linalg.norm(P - Pm) <= 1e-10 * np.linalg.norm(P), cut
+    PBk, PTk, _ = inf_r['left']['kappa']
+    planted = (PTk.transpose(1, 3, 2, 0), PBk.transpose(3, 0, 2, 1))
+    P = _composite(inf_l['right']['kappa'])
+    assert np.linalg.norm(P - _composite(planted)) > 1e-3 * np.linalg.norm(P)
+
+
+def test_paired_moves_are_the_single_moves_of_one_environment():
+    """``paired_move`` (left and right moves on one environment, each taking its P^R from the
+    other's stage-1 pairs): the tensors each move renormalises are those of that move made alone
+    on the same environment with P^R computed in the move, up to the sign gauge of the new bonds
+    (the stage-2 SVDs fix their signs from vectors that P^R's own sign gauge enters): equal
+    magnitudes (1e-10), and the same gauge-invariant values -- the convergence spectrum and
+    ln kappa (1e-12) of the assembled environments; tensors neither move touches are the input's."""
+    T, D, chi = 4.5, 2, 6
+    A = inputs.perturbed_product_peps(D, 3, eps=0.3)
+    O = ising.ising_pepo(1.0 / T)
+    env, *_ = sc.iterate(sc.init_env(chi, D, 2), A, O, A, chi, 3)
+    for pair in ('LR', 'UD'):
+        out = sc.paired_move(env, A, O, A, pair, chi)
+        assembled = dict(env)
+        for w in pair:
+            alone = sc.move(env, A, O, A, w, chi)
+            for key in sc.UPDATED[w]:
+                assembled[key] = alone[key]
+                xs = [alone[key]] if key[0] == 'C' else alone[key]
+                ys = [out[key]] if key[0] == 'C' else out[key]
+                for x, y in zip(xs, ys):
+                    assert np.linalg.norm(np.abs(x) - np.abs(y)) <= 1e-10 * np.linalg.norm(x), key
+        S1, S2 = sc.ctm_spectrum(assembled), sc.ctm_spectrum(out)
+        assert np.max(np.abs(S1 - S2)) <= 1e-12 * S1[0], pair
+        l1 = sc.ln_kappa(sc.local_contractions(assembled, A, O, A))
+        l2 = sc.ln_kappa(sc.local_contractions(out, A, O, A))
+        assert abs(l1 - l2) <= 1e-12 * abs(l1), pair
+        touched = set(sc.UPDATED[pair[0]]) | set(sc.UPDATED[pair[1]])
+        for key in ('C1', 'C2', 'C3', 'C4', 'T1', 'T2', 'T3', 'T4'):
+            if key not in touched:
+                assert out[key] is env[key]
+
+
 def test_oracle_flop_counter():
     """The oracle's algorithmic FLOP count: 2 x the product of every distinct label's dimension
     for a pairwise contraction (2 M N K for a matrix product, batch labels included)."""
