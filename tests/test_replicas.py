@@ -43,3 +43,25 @@ def test_combine_ranks_single_process():
     sys.path.insert(0, ROOT)
     import bench
     assert bench.combine_ranks(12.5, 20.0, None, 'cpu') == (12.5, 20.0)
+
+
+def test_reference_arm_prints_the_contract_line():
+    """`bench.py --impl reference` (the FP64 oracle on the host cores, a bounded sample per step)
+    prints one JSON line with the contract's keys; its ms_per_step is the sample's measured time
+    and the value scales the sample to a converged evaluation (a small workload here)."""
+    import json
+    import subprocess
+    out = subprocess.run([sys.executable, os.path.join(ROOT, 'bench.py'), '--impl', 'reference',
+                          '--steps', '1', '--warmup', '0', '--D', '2', '--chi', '6'],
+                         cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stderr
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    for key in ('impl', 'metric', 'value', 'unit', 'n_gpus', 'steps', 'warmup', 'ms_per_step',
+                'higher_is_better', 'scaling', 'vs_baseline', 'dtype', 'data', 'config',
+                'cpu_baseline', 'e2e'):
+        assert key in line, key
+    assert line['impl'] == 'reference' and line['unit'] == 'evals/s' and line['value'] > 0
+    assert line['cpu_baseline']['value'] == line['value'] and line['cpu_baseline']['kind'] == 'oracle'
+    assert line['e2e']['h2d_bytes_per_step'] == 0 and line['e2e']['d2h_bytes_per_step'] == 0
+    # the step is the bounded sample, much shorter than the evaluation it is scaled to
+    assert line['ms_per_step'] < 1000.0 * line['sec_per_eval_extrapolated']
