@@ -10,7 +10,8 @@
 //     B = Z^T Q_z = Q_y^T M Q_z  (k x k),  B = U_B S V_B^T
 //     M ~ (Q_y U_B) S (Q_z V_B)^T.
 // The products with M, the Gram matrices and the basis updates run on the contraction kernel;
-// the kernels here do the k x k work in one CTA each:
+// the kernels here do the k x k work, each in one CTA, and (further down) each also on a
+// thread-block cluster of 8 CTAs that spreads the FP64 work over 8 SMs:
 //   * chol_orth_kernel: one pass of column-scaled Cholesky QR.  With G = Y^T Y and D the column
 //     norms, D^-1 G D^-1 + shift I = R^T R; it returns T = D^-1 R^-1, so that Y T is orthonormal
 //     up to the shift and rounding.  Column scaling keeps the relative accuracy of small
