@@ -438,6 +438,85 @@ def two_column_halves(env, A, O, B, left, right):
     return out
 
 
+# ----------------------------------------------------------------------------------------------
+# enlarged corners and the half projector 4 (Appendix, projector 4(b))
+# ----------------------------------------------------------------------------------------------
+
+def enlarged_c1(env, A, O, B):
+    """C1 with one column and one row absorbed: C1, the top edge T1^{k,i,b} of the column, the left
+    edge T4^{k,i,b} of the row and the site's three layers, as
+        Ct[h, A.r, O.r, B.r, v, A.d, O.d, B.d]
+    (h: the top chain's bond right of the column; v: the left chain's bond below the row)."""
+    T1k, T1i, T1b = env['T1']
+    T4k, T4i, T4b = env['T4']
+    X = _c2('aw,acp->wcp', env['C1'], T1k)
+    X = _c2('wcp,ceo->wepo', X, T1i)
+    X = _c2('wepo,ehq->whpoq', X, T1b)
+    X = _c2('whpoq,wxl->hpoqxl', X, T4k)
+    X = _c2('hpoqxl,splDR->hoqxsDR', X, A)
+    X = _c2('hoqxsDR,xym->hoqsDRym', X, T4i)
+    X = _c2('hoqsDRym,tsomEF->hqDRytEF', X, O)
+    X = _c2('hqDRytEF,yvn->hqDRtEFvn', X, T4b)
+    X = _c2('hqDRtEFvn,tqnGH->hDREFvGH', X, B)
+    return X.transpose(0, 2, 4, 7, 5, 1, 3, 6)
+
+
+def enlarged_c4(env, A, O, B):
+    """C4 with one column and one row absorbed: C4, the bottom edge T3^{k,i,b} of the column, the
+    left edge T4^{k,i,b} of the row and the site, as
+        Ct[v, A.u, O.u, B.u, h, A.r, O.r, B.r]
+    (v: the left chain's bond above the row; h: the bottom chain's bond right of the column)."""
+    T3k, T3i, T3b = env['T3']
+    T4k, T4i, T4b = env['T4']
+    X = _c2('aw,acp->wcp', env['C4'], T3k)
+    X = _c2('wcp,ceo->wepo', X, T3i)
+    X = _c2('wepo,ehq->whpoq', X, T3b)
+    X = _c2('whpoq,ywn->hpoqyn', X, T4b)
+    X = _c2('hpoqyn,tUnqR->hpoytUR', X, B)
+    X = _c2('hpoytUR,xym->hpotURxm', X, T4i)
+    X = _c2('hpotURxm,tsVmoS->hpURxsVS', X, O)
+    X = _c2('hpURxsVS,vxl->hpURsVSvl', X, T4k)
+    X = _c2('hpURsVSvl,sWlpQ->hURVSvWQ', X, A)
+    return X.transpose(5, 6, 3, 1, 0, 7, 4, 2)
+
+
+def half_p4_halves(env, A, O, B, left, col_T=None, col_B=None):
+    """(rho_T, rho_B) of the half projector 4 (Appendix, projector 4(b)): the 2x1 patch of the
+    two enlarged left corners, the bra lines of both their legs renormalised by projector 1 --
+    this move's P_1T / P_1B on the row cut, and on the column cut the up / down moves' projector 1:
+    col_T = the up move's P_1T[k, xl, B_v] for the upper corner, col_B = the down move's
+    P_1B[xl, B_v, k] for the lower one, each in its own move's frame (in the down move's frame ket
+    and bra trade places, so there it acts on the ket line A.r).  In the D2-symmetric scheme
+    both are this move's own pair (the defaults).  Leg orders:
+        rho_T (k1, A.d, O.d | k2, A.r, O.r)    rho_B (k1, A.u, O.u | k2, B.r, O.r)
+    the first three legs cut by projector 4, the last three remaining."""
+    PBa, PTa, _ = left['alpha']                      # [xl, B_v, k], [k, xl, B_v]
+    cT = PTa if col_T is None else col_T
+    cB = PBa if col_B is None else col_B
+    Ct1 = enlarged_c1(env, A, O, B)                   # [h, A.r, O.r, B.r, v, A.d, O.d, B.d]
+    X = _c2('hpqrvabc,kvc->hpqrkab', Ct1, PTa)
+    U = _c2('hpqrkab,jhr->kabjpq', X, cT)
+    Ct4 = enlarged_c4(env, A, O, B)                   # [v, A.u, O.u, B.u, h, A.r, O.r, B.r]
+    X = _c2('vabchpqr,vck->kabhpqr', Ct4, PBa)
+    L = _c2('kabhpqr,hpj->kabjrq', X, cB)
+    return U, L
+
+
+def perpendicular_alpha_pairs(env, A, O, B, chi, cutoff=1e-12):
+    """The up and down moves' stage-1 alpha pairs (P1) of this environment, each computed in its
+    own frame (the half projector 4 of the directional scheme takes them from the same
+    environment, as P^R is taken; see ``left_move``)."""
+    out = []
+    for w in ('U', 'D'):
+        e, a, o, b = to_frame(w, env, A, O, B)
+        Ct = top_block(e['C1'], e['T1'], e['C2'])
+        Cb = bottom_block(e['C4'], e['T3'], e['C3'])
+        Ua = upper_halves(Ct, e['T4'], e['T2'], a, o, b)[2]
+        La = lower_halves(Cb, e['T4'], e['T2'], a, o, b)[2]
+        out.append(projector_pair(Ua, La, T_AXES_LEFT['alpha'], chi, cutoff))
+    return out
+
+
 def composite_projectors(left, stage2):
     """Stage-1 then stage-2 projector of each cut, as one tensor on the cut's legs:
         P_alpha,B[xl, A_v, O_v, B_v, k],     P_alpha,T[k, xl, A_v, O_v, B_v]
@@ -514,7 +593,7 @@ def stage1_left(env, A, O, B, chi, cutoff=1e-12):
     return {cut: projector_pair(U, L, T_AXES_LEFT[cut], chi, cutoff) for cut, (U, L) in halves.items()}
 
 
-def left_move(env, A, O, B, chi, cutoff=1e-12, info=None, normalise=True, right=None):
+def left_move(env, A, O, B, chi, cutoff=1e-12, info=None, normalise=True, right=None, p4='full'):
     """One left move.  Returns the renormalised, Frobenius-normalised (C1', [T4'^k, T4'^i, T4'^b],
     C4').
 
@@ -526,6 +605,9 @@ def left_move(env, A, O, B, chi, cutoff=1e-12, info=None, normalise=True, right=
     projector 4 and the 1x2 cells of projectors 5 and 6, with P^R computed in the same move).
     right: the opposite boundary's stage-1 pairs to use instead (``opposite_stage1`` of the
     opposite move's pairs: the paper's reading, P^R from the right move); None computes them here.
+    p4: 'full' (the 2x2-cell patch) or 'half' (the 2x1-cell patch of the two enlarged corners,
+    its column cuts renormalised by the up and down moves' P1 computed here from the same
+    environment, ``perpendicular_alpha_pairs``).
     """
     halves = one_column_halves(env, A, O, B)
     if right is None:
@@ -534,6 +616,11 @@ def left_move(env, A, O, B, chi, cutoff=1e-12, info=None, normalise=True, right=
         left = {cut: projector_pair(U, L, T_AXES_LEFT[cut], chi, cutoff)
                 for cut, (U, L) in halves.items()}
     halves2 = two_column_halves(env, A, O, B, left, right)
+    if p4 == 'half':
+        up, down = perpendicular_alpha_pairs(env, A, O, B, chi, cutoff)
+        halves2['alpha'] = half_p4_halves(env, A, O, B, left, up[1], down[0])
+    elif p4 != 'full':
+        raise ValueError(p4)
     stage2 = {cut: projector_pair(U2, L2, (0, 1, 2), chi, cutoff) for cut, (U2, L2) in halves2.items()}
     P = composite_projectors(left, stage2)
     C1n, T4n, C4n = renormalise(env, A, O, B, P)
@@ -552,11 +639,11 @@ def left_move(env, A, O, B, chi, cutoff=1e-12, info=None, normalise=True, right=
     return C1n, T4n, C4n
 
 
-def move(env, A, O, B, which, chi, cutoff=1e-12, right=None, info=None):
-    """One directional move ('L', 'R', 'U' or 'D') on the stored environment (right, info: as
+def move(env, A, O, B, which, chi, cutoff=1e-12, right=None, info=None, p4='full'):
+    """One directional move ('L', 'R', 'U' or 'D') on the stored environment (right, info, p4: as
     ``left_move``, in the move's own frame)."""
     e, a, o, b = to_frame(which, env, A, O, B)
-    C1n, T4n, C4n = left_move(e, a, o, b, chi, cutoff, info=info, right=right)
+    C1n, T4n, C4n = left_move(e, a, o, b, chi, cutoff, info=info, right=right, p4=p4)
     e = dict(e)
     e['C1'], e['T4'], e['C4'] = C1n, T4n, C4n
     return from_frame(which, e)
@@ -603,7 +690,7 @@ def ctm_spectrum(env):
 
 
 def iterate(env, A, O, B, chi, max_iter, tol=None, cutoff=1e-12, S_prev=None, trace=None,
-            pr='in-move', svd_count=None):
+            pr='in-move', svd_count=None, p4='full'):
     """Power iteration of the environment: each iteration is the left, right, up and down moves in
     that order (Sec. III.B); stop once ||S[i+1] - S[i]||_2 < tol (Sec. III.D).  Spectra shorter
     than chi are padded with zeros.  Returns (env, iterations done, last dS, spectrum).
@@ -613,7 +700,8 @@ def iterate(env, A, O, B, chi, max_iter, tol=None, cutoff=1e-12, S_prev=None, tr
     ``opposite_stage1``; six SVDs per move once the opposite move has run) or 'paired' (left and
     right, then up and down, as ``paired_move`` on one environment each: P^R is the opposite
     move's pair of the same environment, twelve SVDs per pair).  svd_count: a list whose first
-    entry is increased by the number of SVDs made."""
+    entry is increased by the number of SVDs made.  p4: projector 4's patch, as ``left_move``
+    (with 'half' every move makes two more SVDs, the up and down moves' P1)."""
     S_old = np.zeros(chi) if S_prev is None else S_prev
     dS = np.inf
     it = 0
@@ -629,10 +717,10 @@ def iterate(env, A, O, B, chi, max_iter, tol=None, cutoff=1e-12, S_prev=None, tr
             elif pr not in ('in-move', 'opposite-move', 'paired'):
                 raise ValueError(pr)
             inf = {}
-            env = move(env, A, O, B, w, chi, cutoff, right=right, info=inf)
+            env = move(env, A, O, B, w, chi, cutoff, right=right, info=inf, p4=p4)
             last[w] = inf['left']
             if svd_count is not None:
-                svd_count[0] += 6 if right is not None else 9
+                svd_count[0] += (6 if right is not None else 9) + (2 if p4 == 'half' else 0)
         S = np.zeros(chi)
         s = ctm_spectrum(env)
         S[:len(s)] = s[:chi]
@@ -693,13 +781,13 @@ def ket_environment(env, loc):
 
 
 def evaluate(A, O_num, O_den, T, chi, max_iter, tol=None, cutoff=1e-12, env_num=None, env_den=None,
-             pr='in-move'):
+             pr='in-move', p4='full'):
     """f and g for PEPS A at temperature T (Eqs. "free energy expression" and "gradient
     expression"):
         f = -T (ln kappa_num - ln kappa_den),
         g = 2 d f / d A-bar = -2T (E_num / Z11_num - E_den / Z11_den).
     The numerator <psi|T|psi> uses the Ising PEPO, the denominator <psi|psi> the identity PEPO.
-    Each network is iterated from the cold start (or from the given environment); pr as
+    Each network is iterated from the cold start (or from the given environment); pr and p4 as
     ``iterate``."""
     A = np.asarray(A, dtype=np.float64)
     B = A
@@ -709,7 +797,8 @@ def evaluate(A, O_num, O_den, T, chi, max_iter, tol=None, cutoff=1e-12, env_num=
         d = O.shape[2]
         env = init_env(chi, D, d) if e0 is None else copy_env(e0)
         svds = [0]
-        env, it, dS, S = iterate(env, A, O, B, chi, max_iter, tol, cutoff, pr=pr, svd_count=svds)
+        env, it, dS, S = iterate(env, A, O, B, chi, max_iter, tol, cutoff, pr=pr, svd_count=svds,
+                                 p4=p4)
         loc = local_contractions(env, A, O, B)
         E = bra_environment(env, loc)
         res[name] = {'env': env, 'iters': it, 'dS': dS, 'S': S, 'lnk': ln_kappa(loc),

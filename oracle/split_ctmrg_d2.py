@@ -109,42 +109,10 @@ def constraint_residual(env):
 # one symmetric iteration
 # ----------------------------------------------------------------------------------------------
 
-def enlarged_c1(env, A, O, B):
-    """C1 with one column and one row absorbed: C1, the top edge T1^{k,i,b} of the column, the left
-    edge T4^{k,i,b} of the row and the site's three layers, as
-        Ct[h, A.r, O.r, B.r, v, A.d, O.d, B.d]
-    (h: the top chain's bond right of the column; v: the left chain's bond below the row)."""
-    T1k, T1i, T1b = env['T1']
-    T4k, T4i, T4b = env['T4']
-    X = sc._c2('aw,acp->wcp', env['C1'], T1k)
-    X = sc._c2('wcp,ceo->wepo', X, T1i)
-    X = sc._c2('wepo,ehq->whpoq', X, T1b)
-    X = sc._c2('whpoq,wxl->hpoqxl', X, T4k)
-    X = sc._c2('hpoqxl,splDR->hoqxsDR', X, A)
-    X = sc._c2('hoqxsDR,xym->hoqsDRym', X, T4i)
-    X = sc._c2('hoqsDRym,tsomEF->hqDRytEF', X, O)
-    X = sc._c2('hqDRytEF,yvn->hqDRtEFvn', X, T4b)
-    X = sc._c2('hqDRtEFvn,tqnGH->hDREFvGH', X, B)
-    return X.transpose(0, 2, 4, 7, 5, 1, 3, 6)
-
-
-def enlarged_c4(env, A, O, B):
-    """C4 with one column and one row absorbed: C4, the bottom edge T3^{k,i,b} of the column, the
-    left edge T4^{k,i,b} of the row and the site, as
-        Ct[v, A.u, O.u, B.u, h, A.r, O.r, B.r]
-    (v: the left chain's bond above the row; h: the bottom chain's bond right of the column)."""
-    T3k, T3i, T3b = env['T3']
-    T4k, T4i, T4b = env['T4']
-    X = sc._c2('aw,acp->wcp', env['C4'], T3k)
-    X = sc._c2('wcp,ceo->wepo', X, T3i)
-    X = sc._c2('wepo,ehq->whpoq', X, T3b)
-    X = sc._c2('whpoq,ywn->hpoqyn', X, T4b)
-    X = sc._c2('hpoqyn,tUnqR->hpoytUR', X, B)
-    X = sc._c2('hpoytUR,xym->hpotURxm', X, T4i)
-    X = sc._c2('hpotURxm,tsVmoS->hpURxsVS', X, O)
-    X = sc._c2('hpURxsVS,vxl->hpURsVSvl', X, T4k)
-    X = sc._c2('hpURsVSvl,sWlpQ->hURVSvWQ', X, A)
-    return X.transpose(5, 6, 3, 1, 0, 7, 4, 2)
+# the enlarged corners (a corner with one column and one row absorbed) are the directional
+# module's; the symmetric corner update below truncates both of their legs
+enlarged_c1 = sc.enlarged_c1
+enlarged_c4 = sc.enlarged_c4
 
 
 # the opposite boundary's stage-1 pairs as the 180-degree-rotation images of this boundary's (the
@@ -153,22 +121,9 @@ def enlarged_c4(env, A, O, B):
 mirror_stage1 = sc.opposite_stage1
 
 
-def half_p4_halves(env, A, O, B, left):
-    """(rho_T, rho_B) of the half projector 4 (Appendix, projector 4(b)): the 2x1 patch of the
-    two enlarged left corners, the bra lines of both their legs renormalised by projector 1 --
-    P_1T / P_1B on the row cut, and on the column cut the up / down moves' projector 1, which the
-    D2 symmetry gives as P_1T^T for the upper corner and P_1B^T for the lower one (in the frame of
-    the down move ket and bra trade places, so there it acts on the ket line A.r).  Leg orders:
-        rho_T (k1, A.d, O.d | k2, A.r, O.r)    rho_B (k1, A.u, O.u | k2, B.r, O.r)
-    the first three legs cut by projector 4, the last three remaining."""
-    PBa, PTa, _ = left['alpha']                      # [xl, B_v, k], [k, xl, B_v]
-    Ct1 = enlarged_c1(env, A, O, B)                   # [h, A.r, O.r, B.r, v, A.d, O.d, B.d]
-    X = sc._c2('hpqrvabc,kvc->hpqrkab', Ct1, PTa)
-    U = sc._c2('hpqrkab,jhr->kabjpq', X, PTa)
-    Ct4 = enlarged_c4(env, A, O, B)                   # [v, A.u, O.u, B.u, h, A.r, O.r, B.r]
-    X = sc._c2('vabchpqr,vck->kabhpqr', Ct4, PBa)
-    L = sc._c2('kabhpqr,hpj->kabjrq', X, PBa)
-    return U, L
+# the half projector 4's patch: with the D2 symmetry the up / down moves' projector 1 are this
+# move's own P_1T / P_1B (the defaults of ``split_ctmrg.half_p4_halves``)
+half_p4_halves = sc.half_p4_halves
 
 
 def sym_projectors(env, A, O, B, chi, cutoff=1e-12, p4='full', pr='mirror', info=None):

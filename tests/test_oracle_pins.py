@@ -493,6 +493,52 @@ def test_paired_moves_are_the_single_moves_of_one_environment():
                 assert out[key] is env[key]
 
 
+def test_half_p4_perpendicular_pairs_are_the_perpendicular_moves():
+    """Appendix, projector 4(b): the half projector 4 renormalises the column cuts of the
+    enlarged corners with the up and down moves' P1.  ``perpendicular_alpha_pairs`` computes them
+    in the frame of whichever move calls it; on a non-symmetric environment (D=2, chi=6) the pairs
+    it finds in the left, right, up and down moves' frames are the (up, down), (down, up),
+    (left, right) and (right, left) moves' own stage-1 alpha pairs (oblique projectors 1e-9)."""
+    T, D, chi = 4.5, 2, 6
+    A = inputs.perturbed_product_peps(D, 3, eps=0.3)
+    O = ising.ising_pepo(1.0 / T)
+    env, *_ = sc.iterate(sc.init_env(chi, D, 2), A, O, A, chi, 3)
+    own = {}
+    for w in 'LRUD':
+        inf = {}
+        sc.move(env, A, O, A, w, chi, info=inf)
+        own[w] = _composite(inf['left']['alpha'])
+    expect = {'L': 'UD', 'R': 'DU', 'U': 'LR', 'D': 'RL'}
+    for w in 'LRUD':
+        up, down = sc.perpendicular_alpha_pairs(*sc.to_frame(w, env, A, O, A), chi)
+        for got, m in zip((_composite(up), _composite(down)), expect[w]):
+            assert np.linalg.norm(got - own[m]) <= 1e-9 * np.linalg.norm(got), (w, m)
+            others = [x for x in 'LRUD' if x != m]
+            assert all(np.linalg.norm(got - own[x]) > 1e-6 * np.linalg.norm(got) for x in others)
+
+
+def test_directional_half_p4_is_the_symmetric_one_on_a_symmetric_environment():
+    """On a D2-symmetric environment of a D4-symmetric PEPS (D=2, chi=6, four symmetric
+    iterations), the directional half projector 4 -- the up and down moves' P1 computed from the
+    environment -- is the symmetric scheme's, which takes them from the symmetry: the same
+    singular values (1e-13 of the largest) and oblique projector (1e-11)."""
+    from oracle import split_ctmrg_d2 as sd
+    T, D, chi = 4.5, 2, 6
+    A = sd.d4_project(inputs.perturbed_product_peps(D, 3, eps=0.3))
+    O = ising.ising_pepo(1.0 / T)
+    env = sd.sym_init_env(chi, D, 2)
+    for _ in range(4):
+        env = sd.sym_iteration(env, A, O, A, chi, p4='half')
+    left = sc.stage1_left(env, A, O, A, chi)
+    up, down = sc.perpendicular_alpha_pairs(env, A, O, A, chi)
+    P_sym = sc.projector_pair(*sc.half_p4_halves(env, A, O, A, left), (0, 1, 2), chi, 1e-12)
+    P_dir = sc.projector_pair(*sc.half_p4_halves(env, A, O, A, left, up[1], down[0]), (0, 1, 2),
+                              chi, 1e-12)
+    assert np.max(np.abs(P_sym[2] - P_dir[2])) <= 1e-13 * P_sym[2][0]
+    a, b = _composite(P_sym), _composite(P_dir)
+    assert np.linalg.norm(a - b) <= 1e-11 * np.linalg.norm(a)
+
+
 def test_oracle_flop_counter():
     """The oracle's algorithmic FLOP count: 2 x the product of every distinct label's dimension
     for a pairwise contraction (2 M N K for a matrix product, batch labels included)."""
