@@ -654,7 +654,7 @@ UPDATED = {'L': ('C1', 'C4', 'T4'), 'R': ('C2', 'C3', 'T2'), 'U': ('C1', 'C2', '
            'D': ('C3', 'C4', 'T3')}  # the stored tensors each move renormalises
 
 
-def paired_move(env, A, O, B, pair, chi, cutoff=1e-12, svd_count=None):
+def paired_move(env, A, O, B, pair, chi, cutoff=1e-12, svd_count=None, p4='full'):
     """Two opposite moves ('LR' or 'UD') on one environment: each move's stage-1 pairs are computed
     once and serve both as its own (P1-P3) and, mapped by ``opposite_stage1``, as the other move's
     P^R (the Appendix takes P^R from the right move); each move's stage-2 pairs and its
@@ -670,14 +670,14 @@ def paired_move(env, A, O, B, pair, chi, cutoff=1e-12, svd_count=None):
         inf = {}
         # left_move recomputes this move's stage-1 pairs from the same halves (same values)
         C1n, T4n, C4n = left_move(e, a, o, b, chi, cutoff, info=inf,
-                                  right=opposite_stage1(left[other]))
+                                  right=opposite_stage1(left[other]), p4=p4)
         e2 = dict(e)
         e2['C1'], e2['T4'], e2['C4'] = C1n, T4n, C4n
         new = from_frame(w, e2)
         for key in UPDATED[w]:
             out[key] = new[key]
     if svd_count is not None:
-        svd_count[0] += 12
+        svd_count[0] += 12 + (4 if p4 == 'half' else 0)
     return out
 
 
@@ -709,7 +709,7 @@ def iterate(env, A, O, B, chi, max_iter, tol=None, cutoff=1e-12, S_prev=None, tr
     for it in range(1, max_iter + 1):
         if pr == 'paired':
             for pair in ('LR', 'UD'):
-                env = paired_move(env, A, O, B, pair, chi, cutoff, svd_count)
+                env = paired_move(env, A, O, B, pair, chi, cutoff, svd_count, p4)
         for w in ('LRUD' if pr != 'paired' else ''):
             right = None
             if pr == 'opposite-move' and OPPOSITE_MOVE[w] in last:
