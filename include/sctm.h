@@ -135,9 +135,11 @@ enum { SCTM_METHOD_SPLIT = 0, SCTM_METHOD_REDUCED = 1, SCTM_METHOD_SPLIT_D2 = 2 
  *   SCTM_P4_HALF  the 2x1-cell patch: the two enlarged left corners (C1 and C4 each with one
  *                 column and one row absorbed), the bra lines of both their legs renormalised by
  *                 projector 1 -- on the column cut by the up / down moves' projector 1, which the
- *                 D2 symmetry gives as the transposed P_1T / P_1B (in the down move's frame ket
+ *                 D2 symmetry gives as the transposed P_1T / P_1B, and which the directional
+ *                 split method computes in each move from the same environment (two more SVD
+ *                 pipelines per move; environment gradient only) (in the down move's frame ket
  *                 and bra trade places, so the lower corner's column-cut projector acts on its
- *                 ket line).  Cost O(chi^3 D^3 d^3); SCTM_METHOD_SPLIT_D2 only. */
+ *                 ket line).  Cost O(chi^3 D^3 d^3); not with SCTM_METHOD_REDUCED. */
 enum { SCTM_P4_FULL = 0, SCTM_P4_HALF = 1 };
 enum { SCTM_MOVE_LEFT = 0, SCTM_MOVE_RIGHT = 1, SCTM_MOVE_UP = 2, SCTM_MOVE_DOWN = 3 };
 
@@ -163,7 +165,7 @@ typedef struct {
     void* cuda_stream;            /* cudaStream_t for all work, NULL = legacy default       */
     int svd_mode;                 /* SCTM_SVD_* (default SCTM_SVD_QR)                       */
     int method;                   /* SCTM_METHOD_SPLIT (default), _REDUCED or _SPLIT_D2     */
-    int p4_mode;                  /* SCTM_P4_FULL (default) or SCTM_P4_HALF (SPLIT_D2 only) */
+    int p4_mode;                  /* SCTM_P4_FULL (default) or SCTM_P4_HALF (not REDUCED)   */
     int jacobi;                   /* SCTM_JACOBI_CTA (default) or SCTM_JACOBI_CLUSTER       */
 } sctm_opts;
 

@@ -192,7 +192,8 @@ sctm_status sctm_create(const double* peps, const double* pepo, int chi, const s
          (opts.precision != SCTM_PREC_FP64 || opts.grad_mode != SCTM_GRAD_ENV)) ||
         (opts.method == SCTM_METHOD_SPLIT_D2 && opts.grad_mode != SCTM_GRAD_ENV) ||
         (opts.p4_mode != SCTM_P4_FULL && opts.p4_mode != SCTM_P4_HALF) ||
-        (opts.p4_mode == SCTM_P4_HALF && opts.method != SCTM_METHOD_SPLIT_D2) ||
+        (opts.p4_mode == SCTM_P4_HALF &&
+         (opts.method == SCTM_METHOD_REDUCED || opts.grad_mode != SCTM_GRAD_ENV)) ||
         (opts.jacobi != SCTM_JACOBI_CTA && opts.jacobi != SCTM_JACOBI_CLUSTER))
         return SCTM_EINVAL;
     std::unique_ptr<sctm_ctx> c(new sctm_ctx());
@@ -496,6 +497,8 @@ sctm_status sctm_set_grad_mode(sctm_ctx* ctx, int mode, double tol, int max_matv
         throw Error(SCTM_EINVAL, "svd_grad_cutoff must lie in [0, 1)");
     if (mode == SCTM_GRAD_ADJOINT && ctx->opts.method != SCTM_METHOD_SPLIT)
         throw Error(SCTM_EINVAL, "the adjoint gradient is built for the split method only");
+    if (mode == SCTM_GRAD_ADJOINT && ctx->opts.p4_mode == SCTM_P4_HALF)
+        throw Error(SCTM_EINVAL, "the adjoint gradient is built for the full projector 4 only");
     if (mode == SCTM_GRAD_ADJOINT && !(tol > 0.0 && tol < 1.0 && max_matvecs >= 1))
         throw Error(SCTM_EINVAL, "adjoint tolerance must lie in (0, 1), max_matvecs >= 1");
     ctx->grad_mode = mode;

@@ -891,13 +891,57 @@ static Frame make_frame(const Network& n, int move) {
     return f;
 }
 
+// The alpha cut's one-column patch halves (rho_T, rho_B) of frame g, legs (xl, A_v, O_v, B_v, xr):
+// the contractions of build_left_move's one-column patches (the alpha halves pass through the
+// kappa and iota ones), for another move's frame.  The directional half projector 4 takes the up
+// and down moves' projector 1 from these, on the same environment as the move's own projectors.
+static void alpha_halves(Engine& e, Network& net, Plan& P, const Frame& g, Ten& Ua, Ten& La) {
+    auto C = [&](const char* spec, const Ten& X, const Ten& Y) { return e.ctr(net, P, spec, X, Y); };
+    const Ten &C1 = g.C[0], &C2 = g.C[1], &C3 = g.C[2], &C4 = g.C[3];
+    const Ten &T1k = g.T[0][0], &T1i = g.T[0][1], &T1b = g.T[0][2];
+    const Ten &T2k = g.T[1][0], &T2i = g.T[1][1], &T2b = g.T[1][2];
+    const Ten &T3k = g.T[2][0], &T3i = g.T[2][1], &T3b = g.T[2][2];
+    const Ten &T4k = g.T[3][0], &T4i = g.T[3][1], &T4b = g.T[3][2];
+    const Ten &A = g.A, &O = g.O, &B = g.B;
+    Ten X = C("av,acp->vcp", C1, T1k);
+    X = C("vcp,ceo->vepo", X, T1i);
+    const Ten Ct1 = C("vepo,ehb->hvpob", X, T1b);            // [h, v, ua, uo, ub]
+    X = C("av,acE->vcE", C4, T3k);
+    X = C("vcE,cef->veEf", X, T3i);
+    const Ten Ct4 = C("veEf,ehg->hvEfg", X, T3b);            // [h, v, da, do, db]
+    const Ten Ctop = C("hvpob,hw->vpobw", Ct1, C2);          // [v1, ua, uo, ub, v2]
+    const Ten Cbot = C("hvEfg,hw->vEfgw", Ct4, C3);          // [v4, da, do, db, v3]
+    X = C("vaobw,vxl->xaoblw", Ctop, T4k);
+    X = C("xaoblw,saler->xobwser", X, A);
+    const Ten Uk = C("xobwser,wyr->xesoby", X, T2k);         // (xl, A.d, s, O.u, B.u, xr)
+    X = C("xesoby,xXl->Xesobyl", Uk, T4i);
+    X = C("Xesobyl,tsolfr->Xebyftr", X, O);
+    const Ten Ui = C("Xebyftr,yYr->XeftbY", X, T2i);         // (xl, A.d, O.d, s', B.u, xr)
+    X = C("xeftby,xXl->Xeftbyl", Ui, T4b);
+    X = C("Xeftbyl,tblgr->Xefygr", X, B);
+    Ua = C("Xefygr,yYr->XefgY", X, T2b);                     // (xl, A_v, O_v, B_v, xr)
+    X = C("vefgw,xvl->xefgwl", Cbot, T4b);
+    X = C("xefgwl,tblgr->xefwtbr", X, B);
+    const Ten Li = C("xefwtbr,ywr->xeftby", X, T2b);
+    X = C("XeftbY,xXl->xeftbYl", Li, T4i);
+    X = C("xeftbYl,tsolfr->xebYsor", X, O);
+    const Ten Lk = C("xebYsor,yYr->xesoby", X, T2i);
+    X = C("XesobY,xXl->xesobYl", Lk, T4k);
+    X = C("xesobYl,saler->xobYar", X, A);
+    La = C("xobYar,yYr->xaoby", X, T2k);
+}
+
 // ---------------------------------------------------------------------------------------------
 // the left move (Sec. III.B, Fig. 5; Sec. III.C and Appendix for the projectors)
 // ---------------------------------------------------------------------------------------------
 // sym: the D2-symmetric iteration (Sec. III.B, Eq. "Symmetry constraints" and the symmetric
 // corner absorption): the same projectors and edge update, but each corner absorbs its column
 // and its row at once and both of its legs are truncated by the alpha pair.
-static void build_left_move(Engine& e, Network& net, Plan& P, const Frame& f, bool sym = false) {
+// fu, fd: the frames of the up and down moves seen from this move (directional scheme with the
+// half projector 4, net.p4_half: their projector 1 renormalises the column cuts of the 2 x 1-cell
+// patch; the D2 scheme has them by symmetry).
+static void build_left_move(Engine& e, Network& net, Plan& P, const Frame& f, bool sym = false,
+                            const Frame* fu = nullptr, const Frame* fd = nullptr) {
     auto C = [&](const char* spec, const Ten& X, const Ten& Y) { return e.ctr(net, P, spec, X, Y); };
     const Ten &C1 = f.C[0], &C2 = f.C[1], &C3 = f.C[2], &C4 = f.C[3];
     const Ten &T1k = f.T[0][0], &T1i = f.T[0][1], &T1b = f.T[0][2];
@@ -952,7 +996,9 @@ static void build_left_move(Engine& e, Network& net, Plan& P, const Frame& f, bo
     Ten ULA, URA, ULAO, URAO, Q1pre, Q2pre;           // upper halves (stream 7)
     Ten LLkpre, LRkpre, LLipre, LRipre;               // lower halves, kappa and iota (stream 8)
     Ten Q4pre, Q3pre;                                 // lower halves, alpha (stream 9)
-    const bool half4 = sym && net.p4_half;
+    const bool half4 = net.p4_half && (sym || (fu && fd));
+    if (net.p4_half && !half4) throw Error(SCTM_EINVAL, "half projector 4 without the up/down frames");
+    Engine::PPair prU, prD;  // directional half projector 4: the up / down moves' projector 1
     {
         const Ten* U[6] = {&Ua, &Ua, &Uk, &Uk, &Ui, &Ui};
         const Ten* L[6] = {&La, &La, &Lk, &Lk, &Li, &Li};
@@ -987,6 +1033,11 @@ static void build_left_move(Engine& e, Network& net, Plan& P, const Frame& f, bo
             Q1pre = D("hbErtfRZM,tbMgS->hErfRZgS", D("hbErXtfR,XZM->hbErtfRZM", ULAO, T4b), B);
             if (!half4)  // the upper-right quarter of the 2x2-cell patch
                 Q2pre = D("hbElWtfLS,tbMgS->hElWfLMg", D("hbElYtfL,YWS->hbElWtfLS", URAO, T2b), B);
+            if (half4 && !sym) {  // the up move's projector 1, on this stream after the halves
+                Ten Uu, Lu;
+                alpha_halves(e, net, S, *fu, Uu, Lu);
+                prU = e.projector(net, S, Uu, Lu, "xAOBy", "xB");
+            }
         }
         {
             Plan& S = sub[7];
@@ -1027,6 +1078,13 @@ static void build_left_move(Engine& e, Network& net, Plan& P, const Frame& f, bo
             Y1 = D("hEbMZsoL,yZr->hEbMsoLyr", Y1, T2k);
             Q3pre = D("hEbMsoLyr,splEr->hbMoLypl", Y1, A);
         }
+        if (half4 && !sym) {  // the down move's projector 1
+            Plan& S = sub[8];
+            e.cur_stream = 9;
+            Ten Ud, Ld;
+            alpha_halves(e, net, S, *fd, Ud, Ld);
+            prD = e.projector(net, S, Ud, Ld, "xAOBy", "xB");
+        }
         e.cur_stream = 0;
         e.parallel(P, std::move(sub));
     }
@@ -1040,9 +1098,10 @@ static void build_left_move(Engine& e, Network& net, Plan& P, const Frame& f, bo
     {
         std::vector<Plan> sub(3);
         // alpha (2 x 2 cells): (k1, A_v, O_v | O_v', B_v', kR)
-        // half (2 x 1 cells, D2 scheme): (k1, A.d, O.d | k2, A.r, O.r) above the cut and
-        // (k1, A.u, O.u | k2, B.r, O.r) below, the column-cut bra lines renormalised by the
-        // transposed projector 1 (the lower corner's in the down move's frame: its ket line)
+        // half (2 x 1 cells): (k1, A.d, O.d | k2, A.r, O.r) above the cut and
+        // (k1, A.u, O.u | k2, B.r, O.r) below, the column-cut bra lines renormalised by the up
+        // move's P_T and the down move's P_B (the lower corner's in the down move's frame: its ket
+        // line); in the D2 scheme those are this move's own pair, by symmetry
         {
             Plan& S = sub[0];
             e.cur_stream = 1;
@@ -1050,8 +1109,8 @@ static void build_left_move(Engine& e, Network& net, Plan& P, const Frame& f, bo
             const Ten Q1 = D("hErfRZgS,kZg->hkEfrRS", Q1pre, Pa.PT);
             const Ten Q4 = D("hbSoRxpr,xbk->hkporRS", Q4pre, Pa.PB);
             if (half4) {
-                const Ten U2a = D("hkEfrRS,jhS->kEfjrR", Q1, Pa.PT);
-                const Ten L2a = D("hkporRS,hrj->kpojSR", Q4, Pa.PB);
+                const Ten U2a = D("hkEfrRS,jhS->kEfjrR", Q1, sym ? Pa.PT : prU.PT);
+                const Ten L2a = D("hkporRS,hrj->kpojSR", Q4, sym ? Pa.PB : prD.PB);
                 pr2[0] = e.projector(net, S, U2a, L2a, "abcdef", "abc");
             } else {
                 const Ten Q2 = D("hElWfLMg,kWE->hlLMfgk", Q2pre, Qa.PT);
@@ -1394,9 +1453,18 @@ void Engine::build_network(Network& net) {
     if (sym) {  // one update per iteration (moves 1..3 stay empty)
         build_left_move(*this, net, net.move[SCTM_MOVE_LEFT], make_frame(net, SCTM_MOVE_LEFT), true);
     } else {
+        // the up and down moves seen from each move (left, right, up, down): the frames of
+        // (up, down), (down, up), (left, right), (right, left)
+        const int perp_up[4] = {SCTM_MOVE_UP, SCTM_MOVE_DOWN, SCTM_MOVE_LEFT, SCTM_MOVE_RIGHT};
+        const int perp_down[4] = {SCTM_MOVE_DOWN, SCTM_MOVE_UP, SCTM_MOVE_RIGHT, SCTM_MOVE_LEFT};
         for (int m = 0; m < 4; ++m) {
             tape = &net.tape_move[m];
-            build_left_move(*this, net, net.move[m], make_frame(net, m));
+            if (net.p4_half) {
+                const Frame fu = make_frame(net, perp_up[m]), fd = make_frame(net, perp_down[m]);
+                build_left_move(*this, net, net.move[m], make_frame(net, m), false, &fu, &fd);
+            } else {
+                build_left_move(*this, net, net.move[m], make_frame(net, m));
+            }
         }
     }
     mixed_build = false;

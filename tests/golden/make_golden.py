@@ -35,6 +35,10 @@ CASES = {
     'cfg2_D3_chi36': (3, 36, 4.5115, 1, 0.1, [2, 'converged'], 1e-12, 400),
     'cfg3_D4_chi64': (4, 64, 4.5, 2, 0.1, [2, 'converged'], 1e-11, 300),
     'cfg4_D5_chi100': (5, 100, 4.52, 3, 0.1, [2, 'converged'], 1e-11, 300),
+    # the directional scheme with the half projector 4 (Appendix, projector 4(b); the up and down
+    # moves' P1 from the same environment, split_ctmrg.perpendicular_alpha_pairs): a ninth entry
+    # names projector 4's patch (default 'full')
+    'cfg3_D4_chi64_half_p4': (4, 64, 4.5, 2, 0.1, ['converged'], 1e-11, 300, 'half'),
 }
 
 # the D2-symmetric scheme (Sec. III.B; oracle/split_ctmrg_d2.py) with the half projector 4 and
@@ -86,7 +90,8 @@ def run_case_d2(name):
 
 
 def run_case(name):
-    D, chi, T, seed, eps, records, tol, max_iter = CASES[name]
+    D, chi, T, seed, eps, records, tol, max_iter = CASES[name][:8]
+    p4 = CASES[name][8] if len(CASES[name]) > 8 else 'full'
     A = inputs.perturbed_product_peps(D, seed, eps=eps)
     nets = {'num': ising.ising_pepo(1.0 / T), 'den': ising.identity_pepo()}
     state = {}
@@ -95,7 +100,7 @@ def run_case(name):
                     'done': False}
     out = {'case': name, 'D': D, 'chi': chi, 'T': T, 'seed': seed, 'eps': eps,
            'peps': 'inputs.perturbed_product_peps(%d, %d, eps=%g)' % (D, seed, eps),
-           'cutoff': 1e-12, 'tol': tol, 'records': {},
+           'cutoff': 1e-12, 'tol': tol, 'p4': p4, 'records': {},
            'written_by': 'tests/golden/make_golden.py (oracle/split_ctmrg.py, FP64 NumPy)',
            'host': platform.machine()}
     t0 = time.time()
@@ -124,7 +129,7 @@ def run_case(name):
             steps = n_it - s['it']
             if steps > 0:
                 s['env'], it, s['dS'], s['S'] = sc.iterate(s['env'], A, O, A, chi, steps,
-                                                           None, 1e-12, s['S'])
+                                                           None, 1e-12, s['S'], p4=p4)
                 s['it'] += it
         record(n_it)
     if 'converged' in records:
@@ -132,7 +137,7 @@ def run_case(name):
             s = state[k]
             while s['it'] < max_iter and not (s['dS'] < tol):
                 s['env'], it, s['dS'], s['S'] = sc.iterate(s['env'], A, O, A, chi, 1, None, 1e-12,
-                                                           s['S'])
+                                                           s['S'], p4=p4)
                 s['it'] += it
                 print('  %s %s iteration %d: dS = %.3e' % (name, k, s['it'], s['dS']), flush=True)
         record('converged')

@@ -158,6 +158,29 @@ def test_symmetric_plans_build_without_gpu(lib, D, chi, svd, p4):
     assert out.stdout.strip() == '0', out.stdout + out.stderr
 
 
+@pytest.mark.parametrize('D,chi,svd', [(2, 6, 0), (3, 10, 2), (4, 64, 3)])
+def test_directional_half_p4_plans_build_without_gpu(lib, D, chi, svd):
+    """SCTM_DRYRUN=1 with the directional split method and the half projector 4 (Appendix,
+    projector 4(b)): each move's plan adds the up and down moves' projector-1 pipelines (their
+    one-column alpha patches in their own frames) and the 2x1-cell patch renormalised by them;
+    every label and dimension of all four moves is checked."""
+    import subprocess
+    import sys
+    code = ('import numpy as np\n'
+            'from paper_2506_19339_gb300 import sctm\n'
+            'st, o = sctm.sctm_default_opts()\n'
+            'o.D, o.d, o.svd_mode, o.method = %d, 2, %d, sctm.SCTM_METHOD_SPLIT\n'
+            'o.p4_mode = sctm.SCTM_P4_HALF\n'
+            'A = np.zeros((2,) + (%d,) * 4); O = np.zeros((2, 2) + (2,) * 4)\n'
+            'st, ctx = sctm.sctm_create(A, O, %d, o)\n'
+            'print(st)\n') % (D, svd, D, chi)
+    env = dict(os.environ, SCTM_DRYRUN='1')
+    out = subprocess.run([sys.executable, '-c', code], cwd=ROOT, env=env, capture_output=True,
+                         text=True, timeout=300)
+    assert out.returncode == 0, out.stderr
+    assert out.stdout.strip() == '0', out.stdout + out.stderr
+
+
 def test_symmetric_method_option_checks(lib):
     """The D2-symmetric method has the environment gradient only: the adjoint is rejected on
     entry, before any device work."""
@@ -170,9 +193,13 @@ def test_symmetric_method_option_checks(lib):
     o.grad_mode = sctm.SCTM_GRAD_ENV
     o.method = 3
     assert sctm.sctm_create(A, O, 4, o)[0] == sctm.SCTM_EINVAL
-    o.method = sctm.SCTM_METHOD_SPLIT          # the half projector 4 needs the symmetric scheme
+    o.method = sctm.SCTM_METHOD_REDUCED        # the half projector 4 is a split-method patch
     o.p4_mode = sctm.SCTM_P4_HALF
     assert sctm.sctm_create(A, O, 4, o)[0] == sctm.SCTM_EINVAL
+    o.method = sctm.SCTM_METHOD_SPLIT          # and has the environment gradient only
+    o.grad_mode = sctm.SCTM_GRAD_ADJOINT
+    assert sctm.sctm_create(A, O, 4, o)[0] == sctm.SCTM_EINVAL
+    o.grad_mode = sctm.SCTM_GRAD_ENV
     o.method = sctm.SCTM_METHOD_SPLIT_D2
     o.p4_mode = 2
     assert sctm.sctm_create(A, O, 4, o)[0] == sctm.SCTM_EINVAL
