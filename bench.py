@@ -532,13 +532,20 @@ def run_ours(args):
         for form in FORMS:
             if form == args.precision:
                 continue
-            inst = Instance(sctm, w, form, args.svd, stream, dev, A_host,
-                            jacobi=jacobi_kernel(args))
-            inst.evaluate()
-            torch.cuda.synchronize(dev)
-            m2, f2, i2, s2 = timed(inst, stream, flush, min(args.steps, 2))
-            forms[form] = form_summary(sctm, m2, f2, i2, s2, ref_f, ref_g, inst.g_dev.cpu().numpy())
-            inst.close()
+            try:
+                inst = Instance(sctm, w, form, args.svd, stream, dev, A_host, 'split', p4,
+                                jacobi_kernel(args))
+                try:
+                    inst.evaluate()
+                    torch.cuda.synchronize(dev)
+                    m2, f2, i2, s2 = timed(inst, stream, flush, min(args.steps, 2))
+                    forms[form] = form_summary(sctm, m2, f2, i2, s2, ref_f, ref_g,
+                                               inst.g_dev.cpu().numpy())
+                finally:
+                    inst.close()
+            except Exception as exc:  # noqa: BLE001 -- reported in the line, not fatal
+                torch.cuda.synchronize(dev)
+                forms[form] = {'error': str(exc)[:300]}
         if p4 == 'full':
             # the directional scheme with the half projector 4 (Appendix, projector 4(b); the up
             # and down moves' P1 from the same environment): the headline precision and stopping
@@ -616,6 +623,10 @@ def run_ours(args):
         'fp64_peak_measured_tflops': fp64_peak,
     }
     head_form = forms[args.precision]
+    full_p4_df = head_form['abs_df_vs_oracle']
+    if gkey == 'split-half-p4':  # the half projector 4 benched: |df| against the full-P4 value too
+        fg = load_golden(w, 'split')
+        full_p4_df = (abs(fs[-1] - fg['records']['converged']['f']) if fg else None)
     n_steps = args.steps * world
     value = n_steps / (total_ms * 1e-3)
     line = {
@@ -634,6 +645,7 @@ def run_ours(args):
                    'parallelism': 'replicas',
                    'l2': 'flushed before every step (256 MiB write, outside the step events)'},
         'accepted': head_form['accepted'], 'abs_df_vs_oracle': head_form['abs_df_vs_oracle'],
+        'abs_df_vs_full_p4_oracle': full_p4_df,
         'forms': forms,
         'iterations_per_s': float(np.sum(its)) / (total_ms * 1e-3),
         'gaussian_seed2_iterations_per_s': gauss_its,

@@ -39,6 +39,8 @@ CASES = {
     # moves' P1 from the same environment, split_ctmrg.perpendicular_alpha_pairs): a ninth entry
     # names projector 4's patch (default 'full')
     'cfg3_D4_chi64_half_p4': (4, 64, 4.5, 2, 0.1, ['converged'], 1e-11, 300, 'half'),
+    # a small case of the same reading, converged further than the GPU's stopping rule
+    'half_p4_D3_chi16': (3, 16, 4.5115, 1, 0.1, ['converged'], 1e-13, 400, 'half'),
 }
 
 # the D2-symmetric scheme (Sec. III.B; oracle/split_ctmrg_d2.py) with the half projector 4 and

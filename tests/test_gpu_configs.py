@@ -147,6 +147,34 @@ def test_converged_mixed_form_cluster_jacobi():
     assert abs(f - ref['f']) <= 1e-8, (f, ref['f'])
 
 
+@pytest.mark.parametrize('svd,prec', [(sctm.SCTM_SVD_QR, sctm.SCTM_PREC_FP64),
+                                      (sctm.SCTM_SVD_PARTIAL_RANDOM, sctm.SCTM_PREC_F64EMU)])
+def test_directional_half_p4_converged(svd, prec):
+    """The directional scheme with the half projector 4 (Appendix, projector 4(b); the up and down
+    moves' projector 1 computed in each move from the same environment) at D=3, chi=16, against
+    the oracle's value of the same reading converged to ||dS|| < 1e-13 (tests/golden/
+    half_p4_D3_chi16.json).  The GPU stops at 1e-11: f to 1e-10; g to 1e-6, because this
+    reading's g still moves below that stopping point -- the oracle's own g stopped at 1e-11 is
+    1.24e-7 from its value at 1e-13 (measured), and the GPU measured the same 1.24e-7 / 1.26e-7
+    (f 1.7e-13 / 1.4e-13) with both SVD paths."""
+    g = golden('half_p4_D3_chi16')
+    ref = g['records']['converged']
+    A = peps(g)
+    st, O = sctm.sctm_ising_pepo(g['T'])
+    r = sctm.SplitCTMRG(A, O, g['chi'], g['T'], precision=prec, svd_mode=svd,
+                        p4_mode=sctm.SCTM_P4_HALF)
+    try:
+        st, it, ds = r.iterate(400, 1e-11)
+        f, gr = r.free_energy(), r.grad()
+    finally:
+        r.close()
+    print('half P4 D=3 chi=16 svd %d precision %d: %d iterations, |df|/|f| = %.2e, |dg|/|g| = %.2e'
+          % (svd, prec, it, abs(f - ref['f']) / abs(ref['f']), rel(gr, ref['g'])))
+    assert st == sctm.SCTM_OK, (st, it)
+    assert abs(f - ref['f']) <= 1e-10 * abs(ref['f']), (f, ref['f'])
+    assert rel(gr, ref['g']) <= 1e-6
+
+
 @pytest.mark.parametrize('network', [sctm.SCTM_NET_NUM, sctm.SCTM_NET_DEN])
 def test_first_left_move_full_size(network):
     """One left move (Sec. III.B) at D=4, chi=64 from the shared SplitMix64 cold start, with the
