@@ -7,11 +7,14 @@ iterated (left, right, up, down moves per iteration, Sec. III.B) until ||S[i+1] 
 libsctm.so.  The workload is D=4, chi=64, T=4.5 with the contractive stand-in PEPS
 (perturbed product state, seed 2, eps 0.1), for which the iteration converges; an evaluation
 counts only if |f - f_oracle| <= 1e-8, f_oracle being the FP64 oracle's converged value stored in
-tests/golden/cfg3_D4_chi64.json (written by tests/golden/make_golden.py).
+tests/golden/cfg3_D4_chi64.json (written by tests/golden/make_golden.py).  Beside the headline
+form the line carries the other precision forms and the directional scheme with the half
+projector 4 (Appendix, projector 4(b)), each with its error against the oracle.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|f64emu|tf32x3]
                     [--impl ours|reference] [--batch B] [--method split|split-d2]
-                    [--gemm M,N,K] [--jacobi-kernel cluster|cta] [--jacobi-timing k]
+                    [--p4 full|half] [--gemm M,N,K] [--jacobi-kernel cluster|cta]
+                    [--jacobi-timing k]
 
 Prints one JSON line (rank 0).  Under torchrun with N > 1 every rank runs an independent replica
 (the single-instance path does not shard) and `value` is the sum over ranks.
