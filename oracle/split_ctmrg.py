@@ -343,13 +343,14 @@ def stage1_projectors(halves, chi, cutoff):
 # two-column patches (stage 2)
 # ----------------------------------------------------------------------------------------------
 
-def two_column_halves(env, A, O, B, left, right):
+def two_column_halves(env, A, O, B, left, right, alpha=True):
     """(rho_T, rho_B) of the two-column patches used by the stage-2 projectors P4 (alpha, 2x2
     cells), P5 (kappa, 1x2 cells) and P6 (iota, 1x2 cells).  Column x belongs to this move and is
     renormalised on its bra-related legs by the stage-1 pair; column x+1 is renormalised on its
     ket-related legs by the opposite boundary's stage-1 pair.  Leg orders:
         kappa: (k2, A.d, O.u | O.u', B.u', kR)   iota: (k3, A.d, O.d | O.d', B.u', kR)
-        alpha: (k1, A_v, O_v | O_v', B_v', kR)"""
+        alpha: (k1, A_v, O_v | O_v', B_v', kR)
+    alpha=False leaves out the alpha patch (the half projector 4 uses its own, 2x1 cells)."""
     Ct1, Ct2, Ct3, Ct4 = absorbed_corners(env)
     T4k, T4i, T4b = env['T4']
     T2k, T2i, T2b = env['T2']
@@ -403,6 +404,8 @@ def two_column_halves(env, A, O, B, left, right):
     L2 = _c2('hkEfQ,hQFBK->kEfFBK', LL, LR)
     out['iota'] = (U2, L2)
 
+    if not alpha:
+        return out
     # ---- alpha (two rows): quarters Q1 (upper-left), Q2 (upper-right), Q4, Q3
     X = _c2('hvpob,vxl->hpobxl', Ct1, T4k)
     X = _c2('hpobxl,splEr->hobxsEr', X, A)
@@ -615,7 +618,7 @@ def left_move(env, A, O, B, chi, cutoff=1e-12, info=None, normalise=True, right=
     else:
         left = {cut: projector_pair(U, L, T_AXES_LEFT[cut], chi, cutoff)
                 for cut, (U, L) in halves.items()}
-    halves2 = two_column_halves(env, A, O, B, left, right)
+    halves2 = two_column_halves(env, A, O, B, left, right, alpha=(p4 != 'half'))
     if p4 == 'half':
         up, down = perpendicular_alpha_pairs(env, A, O, B, chi, cutoff)
         halves2['alpha'] = half_p4_halves(env, A, O, B, left, up[1], down[0])

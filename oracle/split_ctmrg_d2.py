@@ -140,7 +140,7 @@ def sym_projectors(env, A, O, B, chi, cutoff=1e-12, p4='full', pr='mirror', info
     else:
         right = {cut: sc.projector_pair(U, L, sc.T_AXES_RIGHT[cut], chi, cutoff)
                  for cut, (U, L) in halves.items()}
-    halves2 = sc.two_column_halves(env, A, O, B, left, right)
+    halves2 = sc.two_column_halves(env, A, O, B, left, right, alpha=(p4 != 'half'))
     if p4 == 'half':
         halves2['alpha'] = half_p4_halves(env, A, O, B, left)
     stage2 = {cut: sc.projector_pair(U2, L2, (0, 1, 2), chi, cutoff)
