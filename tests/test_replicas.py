@@ -65,3 +65,33 @@ def test_reference_arm_prints_the_contract_line():
     assert line['e2e']['h2d_bytes_per_step'] == 0 and line['e2e']['d2h_bytes_per_step'] == 0
     # the step is the bounded sample, much shorter than the evaluation it is scaled to
     assert line['ms_per_step'] < 1000.0 * line['sec_per_eval_extrapolated']
+
+
+def test_bench_option_logic():
+    """The bench's defaults (FP64 emulation, randomized partial SVD, directional scheme, the
+    cluster Jacobi kernel; the one-CTA kernel for the D2 scheme) and its stored oracle values: each
+    method and projector-4 choice finds the golden file of its own reading at the workload size."""
+    import importlib
+    sys.path.insert(0, ROOT)
+    bench = importlib.import_module('bench')
+    saved = sys.argv
+    try:
+        sys.argv = ['bench.py']
+        args = bench.parse()
+        assert (args.precision, args.svd, args.method) == ('f64emu', 'partial-random', 'split')
+        assert bench.jacobi_kernel(args) == 'cluster'
+        args.method = 'split-d2'
+        assert bench.jacobi_kernel(args) == 'cta'
+        w = bench.workload(bench.parse())
+        fs = {}
+        for key in ('split', 'split-half-p4', 'split-d2'):
+            g = bench.load_golden(w, key)
+            assert g is not None, key
+            rec = g['records'].get('converged') or g['records'].get('fixed')
+            assert len(rec['g']) == 2 * w['D'] ** 4
+            fs[key] = rec['f']
+        # the two projector-4 readings agree in f to the bench's acceptance bound
+        assert abs(fs['split'] - fs['split-half-p4']) <= bench.ACCEPT_DF
+        assert bench.load_golden(dict(w, chi=32), 'split') is None
+    finally:
+        sys.argv = saved
